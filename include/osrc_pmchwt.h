@@ -1,0 +1,199 @@
+/*
+ * osrc_pmchwt.h -- C ABI of the GB300 (sm_103a) OSRC-preconditioned PMCHWT
+ * library for harmonic acoustic transmission through a penetrable object
+ * (van 't Wout, Haqshenas, Gelat, Betcke, Saffari, "Frequency-robust
+ * preconditioning of boundary integral equations for acoustic transmission",
+ * J. Comput. Phys. 2022, arXiv 2104.04609).
+ *
+ * The problem (Sec. 2.1, eq. "helmholtz"): exterior wavenumber k_ext, interior
+ * wavenumber k_int, density ratio rho = rho_int / rho_ext, a closed surface
+ * given as a flat-triangle mesh.  The unknowns are the P1 coefficients of
+ * psi = gamma_N^+ u_tot and phi = gamma_D u_tot (Sec. 2.2), stored in the
+ * permuted order of Sec. 2.7:  x = [psi_0 .. psi_{nv-1}, phi_0 .. phi_{nv-1}].
+ * The system matrix is the permuted PMCHWT operator of Sec. 2.7,
+ *     B = [[V0 + rho V1, -K0 - K1], [T0 + T1, D0 + D1 / rho]],
+ * discretised with P1 Galerkin (Sec. 2.3), left-preconditioned by the mass
+ * matrix (strong form, Sec. 2.4) and by the OSRC operator
+ * diag(L_DtN, L_NtD) (Sec. 2.6, 2.7), and solved by GMRES without restart
+ * (Sec. 3.1).
+ *
+ * Conventions for every entry point:
+ *  - Complex vectors are interleaved double (re, im), i.e. C99
+ *    "double complex" / cuDoubleComplex, one vector of 2*nv entries per
+ *    right-hand side, right-hand sides stored one after another.
+ *  - "device" pointers are CUDA global-memory pointers owned by the caller
+ *    (for instance PyTorch tensors); "host" pointers are ordinary memory.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    All device work of a call is enqueued on that stream.
+ *  - Every call returns an osrc_status.  No C++ exception and no device trap
+ *    crosses the ABI.  On error the output buffers are unspecified and the
+ *    handles stay valid.
+ *  - Handles (osrc_ctx, osrc_mesh, osrc_problem) own the device memory they
+ *    allocate.  A handle must not be used from two host threads at once.
+ */
+#ifndef OSRC_PMCHWT_H
+#define OSRC_PMCHWT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+typedef enum osrc_status {
+    OSRC_OK = 0,
+    OSRC_INVALID_ARG = 1,     /* bad pointer, size, index, NaN, degenerate mesh */
+    OSRC_OUT_OF_MEMORY = 2,   /* device allocation failed or memory budget exceeded */
+    OSRC_CUDA_ERROR = 3,      /* a CUDA runtime call failed */
+    OSRC_NOT_CONVERGED = 4,   /* an iterative solver reached its iteration limit */
+    OSRC_BREAKDOWN = 5,       /* Krylov breakdown (zero pivot in COCG / GMRES) */
+    OSRC_TIMEOUT = 6,         /* a bounded device wait gave up */
+    OSRC_UNSUPPORTED = 7      /* option not implemented or device not capable */
+} osrc_status;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *osrc_status_string(int status);
+
+/* ---- opaque handles ------------------------------------------------------- */
+typedef struct osrc_ctx osrc_ctx;
+typedef struct osrc_mesh osrc_mesh;
+typedef struct osrc_problem osrc_problem;
+
+/* Precision / operator path of a problem. */
+enum {
+    OSRC_FP32_MATFREE = 0,  /* matrix-free FP32 far field + FP64 near CSR (Sec. 2.2/2.3 operators) */
+    OSRC_FP64_DENSE = 1     /* dense FP64 assembled 2nv x 2nv system */
+};
+
+/* Parameters of one transmission problem (Sec. 2.1, 2.6, 3.1). */
+typedef struct osrc_params {
+    double k_ext;        /* exterior wavenumber k_0 (> 0) */
+    double k_int;        /* interior wavenumber k_1 (> 0) */
+    double rho_ratio;    /* rho_1 / rho_0 (> 0) */
+    int n_pade;          /* number of Pade terms N_Pade (1..16; paper: 4) */
+    double theta;        /* branch-cut rotation angle (paper: pi/3) */
+    double damping_R;    /* R in k_eps = k (1 + 0.4 i (k R)^(-2/3)); <= 0: mean edge length */
+    int osrc_side;       /* wavenumber of the OSRC operator: 0 exterior, 1 interior */
+    int n_ss;            /* Gauss points per dimension of the Sauter-Schwab rules (2..12) */
+    int precision;       /* OSRC_FP32_MATFREE or OSRC_FP64_DENSE */
+    double inner_tol;    /* relative residual of the inner mass / shifted solves (<= 1e-8) */
+    int inner_maxit;     /* iteration cap of the inner solves */
+} osrc_params;
+
+/* Fills p with the paper's defaults: n_pade 4, theta pi/3, interior OSRC
+ * wavenumber, R = mean edge length, n_ss 4, FP32 matrix-free, inner_tol 1e-10. */
+void osrc_params_default(osrc_params *p);
+
+/* Result record of osrc_gmres_solve (per right-hand side: the last one). */
+typedef struct osrc_solve_info {
+    int iterations;            /* GMRES iterations of the last right-hand side */
+    int converged;             /* 1 if every right-hand side reached tol */
+    double precond_residual;   /* |P M^-1 (b - B x)| / |P M^-1 b| (GMRES estimate) */
+    double true_residual;      /* |b - B x| / |b|, weak form, recomputed at the end */
+    double ms_total;           /* wall time of the call in ms */
+    double ms_matvec;          /* time in B x (far + near), ms, summed */
+    double ms_precond;         /* time in M^-1 and OSRC, ms, summed */
+    double ms_arnoldi;         /* time in orthogonalisation, ms, summed */
+    int inner_iterations_max;  /* largest inner CG/COCG iteration count seen */
+    int total_iterations;      /* GMRES iterations summed over right-hand sides */
+} osrc_solve_info;
+
+/* ---- context -------------------------------------------------------------- */
+/* Creates a context on CUDA device `device`.  mem_budget_bytes caps the device
+ * memory the library allocates through this context (0 = no cap); an
+ * allocation beyond it fails with OSRC_OUT_OF_MEMORY. */
+int osrc_create(osrc_ctx **out, int device, size_t mem_budget_bytes);
+void osrc_destroy(osrc_ctx *ctx);
+/* Device bytes currently allocated through the context. */
+size_t osrc_mem_used(const osrc_ctx *ctx);
+
+/* ---- mesh ----------------------------------------------------------------- */
+/* Host-only check of a surface mesh (no device work): indices in range, no
+ * repeated vertex in a triangle, no zero-area triangle, finite coordinates,
+ * every edge shared by exactly two triangles with opposite orientation
+ * (closed, consistently oriented 2-manifold).  verts: host, nv x 3 row-major;
+ * tris: host, nt x 3, counter-clockwise seen from outside. */
+int osrc_mesh_validate(const double *verts, int32_t nv, const int32_t *tris, int32_t nt);
+
+/* Validates (as above), copies the mesh to the device and builds its
+ * topology.  verts, tris: host, not retained. */
+int osrc_mesh_create(osrc_ctx *ctx, const double *verts, int32_t nv,
+                     const int32_t *tris, int32_t nt, osrc_mesh **out);
+void osrc_mesh_destroy(osrc_mesh *mesh);
+/* Mean edge length of the mesh (the default damping length R). */
+double osrc_mesh_mean_edge(const osrc_mesh *mesh);
+
+/* ---- problem (resident per-mesh, per-frequency state) ----------------------- */
+/* Builds the resident state of one problem on the mesh: FP32 far-field
+ * geometry, the near-field CSR of touching triangle pairs computed on the
+ * device in FP64 by Sauter-Schwab quadrature, the P1 mass M and stiffness S
+ * (CSR, FP64), the Pade constants of the OSRC operator (Sec. 2.6).  With
+ * OSRC_FP64_DENSE it also assembles the dense system matrix.  The mesh must
+ * outlive the problem. */
+int osrc_problem_create(osrc_mesh *mesh, const osrc_params *params,
+                        osrc_problem **out, void *stream);
+void osrc_problem_destroy(osrc_problem *pb);
+int osrc_problem_nv(const osrc_problem *pb);
+
+/* ---- right-hand sides (Sec. 2.7) --------------------------------------------- */
+/* b[r] = [<u_inc, phi_i>; <du_inc/dn, phi_i>], 6-point rule per triangle.
+ * Plane wave u_inc = exp(i k_ext d.x), dirs: host, nrhs x 3 unit vectors.
+ * b: device, nrhs x 2nv complex. */
+int osrc_rhs_planewave(osrc_problem *pb, const double *dirs, int nrhs, void *b, void *stream);
+/* Point source u_inc = exp(i k_ext |x - x0|) / (4 pi |x - x0|); srcs: host,
+ * nrhs x 3 positions off the surface. */
+int osrc_rhs_pointsource(osrc_problem *pb, const double *srcs, int nrhs, void *b, void *stream);
+
+/* ---- operators ------------------------------------------------------------------ */
+enum { OSRC_WEAK = 0, OSRC_STRONG = 1 };
+enum { OSRC_PART_FAR = 1, OSRC_PART_NEAR = 2, OSRC_PART_ALL = 3 };
+
+/* y = B x (form OSRC_WEAK) or y = M^-1 B x (OSRC_STRONG), for nrhs vectors.
+ * part selects the far-field (triangle pairs sharing no vertex, 6-point rule
+ * on both triangles) and/or near-field (touching pairs, Sauter-Schwab) terms;
+ * a partial apply is only meaningful with OSRC_WEAK.  x, y: device,
+ * nrhs x 2nv complex, must not overlap. */
+int osrc_pmchwt_apply(osrc_problem *pb, const void *x, void *y, int nrhs,
+                      int form, int part, void *stream);
+
+/* y = M^-1 x on both block rows (mass preconditioning, Sec. 2.4): CG on the
+ * P1 mass matrix to params.inner_tol.  x, y: device, nrhs x 2nv complex. */
+int osrc_mass_solve(osrc_problem *pb, const void *x, void *y, int nrhs, void *stream);
+
+/* y = diag(L_DtN, L_NtD) x on strong-form coefficient vectors (Sec. 2.6, 2.7):
+ *   L_DtN u = i k [C0 u + sum_j A_j w_j],  (M - B_j S / k_eps^2) w_j = -S u / k_eps^2
+ *   L_NtD u = [g0 v_0 + sum_j g_j v_j] / (i k),
+ *             (M - S / k_eps^2) v_0 = M u,  (M - B_j S / k_eps^2) v_j = M u
+ * with the rotated-branch Pade coefficients C0, A_j, B_j of sqrt(1+z) and
+ * the partial fractions g0, g_j of its product with (1+z)^-1.  The 2 N_Pade + 1
+ * complex-symmetric shifted systems are solved together by a batched COCG to
+ * params.inner_tol.  x, y: device, nrhs x 2nv complex. */
+int osrc_precond_apply(osrc_problem *pb, const void *x, void *y, int nrhs, void *stream);
+
+/* ---- solve ----------------------------------------------------------------------- */
+enum { OSRC_HOST_BUFFERS = 1 };
+
+/* Solves B x = b for nrhs right-hand sides with GMRES without restart
+ * (Sec. 3.1), x0 = 0, on the OSRC- and mass-preconditioned system
+ * P M^-1 B x = P M^-1 b, stopping when the preconditioned relative residual
+ * is <= tol or after maxit iterations (OSRC_NOT_CONVERGED).  Orthogonalisation
+ * (classical Gram-Schmidt, twice) and the Givens updates are FP64 on the
+ * device.  b, x: nrhs x 2nv complex; device pointers, or host pointers when
+ * flags has OSRC_HOST_BUFFERS (the copies are then part of the call).
+ * info may be NULL. */
+int osrc_gmres_solve(osrc_problem *pb, const void *b, void *x, int nrhs, double tol,
+                     int maxit, int flags, osrc_solve_info *info, void *stream);
+
+/* ---- introspection ---------------------------------------------------------------- */
+/* Number of kernel launches the library has issued on this problem so far. */
+long long osrc_launch_count(const osrc_problem *pb);
+/* Number of touching triangle pairs (near-field pairs) and near CSR blocks. */
+long long osrc_near_pairs(const osrc_problem *pb);
+long long osrc_near_nnz(const osrc_problem *pb);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OSRC_PMCHWT_H */

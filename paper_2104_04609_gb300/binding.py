@@ -1,0 +1,378 @@
+"""Thin ctypes binding of the C ABI in include/osrc_pmchwt.h.
+
+Argument marshalling only: every function has the name of the C entry point
+it calls, takes numpy arrays for host data and torch CUDA tensors (complex128,
+contiguous) for device data, and raises ``OsrcError`` on a non-zero status.
+All computation happens in the CUDA library; if the library is missing the
+import fails loudly (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libosrc_pmchwt.so")
+
+OSRC_OK = 0
+OSRC_INVALID_ARG = 1
+OSRC_OUT_OF_MEMORY = 2
+OSRC_CUDA_ERROR = 3
+OSRC_NOT_CONVERGED = 4
+OSRC_BREAKDOWN = 5
+OSRC_TIMEOUT = 6
+OSRC_UNSUPPORTED = 7
+
+OSRC_FP32_MATFREE = 0
+OSRC_FP64_DENSE = 1
+OSRC_WEAK = 0
+OSRC_STRONG = 1
+OSRC_PART_FAR = 1
+OSRC_PART_NEAR = 2
+OSRC_PART_ALL = 3
+OSRC_HOST_BUFFERS = 1
+
+
+class OsrcError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__(f"{where}: {osrc_status_string(status)} ({status})")
+
+
+class osrc_params(ctypes.Structure):
+    _fields_ = [
+        ("k_ext", ctypes.c_double), ("k_int", ctypes.c_double),
+        ("rho_ratio", ctypes.c_double), ("n_pade", ctypes.c_int),
+        ("theta", ctypes.c_double), ("damping_R", ctypes.c_double),
+        ("osrc_side", ctypes.c_int), ("n_ss", ctypes.c_int),
+        ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double),
+        ("inner_maxit", ctypes.c_int),
+    ]
+
+
+class osrc_solve_info(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+        ("precond_residual", ctypes.c_double), ("true_residual", ctypes.c_double),
+        ("ms_total", ctypes.c_double), ("ms_matvec", ctypes.c_double),
+        ("ms_precond", ctypes.c_double), ("ms_arnoldi", ctypes.c_double),
+        ("inner_iterations_max", ctypes.c_int), ("total_iterations", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_VP = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int32)
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "osrc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "osrc_params_default": (None, [ctypes.POINTER(osrc_params)]),
+    "osrc_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_size_t]),
+    "osrc_destroy": (None, [_VP]),
+    "osrc_mem_used": (ctypes.c_size_t, [_VP]),
+    "osrc_mesh_validate": (ctypes.c_int, [_DP, ctypes.c_int32, _IP, ctypes.c_int32]),
+    "osrc_mesh_create": (ctypes.c_int, [_VP, _DP, ctypes.c_int32, _IP, ctypes.c_int32,
+                                        ctypes.POINTER(_VP)]),
+    "osrc_mesh_destroy": (None, [_VP]),
+    "osrc_mesh_mean_edge": (ctypes.c_double, [_VP]),
+    "osrc_problem_create": (ctypes.c_int, [_VP, ctypes.POINTER(osrc_params),
+                                           ctypes.POINTER(_VP), _VP]),
+    "osrc_problem_destroy": (None, [_VP]),
+    "osrc_problem_nv": (ctypes.c_int, [_VP]),
+    "osrc_rhs_planewave": (ctypes.c_int, [_VP, _DP, ctypes.c_int, _VP, _VP]),
+    "osrc_rhs_pointsource": (ctypes.c_int, [_VP, _DP, ctypes.c_int, _VP, _VP]),
+    "osrc_pmchwt_apply": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, _VP]),
+    "osrc_mass_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+    "osrc_precond_apply": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+    "osrc_gmres_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(osrc_solve_info), _VP]),
+    "osrc_launch_count": (ctypes.c_longlong, [_VP]),
+    "osrc_near_pairs": (ctypes.c_longlong, [_VP]),
+    "osrc_near_nnz": (ctypes.c_longlong, [_VP]),
+}
+
+_LIB = None
+
+
+def lib():
+    """Load the in-tree CUDA library (built by paper_2104_04609_gb300.build)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"CUDA library not built: {LIB_PATH} is missing; run "
+                "`python -c 'import __graft_entry__ as g; g.build()'` first")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(status, where):
+    if status != OSRC_OK:
+        raise OsrcError(status, where)
+
+
+def _host_f64(a, shape_last=3):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_DP)
+
+
+def _host_i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_IP)
+
+
+def _dev(t):
+    """Device pointer of a contiguous complex128 CUDA tensor."""
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128
+            and t.is_contiguous()):
+        raise TypeError("expected a contiguous complex128 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# entry points
+# ---------------------------------------------------------------------------
+def osrc_status_string(status):
+    return lib().osrc_status_string(int(status)).decode()
+
+
+def osrc_params_default(**overrides):
+    p = osrc_params()
+    lib().osrc_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def osrc_create(device=0, mem_budget_bytes=0):
+    h = _VP()
+    _check(lib().osrc_create(ctypes.byref(h), int(device), int(mem_budget_bytes)), "osrc_create")
+    return h
+
+
+def osrc_destroy(ctx):
+    lib().osrc_destroy(ctx)
+
+
+def osrc_mem_used(ctx):
+    return lib().osrc_mem_used(ctx)
+
+
+def osrc_mesh_validate(verts, tris):
+    v, vp = _host_f64(verts)
+    t, tp = _host_i32(tris)
+    return lib().osrc_mesh_validate(vp, v.shape[0] if v.ndim == 2 else 0, tp,
+                                    t.shape[0] if t.ndim == 2 else 0)
+
+
+def osrc_mesh_create(ctx, verts, tris):
+    v, vp = _host_f64(verts)
+    t, tp = _host_i32(tris)
+    h = _VP()
+    _check(lib().osrc_mesh_create(ctx, vp, v.shape[0], tp, t.shape[0], ctypes.byref(h)),
+           "osrc_mesh_create")
+    return h
+
+
+def osrc_mesh_destroy(mesh):
+    lib().osrc_mesh_destroy(mesh)
+
+
+def osrc_mesh_mean_edge(mesh):
+    return lib().osrc_mesh_mean_edge(mesh)
+
+
+def osrc_problem_create(mesh, params, stream=None):
+    h = _VP()
+    _check(lib().osrc_problem_create(mesh, ctypes.byref(params), ctypes.byref(h), _stream(stream)),
+           "osrc_problem_create")
+    return h
+
+
+def osrc_problem_destroy(pb):
+    lib().osrc_problem_destroy(pb)
+
+
+def osrc_problem_nv(pb):
+    return lib().osrc_problem_nv(pb)
+
+
+def osrc_rhs_planewave(pb, dirs, b, stream=None):
+    d, dp = _host_f64(np.atleast_2d(dirs))
+    _check(lib().osrc_rhs_planewave(pb, dp, d.shape[0], _dev(b), _stream(stream)),
+           "osrc_rhs_planewave")
+
+
+def osrc_rhs_pointsource(pb, srcs, b, stream=None):
+    d, dp = _host_f64(np.atleast_2d(srcs))
+    _check(lib().osrc_rhs_pointsource(pb, dp, d.shape[0], _dev(b), _stream(stream)),
+           "osrc_rhs_pointsource")
+
+
+def osrc_pmchwt_apply(pb, x, y, nrhs=1, form=OSRC_WEAK, part=OSRC_PART_ALL, stream=None):
+    _check(lib().osrc_pmchwt_apply(pb, _dev(x), _dev(y), int(nrhs), int(form), int(part),
+                                   _stream(stream)), "osrc_pmchwt_apply")
+
+
+def osrc_mass_solve(pb, x, y, nrhs=1, stream=None):
+    _check(lib().osrc_mass_solve(pb, _dev(x), _dev(y), int(nrhs), _stream(stream)),
+           "osrc_mass_solve")
+
+
+def osrc_precond_apply(pb, x, y, nrhs=1, stream=None):
+    _check(lib().osrc_precond_apply(pb, _dev(x), _dev(y), int(nrhs), _stream(stream)),
+           "osrc_precond_apply")
+
+
+def osrc_gmres_solve(pb, b, x, nrhs=1, tol=1e-5, maxit=500, host_buffers=False,
+                     stream=None, raise_on_nonconvergence=True):
+    """Returns the osrc_solve_info record.  With host_buffers, b and x are
+    numpy complex128 arrays (C-contiguous), else CUDA tensors."""
+    info = osrc_solve_info()
+    if host_buffers:
+        if not (isinstance(b, np.ndarray) and isinstance(x, np.ndarray)
+                and b.dtype == np.complex128 and x.dtype == np.complex128
+                and b.flags.c_contiguous and x.flags.c_contiguous):
+            raise TypeError("host buffers must be C-contiguous complex128 numpy arrays")
+        bp, xp = ctypes.c_void_p(b.ctypes.data), ctypes.c_void_p(x.ctypes.data)
+        flags = OSRC_HOST_BUFFERS
+    else:
+        bp, xp = _dev(b), _dev(x)
+        flags = 0
+    s = lib().osrc_gmres_solve(pb, bp, xp, int(nrhs), float(tol), int(maxit), flags,
+                               ctypes.byref(info), _stream(stream))
+    if s != OSRC_OK and (s != OSRC_NOT_CONVERGED or raise_on_nonconvergence):
+        raise OsrcError(s, "osrc_gmres_solve")
+    return info
+
+
+def osrc_launch_count(pb):
+    return lib().osrc_launch_count(pb)
+
+
+def osrc_near_pairs(pb):
+    return lib().osrc_near_pairs(pb)
+
+
+def osrc_near_nnz(pb):
+    return lib().osrc_near_nnz(pb)
+
+
+# ---------------------------------------------------------------------------
+# convenience owner of the three handles
+# ---------------------------------------------------------------------------
+class Solver:
+    """Context + mesh + problem for one transmission problem, with device
+    tensors in and out.  Parameters are those of ``osrc_params``."""
+
+    def __init__(self, verts, tris, k_ext, k_int, rho_ratio, device=0, mem_budget_bytes=0,
+                 **params):
+        import torch
+
+        self.device = torch.device("cuda", device)
+        self.ctx = osrc_create(device, mem_budget_bytes)
+        self.mesh = None
+        self.pb = None
+        try:
+            self.mesh = osrc_mesh_create(self.ctx, verts, tris)
+            p = osrc_params_default(k_ext=float(k_ext), k_int=float(k_int),
+                                    rho_ratio=float(rho_ratio))
+            for k, v in params.items():
+                setattr(p, k, v)
+            self.params = p
+            self.pb = osrc_problem_create(self.mesh, p)
+        except Exception:
+            self.close()
+            raise
+        self.nv = osrc_problem_nv(self.pb)
+
+    def zeros(self, nrhs=1):
+        import torch
+
+        return torch.zeros((nrhs, 2 * self.nv), dtype=torch.complex128, device=self.device)
+
+    def rhs_planewave(self, dirs):
+        dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
+        b = self.zeros(dirs.shape[0])
+        osrc_rhs_planewave(self.pb, dirs, b)
+        return b
+
+    def rhs_pointsource(self, srcs):
+        srcs = np.atleast_2d(np.asarray(srcs, dtype=np.float64))
+        b = self.zeros(srcs.shape[0])
+        osrc_rhs_pointsource(self.pb, srcs, b)
+        return b
+
+    def apply(self, x, form=OSRC_WEAK, part=OSRC_PART_ALL):
+        x = x.contiguous()
+        y = torch_empty_like(x)
+        osrc_pmchwt_apply(self.pb, x, y, x.shape[0] if x.ndim == 2 else 1, form, part)
+        return y
+
+    def mass_solve(self, x):
+        x = x.contiguous()
+        y = torch_empty_like(x)
+        osrc_mass_solve(self.pb, x, y, x.shape[0] if x.ndim == 2 else 1)
+        return y
+
+    def precond(self, x):
+        x = x.contiguous()
+        y = torch_empty_like(x)
+        osrc_precond_apply(self.pb, x, y, x.shape[0] if x.ndim == 2 else 1)
+        return y
+
+    def solve(self, b, tol=1e-5, maxit=500, raise_on_nonconvergence=True):
+        b = b.contiguous()
+        x = torch_empty_like(b)
+        info = osrc_gmres_solve(self.pb, b, x, b.shape[0] if b.ndim == 2 else 1, tol, maxit,
+                                raise_on_nonconvergence=raise_on_nonconvergence)
+        return x, info
+
+    def launches(self):
+        return osrc_launch_count(self.pb)
+
+    def close(self):
+        if self.pb is not None:
+            osrc_problem_destroy(self.pb)
+            self.pb = None
+        if self.mesh is not None:
+            osrc_mesh_destroy(self.mesh)
+            self.mesh = None
+        if self.ctx is not None:
+            osrc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def torch_empty_like(x):
+    import torch
+
+    return torch.empty_like(x)

@@ -1,0 +1,400 @@
+// k_far.cu -- matrix-free FP32 far-field apply of the permuted PMCHWT
+// operator (Sec. 2.7) for all triangle pairs that share no vertex, with the
+// 6-point degree-4 triangle rule (Strang & Fix / Dunavant) on both triangles.
+//
+// Structure of one apply y = B_far x:
+//   1. far_prep_kernel   (per source triangle)  densities at the 6 source
+//      points and the surface-curl vector of the phi density, FP32;
+//   2. far_kernel        (per test point)       N-body sum over all source
+//      points staged through shared memory in tiles of triangles; both
+//      wavenumbers are evaluated from one distance; the source range is split
+//      over gridDim.y so that the grid fills every SM; partial sums per test
+//      point go to d_part (no atomics);
+//   3. gather_kernel     (per vertex)           sums the partials of the test
+//      points of the incident triangles with the test weights (FP64) and adds
+//      the near-field CSR product (touching pairs, Sauter-Schwab values).
+//
+// Kernel identities (G = e^{ikr}/(4 pi r), d = x - y, r = |d|):
+//   dG/dn_y = H (y - x).n_y,  dG/dn_x = H (x - y).n_x,
+//   H = e^{ikr} (ikr - 1) / (4 pi r^3);
+//   D (Maue form) = G [curl phi_i . curl phi_j - k^2 (n_x.n_y) phi_i phi_j].
+// Because every source point of a flat triangle lies in its plane,
+// (x - y).n_y = x.n_y - n_y.P0 is constant over the triangle's six points,
+// and so is n_x.n_y; the surface curl of the P1 density is constant per
+// triangle.  These per-triangle factors are applied once per (test point,
+// source triangle), not per point pair.
+#include "osrc_internal.cuh"
+
+namespace {
+
+// 6-point symmetric rule: barycentric (1-2a, a, a) and permutations.
+constexpr double kQa1 = 0.445948490915965;
+constexpr double kQw1 = 0.223381589678011;
+constexpr double kQa2 = 0.091576213509771;
+constexpr double kQw2 = 0.109951743655322;
+
+__host__ __device__ inline void rule_point(int q, double bary[3], double &w) {
+    const double a = q < 3 ? kQa1 : kQa2;
+    w = q < 3 ? kQw1 : kQw2;
+    const int i = q % 3;
+    for (int j = 0; j < 3; ++j) bary[j] = (j == i) ? 1.0 - 2.0 * a : a;
+}
+
+constexpr int FAR_THREADS = 128;
+constexpr int FAR_TS = 64;  // source triangles per shared-memory tile
+
+__global__ void far_geom_kernel(const double *__restrict__ verts, const int *__restrict__ tris,
+                                int nt, float4 *__restrict__ pt, float4 *__restrict__ tn,
+                                int4 *__restrict__ tv, double *__restrict__ tgeo) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    double P[3][3];
+    int v[3];
+    for (int a = 0; a < 3; ++a) {
+        v[a] = tris[3 * t + a];
+        for (int j = 0; j < 3; ++j) P[a][j] = verts[3 * v[a] + j];
+    }
+    double e1[3], e2[3], c[3];
+    for (int j = 0; j < 3; ++j) {
+        e1[j] = P[1][j] - P[0][j];
+        e2[j] = P[2][j] - P[0][j];
+    }
+    c[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    c[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    c[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    const double len = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    const double area = 0.5 * len;
+    double n[3] = {c[0] / len, c[1] / len, c[2] / len};
+    for (int q = 0; q < 6; ++q) {
+        double b[3], w;
+        rule_point(q, b, w);
+        double x[3];
+        for (int j = 0; j < 3; ++j) x[j] = b[0] * P[0][j] + b[1] * P[1][j] + b[2] * P[2][j];
+        pt[6 * t + q] = make_float4((float)x[0], (float)x[1], (float)x[2], (float)(w * area));
+    }
+    const double h = n[0] * P[0][0] + n[1] * P[0][1] + n[2] * P[0][2];
+    tn[t] = make_float4((float)n[0], (float)n[1], (float)n[2], (float)h);
+    tv[t] = make_int4(v[0], v[1], v[2], 0);
+    double *g = tgeo + 16 * (size_t)t;
+    g[0] = area;
+    g[1] = n[0];
+    g[2] = n[1];
+    g[3] = n[2];
+    // curl phi_a = n x grad phi_a = (P_{a+1} - P_{a+2}) / (2 area)
+    for (int a = 0; a < 3; ++a)
+        for (int j = 0; j < 3; ++j)
+            g[4 + 3 * a + j] = (P[(a + 1) % 3][j] - P[(a + 2) % 3][j]) / (2.0 * area);
+    g[13] = g[14] = g[15] = 0.0;
+}
+
+// Source densities of one apply: psi_q = w_q |s| sum_b lambda_b(q) psi_b, the
+// same for phi, and c_s = |s| sum_b phi_b curl phi_b (complex 3-vector).
+__global__ void far_prep_kernel(const double2 *__restrict__ x, int nv, int nt,
+                                const int *__restrict__ tris, const float4 *__restrict__ pt,
+                                const double *__restrict__ tgeo, float4 *__restrict__ sA,
+                                float4 *__restrict__ sB, float4 *__restrict__ sC,
+                                float2 *__restrict__ sC2) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    double2 ps[3], ph[3];
+    for (int a = 0; a < 3; ++a) {
+        const int v = tris[3 * t + a];
+        ps[a] = x[v];
+        ph[a] = x[nv + v];
+    }
+    const double *g = tgeo + 16 * (size_t)t;
+    const double area = g[0];
+    for (int q = 0; q < 6; ++q) {
+        double b[3], w;
+        rule_point(q, b, w);
+        const double W = w * area;
+        double2 s = cd(0, 0), f = cd(0, 0);
+        for (int a = 0; a < 3; ++a) {
+            s = cadd(s, cscale(ps[a], b[a]));
+            f = cadd(f, cscale(ph[a], b[a]));
+        }
+        const float4 p = pt[6 * t + q];
+        sA[6 * t + q] = make_float4(p.x, p.y, p.z, (float)(W * s.x));
+        sB[6 * t + q] = make_float4((float)(W * s.y), (float)(W * f.x), (float)(W * f.y), 0.f);
+    }
+    double2 cv[3];
+    for (int j = 0; j < 3; ++j) {
+        cv[j] = cd(0, 0);
+        for (int a = 0; a < 3; ++a) cv[j] = cadd(cv[j], cscale(ph[a], g[4 + 3 * a + j]));
+        cv[j] = cscale(cv[j], area);
+    }
+    sC[t] = make_float4((float)cv[0].x, (float)cv[0].y, (float)cv[1].x, (float)cv[1].y);
+    sC2[t] = make_float2((float)cv[2].x, (float)cv[2].y);
+}
+
+struct FarConst {
+    float k0, k1;      // wavenumbers
+    float k0r, k1r;    // k / (2 pi): phase in revolutions per unit length
+    float rho, irho;   // V and D block weights of the interior operators
+    float dk0, dk1;    // k0^2 and k1^2 / rho: weights of the D normal term
+};
+
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float v) {
+    const float y = v - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+// One thread per test point p (test triangle p / 6, rule point p % 6).
+// Output part[(split * 10 + c) * npts + p], c = u1 (re, im), u2 (re, im),
+// A (x re, x im, y re, y im, z re, z im):
+//   u1 = sum [ (G0 + rho G1) psi_q + (x.n_y - h_y)(H0 + H1) phi_q ]
+//   u2 = sum [ (H0 + H1)(x - y).n_x psi_q - (n_x.n_y)(k0^2 G0 + k1^2/rho G1) phi_q ]
+//   A  = sum_s (sum_q w_q (G0 + G1/rho)) c_s
+// with G, H here without the factor 1/(4 pi) (applied in the gather).
+__global__ void __launch_bounds__(FAR_THREADS)
+far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ tn,
+           const int4 *__restrict__ tv, const float4 *__restrict__ sA,
+           const float4 *__restrict__ sB, const float4 *__restrict__ sC,
+           const float2 *__restrict__ sC2, int nt, int npts, int tris_per_split,
+           FarConst c, float *__restrict__ part) {
+    __shared__ float4 shA[FAR_TS * 6];
+    __shared__ float4 shB[FAR_TS * 6];
+    __shared__ float4 shN[FAR_TS];
+    __shared__ float4 shC[FAR_TS];
+    __shared__ float2 shC2[FAR_TS];
+    __shared__ int4 shV[FAR_TS];
+
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int split = blockIdx.y;
+    const int s_begin = split * tris_per_split;
+    const int s_end = min(nt, s_begin + tris_per_split);
+    const bool active = p < npts;
+    const int tau = active ? p / 6 : 0;
+    const float4 xp = pt[active ? p : 0];
+    const float4 n4 = tn[tau];
+    const int4 vt = tv[tau];
+    const float nxx = n4.x, nxy = n4.y, nxz = n4.z;
+    const float W1 = (float)kQw1, W2 = (float)kQw2;
+
+    float acc[10], cmp[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) acc[i] = cmp[i] = 0.f;
+
+    for (int t0 = s_begin; t0 < s_end; t0 += FAR_TS) {
+        const int cnt = min(FAR_TS, s_end - t0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt * 6; i += blockDim.x) {
+            shA[i] = sA[6 * t0 + i];
+            shB[i] = sB[6 * t0 + i];
+        }
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            shN[i] = tn[t0 + i];
+            shC[i] = sC[t0 + i];
+            shC2[i] = sC2[t0 + i];
+            shV[i] = tv[t0 + i];
+        }
+        __syncthreads();
+
+        float u1r = 0.f, u1i = 0.f, u2r = 0.f, u2i = 0.f;
+        float axr = 0.f, axi = 0.f, ayr = 0.f, ayi = 0.f, azr = 0.f, azi = 0.f;
+        for (int s = 0; s < cnt; ++s) {
+            const int4 vs = shV[s];
+            const bool touch = (vs.x == vt.x) | (vs.x == vt.y) | (vs.x == vt.z) |
+                               (vs.y == vt.x) | (vs.y == vt.y) | (vs.y == vt.z) |
+                               (vs.z == vt.x) | (vs.z == vt.y) | (vs.z == vt.z);
+            if (touch) continue;
+            const float4 ns = shN[s];
+            const float xny = xp.x * ns.x + xp.y * ns.y + xp.z * ns.z - ns.w;
+            const float nxny = nxx * ns.x + nxy * ns.y + nxz * ns.z;
+            float t1r = 0.f, t1i = 0.f, ur = 0.f, ui = 0.f, t3r = 0.f, t3i = 0.f;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const float4 A = shA[6 * s + q];
+                const float4 B = shB[6 * s + q];
+                const float dx = xp.x - A.x, dy = xp.y - A.y, dz = xp.z - A.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                const float ri = rsqrtf(r2);
+                const float r = r2 * ri;
+                const float ri3 = ri * ri * ri;
+                const float dnx = dx * nxx + dy * nxy + dz * nxz;
+                // e^{i k r}: reduce k r / (2 pi) to [-1/2, 1/2] revolutions first
+                float s0, c0, s1, c1;
+                {
+                    const float t = r * c.k0r;
+                    __sincosf(6.28318530717958647692f * (t - rintf(t)), &s0, &c0);
+                }
+                {
+                    const float t = r * c.k1r;
+                    __sincosf(6.28318530717958647692f * (t - rintf(t)), &s1, &c1);
+                }
+                const float kr0 = c.k0 * r, kr1 = c.k1 * r;
+                const float g0r = c0 * ri, g0i = s0 * ri;
+                const float g1r = c1 * ri, g1i = s1 * ri;
+                const float hsr = (-c0 - kr0 * s0 - c1 - kr1 * s1) * ri3;
+                const float hsi = (kr0 * c0 - s0 + kr1 * c1 - s1) * ri3;
+                const float gpr = g0r + c.rho * g1r, gpi = g0i + c.rho * g1i;
+                const float gdr = g0r + c.irho * g1r, gdi = g0i + c.irho * g1i;
+                const float gkr = c.dk0 * g0r + c.dk1 * g1r, gki = c.dk0 * g0i + c.dk1 * g1i;
+                const float psr = A.w, psi = B.x, phr = B.y, phi = B.z;
+                u1r += gpr * psr - gpi * psi;
+                u1i += gpr * psi + gpi * psr;
+                t1r += hsr * phr - hsi * phi;
+                t1i += hsr * phi + hsi * phr;
+                const float hxr = hsr * dnx, hxi = hsi * dnx;
+                u2r += hxr * psr - hxi * psi;
+                u2i += hxr * psi + hxi * psr;
+                ur += gkr * phr - gki * phi;
+                ui += gkr * phi + gki * phr;
+                const float wq = q < 3 ? W1 : W2;
+                t3r += gdr * wq;
+                t3i += gdi * wq;
+            }
+            u1r += xny * t1r;
+            u1i += xny * t1i;
+            u2r -= nxny * ur;
+            u2i -= nxny * ui;
+            const float4 C = shC[s];
+            const float2 C2 = shC2[s];
+            axr += t3r * C.x - t3i * C.y;
+            axi += t3r * C.y + t3i * C.x;
+            ayr += t3r * C.z - t3i * C.w;
+            ayi += t3r * C.w + t3i * C.z;
+            azr += t3r * C2.x - t3i * C2.y;
+            azi += t3r * C2.y + t3i * C2.x;
+        }
+        kahan_add(acc[0], cmp[0], u1r);
+        kahan_add(acc[1], cmp[1], u1i);
+        kahan_add(acc[2], cmp[2], u2r);
+        kahan_add(acc[3], cmp[3], u2i);
+        kahan_add(acc[4], cmp[4], axr);
+        kahan_add(acc[5], cmp[5], axi);
+        kahan_add(acc[6], cmp[6], ayr);
+        kahan_add(acc[7], cmp[7], ayi);
+        kahan_add(acc[8], cmp[8], azr);
+        kahan_add(acc[9], cmp[9], azi);
+    }
+    if (active) {
+#pragma unroll
+        for (int i = 0; i < 10; ++i) part[((size_t)split * 10 + i) * npts + p] = acc[i];
+    }
+}
+
+// Per vertex v: y1_v = (1/4pi) sum_{(t,a) incident} |t| sum_q w_q lambda_a(q) u1(t,q)
+//               y2_v = (1/4pi) sum |t| [sum_q w_q lambda_a(q) u2(t,q) + curl_a . sum_q w_q A(t,q)]
+// plus the near-field CSR rows (2x2 complex blocks) applied to x.
+__global__ void gather_kernel(int nv, int npts, int nsplit, const int *__restrict__ vt_ptr,
+                              const int *__restrict__ vt_idx, const double *__restrict__ tgeo,
+                              const float *__restrict__ part, int use_far,
+                              const int *__restrict__ nr_ptr, const int *__restrict__ nr_col,
+                              const double2 *__restrict__ nr_val, int use_near,
+                              const double2 *__restrict__ x, double2 *__restrict__ y) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    double2 y1 = cd(0, 0), y2 = cd(0, 0);
+    if (use_far) {
+        for (int e = vt_ptr[v]; e < vt_ptr[v + 1]; ++e) {
+            const int t = vt_idx[e] / 3, a = vt_idx[e] % 3;
+            const double *g = tgeo + 16 * (size_t)t;
+            double2 s1 = cd(0, 0), s2 = cd(0, 0), ax = cd(0, 0), ay = cd(0, 0), az = cd(0, 0);
+            for (int q = 0; q < 6; ++q) {
+                double b[3], w;
+                rule_point(q, b, w);
+                const double wl = w * b[a];
+                const size_t p = 6 * (size_t)t + q;
+                for (int sp = 0; sp < nsplit; ++sp) {
+                    const float *P = part + (size_t)sp * 10 * npts + p;
+                    s1 = cadd(s1, cd(wl * P[0], wl * P[(size_t)npts]));
+                    s2 = cadd(s2, cd(wl * P[2 * (size_t)npts], wl * P[3 * (size_t)npts]));
+                    ax = cadd(ax, cd(w * P[4 * (size_t)npts], w * P[5 * (size_t)npts]));
+                    ay = cadd(ay, cd(w * P[6 * (size_t)npts], w * P[7 * (size_t)npts]));
+                    az = cadd(az, cd(w * P[8 * (size_t)npts], w * P[9 * (size_t)npts]));
+                }
+            }
+            const double *cu = g + 4 + 3 * a;
+            s2 = cadd(s2, cadd(cadd(cscale(ax, cu[0]), cscale(ay, cu[1])), cscale(az, cu[2])));
+            y1 = cadd(y1, cscale(s1, g[0]));
+            y2 = cadd(y2, cscale(s2, g[0]));
+        }
+        const double inv4pi = 0.079577471545947667884;
+        y1 = cscale(y1, inv4pi);
+        y2 = cscale(y2, inv4pi);
+    }
+    if (use_near) {
+        for (int e = nr_ptr[v]; e < nr_ptr[v + 1]; ++e) {
+            const int j = nr_col[e];
+            const double2 xa = x[j], xb = x[nv + j];
+            const double2 *B = nr_val + 4 * (size_t)e;
+            y1 = cadd(y1, cadd(cmul(B[0], xa), cmul(B[1], xb)));
+            y2 = cadd(y2, cadd(cmul(B[2], xa), cmul(B[3], xb)));
+        }
+    }
+    y[v] = y1;
+    y[nv + v] = y2;
+}
+
+}  // namespace
+
+int far_setup_geometry(osrc_problem *pb, cudaStream_t st) {
+    osrc_mesh *m = pb->mesh;
+    const int nt = pb->nt;
+    OSRC_TRY(pb->d_pt.alloc(m->ctx, 6 * (size_t)nt));
+    OSRC_TRY(pb->d_tn.alloc(m->ctx, nt));
+    OSRC_TRY(pb->d_tv.alloc(m->ctx, nt));
+    OSRC_TRY(pb->d_tgeo.alloc(m->ctx, 16 * (size_t)nt));
+    OSRC_TRY(pb->d_sA.alloc(m->ctx, 6 * (size_t)nt));
+    OSRC_TRY(pb->d_sB.alloc(m->ctx, 6 * (size_t)nt));
+    OSRC_TRY(pb->d_sC.alloc(m->ctx, nt));
+    OSRC_TRY(pb->d_sC2.alloc(m->ctx, nt));
+    far_geom_kernel<<<(nt + 127) / 128, 128, 0, st>>>(m->d_verts.p, m->d_tris.p, nt, pb->d_pt.p,
+                                                      pb->d_tn.p, pb->d_tv.p, pb->d_tgeo.p);
+    pb->launches++;
+    OSRC_CK(cudaGetLastError());
+    // split the source range so that the grid covers the GPU several times
+    int dev = m->ctx->device, sms = 0, per_sm = 0;
+    OSRC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    OSRC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far_kernel, FAR_THREADS, 0));
+    if (per_sm < 1) per_sm = 1;
+    const int bx = (pb->npts + FAR_THREADS - 1) / FAR_THREADS;
+    const int slots = sms * per_sm;
+    int ns = (4 * slots + bx - 1) / bx;
+    const int max_ns = (nt + FAR_TS - 1) / FAR_TS;
+    if (ns > max_ns) ns = max_ns;
+    if (ns < 1) ns = 1;
+    pb->nsplit = ns;
+    OSRC_TRY(pb->d_part.alloc(m->ctx, (size_t)ns * 10 * pb->npts));
+    return OSRC_OK;
+}
+
+int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStream_t st) {
+    osrc_mesh *m = pb->mesh;
+    const int nt = pb->nt, nv = pb->nv, npts = pb->npts;
+    const int use_far = (part & OSRC_PART_FAR) ? 1 : 0;
+    const int use_near = (part & OSRC_PART_NEAR) ? 1 : 0;
+    if (use_far) {
+        far_prep_kernel<<<(nt + 127) / 128, 128, 0, st>>>(x, nv, nt, m->d_tris.p, pb->d_pt.p,
+                                                          pb->d_tgeo.p, pb->d_sA.p, pb->d_sB.p,
+                                                          pb->d_sC.p, pb->d_sC2.p);
+        pb->launches++;
+        FarConst c;
+        const double k0 = pb->p.k_ext, k1 = pb->p.k_int, rho = pb->p.rho_ratio;
+        const double inv2pi = 0.15915494309189533577;
+        c.k0 = (float)k0;
+        c.k1 = (float)k1;
+        c.k0r = (float)(k0 * inv2pi);
+        c.k1r = (float)(k1 * inv2pi);
+        c.rho = (float)rho;
+        c.irho = (float)(1.0 / rho);
+        c.dk0 = (float)(k0 * k0);
+        c.dk1 = (float)(k1 * k1 / rho);
+        const int ns = pb->nsplit;
+        const int tps = (nt + ns - 1) / ns;
+        dim3 grid((npts + FAR_THREADS - 1) / FAR_THREADS, ns);
+        far_kernel<<<grid, FAR_THREADS, 0, st>>>(pb->d_pt.p, pb->d_tn.p, pb->d_tv.p, pb->d_sA.p,
+                                                 pb->d_sB.p, pb->d_sC.p, pb->d_sC2.p, nt, npts,
+                                                 tps, c, pb->d_part.p);
+        pb->launches++;
+    }
+    gather_kernel<<<(nv + 127) / 128, 128, 0, st>>>(
+        nv, npts, pb->nsplit, m->d_vt_ptr.p, m->d_vt_idx.p, pb->d_tgeo.p, pb->d_part.p, use_far,
+        pb->d_nr_ptr.p, pb->d_nr_col.p, pb->d_nr_val.p, use_near, x, y);
+    pb->launches++;
+    OSRC_CK(cudaGetLastError());
+    return OSRC_OK;
+}

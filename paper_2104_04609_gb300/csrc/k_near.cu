@@ -1,0 +1,462 @@
+// k_near.cu -- near-field (touching triangle pairs) in FP64 by Sauter-Schwab
+// quadrature, assembled on the device into a vertex-pair CSR of 2x2 complex
+// blocks of the permuted PMCHWT operator (Sec. 2.7); and the dense FP64
+// system of the assembled path.
+//
+// Sauter-Schwab (Sauter & Schwab, Boundary Element Methods, Sec. 5.2): the
+// reference triangle is That = {0 <= x2 <= x1 <= 1}, mapped to a flat
+// triangle (P0, P1, P2) by P0 + x1 (P1 - P0) + x2 (P2 - P1), so that the hat
+// functions are (1 - x1, x1 - x2, x2).  Touching pairs are re-ordered so that
+// the shared vertices come first in both triangles; then the singular set is
+// the origin (common vertex), the edge x2 = 0 (common edge) or the diagonal
+// (identical triangles).  Each case splits [0,1]^4 into 2, 5 or 6 regions
+// whose Jacobians (xi^3 eta2, xi^3 eta1^2 [eta2], xi^3 eta1^2 eta2) cancel the
+// 1/r and 1/r^2 singularities, leaving integrands that tensor Gauss-Legendre
+// rules integrate with exponential convergence.
+#include "osrc_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ int ss_nmaps(int kase) { return kase == 3 ? 6 : (kase == 2 ? 5 : 2); }
+
+// Map m of case kase: (xi, e1, e2, e3) -> (xh, yh) with Jacobian jac.
+__device__ __forceinline__ void ss_map(int kase, int m, double xi, double e1, double e2, double e3,
+                                       double xh[2], double yh[2], double &jac) {
+    if (kase == 3) {
+        jac = xi * xi * xi * e1 * e1 * e2;
+        double ax, ay, bx, by;  // first point, second point
+        double cx, cy, dx, dy;
+        const int pm = m >> 1;
+        if (pm == 0) {
+            ax = xi;                          ay = xi * (1.0 - e1 + e1 * e2);
+            bx = xi * (1.0 - e1 * e2 * e3);   by = xi * (1.0 - e1);
+        } else if (pm == 1) {
+            ax = xi;                          ay = xi * e1 * (1.0 - e2 + e2 * e3);
+            bx = xi * (1.0 - e1 * e2);        by = xi * e1 * (1.0 - e2);
+        } else {
+            ax = xi * (1.0 - e1 * e2 * e3);   ay = xi * e1 * (1.0 - e2 * e3);
+            bx = xi;                          by = xi * e1 * (1.0 - e2);
+        }
+        if (m & 1) { cx = bx; cy = by; dx = ax; dy = ay; }
+        else       { cx = ax; cy = ay; dx = bx; dy = by; }
+        xh[0] = cx; xh[1] = cy; yh[0] = dx; yh[1] = dy;
+        return;
+    }
+    if (kase == 2) {
+        const double J1 = xi * xi * xi * e1 * e1;
+        switch (m) {
+            case 0:
+                xh[0] = xi;                        xh[1] = xi * e1 * e3;
+                yh[0] = xi * (1.0 - e1 * e2);      yh[1] = xi * e1 * (1.0 - e2);
+                jac = J1; return;
+            case 1:
+                xh[0] = xi;                        xh[1] = xi * e1;
+                yh[0] = xi * (1.0 - e1 * e2 * e3); yh[1] = xi * e1 * e2 * (1.0 - e3);
+                jac = J1 * e2; return;
+            case 2:
+                xh[0] = xi * (1.0 - e1 * e2);      xh[1] = xi * e1 * (1.0 - e2);
+                yh[0] = xi;                        yh[1] = xi * e1 * e2 * e3;
+                jac = J1 * e2; return;
+            case 3:
+                xh[0] = xi * (1.0 - e1 * e2 * e3); xh[1] = xi * e1 * e2 * (1.0 - e3);
+                yh[0] = xi;                        yh[1] = xi * e1;
+                jac = J1 * e2; return;
+            default:
+                xh[0] = xi * (1.0 - e1 * e2 * e3); xh[1] = xi * e1 * (1.0 - e2 * e3);
+                yh[0] = xi;                        yh[1] = xi * e1 * e2;
+                jac = J1 * e2; return;
+        }
+    }
+    jac = xi * xi * xi * e2;
+    if (m == 0) {
+        xh[0] = xi;       xh[1] = xi * e1;
+        yh[0] = xi * e2;  yh[1] = xi * e2 * e3;
+    } else {
+        xh[0] = xi * e2;  xh[1] = xi * e2 * e3;
+        yh[0] = xi;       yh[1] = xi * e1;
+    }
+}
+
+struct NearConst {
+    double k0, k1, rho;
+    int nss;
+};
+
+constexpr int NEAR_WARPS = 4;
+constexpr double kInv4Pi = 0.079577471545947667884;
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One warp per touching pair.  out[pair][36]: blocks (V0 + rho V1),
+// -(K0 + K1), (T0 + T1), (D0 + D1/rho), each 3x3 in the original local
+// vertex order of (test, source) triangle.
+__global__ void __launch_bounds__(32 * NEAR_WARPS)
+near_ss_kernel(const NearPair *__restrict__ pairs, long long npairs,
+               const double *__restrict__ verts, const int *__restrict__ tris,
+               const double *__restrict__ tgeo, const double *__restrict__ gl,
+               NearConst c, double2 *__restrict__ out) {
+    __shared__ double sx[16], sw[16];
+    if (threadIdx.x < c.nss) {
+        sx[threadIdx.x] = gl[threadIdx.x];
+        sw[threadIdx.x] = gl[16 + threadIdx.x];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const long long pi = (long long)blockIdx.x * NEAR_WARPS + (threadIdx.x >> 5);
+    if (pi >= npairs) return;
+    const NearPair pr = pairs[pi];
+    int pt[3], ps[3];
+    for (int a = 0; a < 3; ++a) {
+        pt[a] = (pr.perm >> (2 * a)) & 3;
+        ps[a] = (pr.perm >> (6 + 2 * a)) & 3;
+    }
+    double Pt[3][3], Ps[3][3];
+    for (int a = 0; a < 3; ++a) {
+        const int vt = tris[3 * pr.t + pt[a]], vs = tris[3 * pr.s + ps[a]];
+        for (int j = 0; j < 3; ++j) {
+            Pt[a][j] = verts[3 * vt + j];
+            Ps[a][j] = verts[3 * vs + j];
+        }
+    }
+    const double *gt = tgeo + 16 * (size_t)pr.t, *gs = tgeo + 16 * (size_t)pr.s;
+    const double nt0 = gt[1], nt1 = gt[2], nt2 = gt[3];
+    const double ns0 = gs[1], ns1 = gs[2], ns2 = gs[3];
+    const double nn = nt0 * ns0 + nt1 * ns1 + nt2 * ns2;
+    const double scale = 4.0 * gt[0] * gs[0];
+    const int n = c.nss, n2 = n * n, n4 = n2 * n2;
+    const int total = ss_nmaps(pr.kase) * n4;
+
+    double vr[9], vi[9], kr_[9], ki_[9], tr_[9], ti_[9], dr[9], di[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) vr[i] = vi[i] = kr_[i] = ki_[i] = tr_[i] = ti_[i] = dr[i] = di[i] = 0.0;
+    double dcr = 0.0, dci = 0.0;
+
+    for (int idx = lane; idx < total; idx += 32) {
+        const int m = idx / n4;
+        int rem = idx - m * n4;
+        const int i0 = rem / (n2 * n);
+        rem -= i0 * n2 * n;
+        const int i1 = rem / n2;
+        rem -= i1 * n2;
+        const int i2 = rem / n, i3 = rem - (rem / n) * n;
+        double xh[2], yh[2], jac;
+        ss_map(pr.kase, m, sx[i0], sx[i1], sx[i2], sx[i3], xh, yh, jac);
+        const double w = sw[i0] * sw[i1] * sw[i2] * sw[i3] * jac * scale;
+        double x[3], y[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            x[j] = Pt[0][j] + xh[0] * (Pt[1][j] - Pt[0][j]) + xh[1] * (Pt[2][j] - Pt[1][j]);
+            y[j] = Ps[0][j] + yh[0] * (Ps[1][j] - Ps[0][j]) + yh[1] * (Ps[2][j] - Ps[1][j]);
+        }
+        const double la[3] = {1.0 - xh[0], xh[0] - xh[1], xh[1]};
+        const double lb[3] = {1.0 - yh[0], yh[0] - yh[1], yh[1]};
+        const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+        const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+        const double r = sqrt(r2);
+        const double ri = 1.0 / r;
+        double s0, c0, s1, c1;
+        sincos(c.k0 * r, &s0, &c0);
+        sincos(c.k1 * r, &s1, &c1);
+        const double kr0 = c.k0 * r, kr1 = c.k1 * r;
+        const double f = kInv4Pi * ri, f3 = f * ri * ri;
+        const double g0r = c0 * f, g0i = s0 * f, g1r = c1 * f, g1i = s1 * f;
+        const double hsr = (-c0 - kr0 * s0 - c1 - kr1 * s1) * f3;
+        const double hsi = (kr0 * c0 - s0 + kr1 * c1 - s1) * f3;
+        const double gpr = g0r + c.rho * g1r, gpi = g0i + c.rho * g1i;
+        const double gdr = g0r + g1r / c.rho, gdi = g0i + g1i / c.rho;
+        const double dk0 = c.k0 * c.k0, dk1 = c.k1 * c.k1 / c.rho;
+        const double gkr = dk0 * g0r + dk1 * g1r, gki = dk0 * g0i + dk1 * g1i;
+        const double dny = -(d0 * ns0 + d1 * ns1 + d2 * ns2);  // (y - x).n_y
+        const double dnx = d0 * nt0 + d1 * nt1 + d2 * nt2;     // (x - y).n_x
+        dcr += gdr * w;
+        dci += gdi * w;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double wa = la[a] * w;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const double ll = wa * lb[b];
+                const int i = 3 * a + b;
+                vr[i] += gpr * ll;
+                vi[i] += gpi * ll;
+                kr_[i] -= hsr * dny * ll;
+                ki_[i] -= hsi * dny * ll;
+                tr_[i] += hsr * dnx * ll;
+                ti_[i] += hsi * dnx * ll;
+                dr[i] += gkr * ll;
+                di[i] += gki * ll;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        vr[i] = warp_sum(vr[i]);
+        vi[i] = warp_sum(vi[i]);
+        kr_[i] = warp_sum(kr_[i]);
+        ki_[i] = warp_sum(ki_[i]);
+        tr_[i] = warp_sum(tr_[i]);
+        ti_[i] = warp_sum(ti_[i]);
+        dr[i] = warp_sum(dr[i]);
+        di[i] = warp_sum(di[i]);
+    }
+    dcr = warp_sum(dcr);
+    dci = warp_sum(dci);
+    if (lane == 0) {
+        double2 *o = out + 36 * (size_t)pi;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const int A = pt[a], B = ps[b], i = 3 * a + b, j = 3 * A + B;
+                const double *ca = gt + 4 + 3 * A, *cb = gs + 4 + 3 * B;
+                const double cc = ca[0] * cb[0] + ca[1] * cb[1] + ca[2] * cb[2];
+                o[j] = cd(vr[i], vi[i]);
+                o[9 + j] = cd(kr_[i], ki_[i]);
+                o[18 + j] = cd(tr_[i], ti_[i]);
+                o[27 + j] = cd(dcr * cc - nn * dr[i], dci * cc - nn * di[i]);
+            }
+    }
+}
+
+// CSR value of entry e = sum of its contributions (pair * 9 + 3 A + B).
+__global__ void near_csr_kernel(int nnz, const int *__restrict__ cptr, const int *__restrict__ cidx,
+                                const double2 *__restrict__ buf, double2 *__restrict__ val) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    double2 s[4] = {cd(0, 0), cd(0, 0), cd(0, 0), cd(0, 0)};
+    for (int k = cptr[e]; k < cptr[e + 1]; ++k) {
+        const long long c = cidx[k];
+        const long long pair = c / 9, ab = c % 9;
+        const double2 *b = buf + 36 * pair + ab;
+        for (int o = 0; o < 4; ++o) s[o] = cadd(s[o], b[9 * o]);
+    }
+    for (int o = 0; o < 4; ++o) val[4 * (size_t)e + o] = s[o];
+}
+
+// ---------------------------------------------------------------------------
+// dense FP64 system (assembled path): far pairs with the 6-point rule, one
+// thread per (test triangle, source triangle), accumulated with FP64 atomics.
+// ---------------------------------------------------------------------------
+constexpr double kDa1 = 0.445948490915965, kDw1 = 0.223381589678011;
+constexpr double kDa2 = 0.091576213509771, kDw2 = 0.109951743655322;
+
+__device__ inline void dense_rule(int q, double b[3], double &w) {
+    const double a = q < 3 ? kDa1 : kDa2;
+    w = q < 3 ? kDw1 : kDw2;
+    for (int j = 0; j < 3; ++j) b[j] = (j == q % 3) ? 1.0 - 2.0 * a : a;
+}
+
+__global__ void dense_far_kernel(int nv, int nt, const double *__restrict__ verts,
+                                 const int *__restrict__ tris, const double *__restrict__ tgeo,
+                                 NearConst c, double2 *__restrict__ A) {
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (long long)nt * nt) return;
+    const int t = (int)(id / nt), s = (int)(id % nt);
+    int vt[3], vs[3];
+    for (int a = 0; a < 3; ++a) {
+        vt[a] = tris[3 * t + a];
+        vs[a] = tris[3 * s + a];
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            if (vt[a] == vs[b]) return;  // touching: near field
+    const double *gt = tgeo + 16 * (size_t)t, *gs = tgeo + 16 * (size_t)s;
+    double X[6][3], Y[6][3], bx[6][3], wq[6];
+    for (int q = 0; q < 6; ++q) {
+        dense_rule(q, bx[q], wq[q]);
+        for (int j = 0; j < 3; ++j) {
+            X[q][j] = bx[q][0] * verts[3 * vt[0] + j] + bx[q][1] * verts[3 * vt[1] + j] +
+                      bx[q][2] * verts[3 * vt[2] + j];
+            Y[q][j] = bx[q][0] * verts[3 * vs[0] + j] + bx[q][1] * verts[3 * vs[1] + j] +
+                      bx[q][2] * verts[3 * vs[2] + j];
+        }
+    }
+    const double nn = gt[1] * gs[1] + gt[2] * gs[2] + gt[3] * gs[3];
+    const double scale = gt[0] * gs[0];
+    double2 V[9], K[9], T[9], D[9];
+    for (int i = 0; i < 9; ++i) V[i] = K[i] = T[i] = D[i] = cd(0, 0);
+    double2 dc = cd(0, 0);
+    const double dk0 = c.k0 * c.k0, dk1 = c.k1 * c.k1 / c.rho;
+    for (int p = 0; p < 6; ++p)
+        for (int q = 0; q < 6; ++q) {
+            const double w = wq[p] * wq[q] * scale;
+            const double d0 = X[p][0] - Y[q][0], d1 = X[p][1] - Y[q][1], d2 = X[p][2] - Y[q][2];
+            const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2), ri = 1.0 / r;
+            double s0, c0, s1, c1;
+            sincos(c.k0 * r, &s0, &c0);
+            sincos(c.k1 * r, &s1, &c1);
+            const double kr0 = c.k0 * r, kr1 = c.k1 * r;
+            const double f = kInv4Pi * ri, f3 = f * ri * ri;
+            const double2 g0 = cd(c0 * f, s0 * f), g1 = cd(c1 * f, s1 * f);
+            const double2 hs = cd((-c0 - kr0 * s0 - c1 - kr1 * s1) * f3,
+                                  (kr0 * c0 - s0 + kr1 * c1 - s1) * f3);
+            const double2 gp = cadd(g0, cscale(g1, c.rho));
+            const double2 gd = cadd(g0, cscale(g1, 1.0 / c.rho));
+            const double2 gk = cadd(cscale(g0, dk0), cscale(g1, dk1));
+            const double dny = -(d0 * gs[1] + d1 * gs[2] + d2 * gs[3]);
+            const double dnx = d0 * gt[1] + d1 * gt[2] + d2 * gt[3];
+            dc = cadd(dc, cscale(gd, w));
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    const double ll = bx[p][a] * bx[q][b] * w;
+                    const int i = 3 * a + b;
+                    V[i] = cadd(V[i], cscale(gp, ll));
+                    K[i] = csub(K[i], cscale(hs, dny * ll));
+                    T[i] = cadd(T[i], cscale(hs, dnx * ll));
+                    D[i] = cadd(D[i], cscale(gk, ll));
+                }
+        }
+    const size_t n2 = 2 * (size_t)nv;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const int i = 3 * a + b;
+            const double *ca = gt + 4 + 3 * a, *cb = gs + 4 + 3 * b;
+            const double cc = ca[0] * cb[0] + ca[1] * cb[1] + ca[2] * cb[2];
+            const double2 dd = csub(cscale(dc, cc), cscale(D[i], nn));
+            const size_t r1 = vt[a], r2 = nv + vt[a], c1 = vs[b], c2 = nv + vs[b];
+            double *p;
+            p = (double *)&A[r1 * n2 + c1]; atomicAdd(p, V[i].x); atomicAdd(p + 1, V[i].y);
+            p = (double *)&A[r1 * n2 + c2]; atomicAdd(p, K[i].x); atomicAdd(p + 1, K[i].y);
+            p = (double *)&A[r2 * n2 + c1]; atomicAdd(p, T[i].x); atomicAdd(p + 1, T[i].y);
+            p = (double *)&A[r2 * n2 + c2]; atomicAdd(p, dd.x); atomicAdd(p + 1, dd.y);
+        }
+}
+
+// Adds the near CSR blocks into the dense matrix (one thread per vertex row).
+__global__ void dense_add_near_kernel(int nv, const int *__restrict__ ptr, const int *__restrict__ col,
+                                      const double2 *__restrict__ val, double2 *__restrict__ A) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const size_t n2 = 2 * (size_t)nv;
+    for (int e = ptr[v]; e < ptr[v + 1]; ++e) {
+        const int j = col[e];
+        const double2 *B = val + 4 * (size_t)e;
+        A[(size_t)v * n2 + j] = cadd(A[(size_t)v * n2 + j], B[0]);
+        A[(size_t)v * n2 + nv + j] = cadd(A[(size_t)v * n2 + nv + j], B[1]);
+        A[(size_t)(nv + v) * n2 + j] = cadd(A[(size_t)(nv + v) * n2 + j], B[2]);
+        A[(size_t)(nv + v) * n2 + nv + j] = cadd(A[(size_t)(nv + v) * n2 + nv + j], B[3]);
+    }
+}
+
+// y = A x, one warp per row, coalesced row reads.
+__global__ void dense_gemv_kernel(int n, const double2 *__restrict__ A, const double2 *__restrict__ x,
+                                  double2 *__restrict__ y) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const double2 *a = A + (size_t)row * n;
+    double sr = 0.0, si = 0.0;
+    for (int j = lane; j < n; j += 32) {
+        const double2 u = a[j], v = x[j];
+        sr += u.x * v.x - u.y * v.y;
+        si += u.x * v.y + u.y * v.x;
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) y[row] = cd(sr, si);
+}
+
+// Gauss-Legendre nodes and weights on [0,1] (Newton on the three-term
+// recurrence of the Legendre polynomials).
+void gauss_legendre01(int n, double *x, double *w) {
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < n; ++i) {
+        double z = cos(pi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double pm = 1.0, pc = z;
+            for (int j = 2; j <= n; ++j) {
+                const double pn = ((2.0 * j - 1.0) * z * pc - (j - 1.0) * pm) / j;
+                pm = pc;
+                pc = pn;
+            }
+            if (n == 1) { pc = z; pm = 1.0; }
+            dp = n * (z * pc - pm) / (z * z - 1.0);
+            const double dz = pc / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        double pm = 1.0, pc = z;
+        for (int j = 2; j <= n; ++j) {
+            const double pn = ((2.0 * j - 1.0) * z * pc - (j - 1.0) * pm) / j;
+            pm = pc;
+            pc = pn;
+        }
+        if (n == 1) { pc = z; pm = 1.0; }
+        dp = n * (z * pc - pm) / (z * z - 1.0);
+        x[i] = 0.5 * (1.0 - z);
+        w[i] = 1.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+}  // namespace
+
+int near_build(osrc_problem *pb, const std::vector<NearPair> &pairs,
+               const std::vector<int> &cptr, const std::vector<int> &cidx, cudaStream_t st) {
+    osrc_mesh *m = pb->mesh;
+    osrc_ctx *ctx = m->ctx;
+    const long long np = (long long)pairs.size();
+    pb->near_pairs = np;
+    const int nnz = pb->near_nnz;
+    DBuf<NearPair> d_pairs;
+    DBuf<double2> d_buf;
+    DBuf<int> d_cptr, d_cidx;
+    DBuf<double> d_gl;
+    OSRC_TRY(d_pairs.alloc(ctx, np));
+    OSRC_TRY(d_buf.alloc(ctx, 36 * (size_t)np));
+    OSRC_TRY(d_cptr.alloc(ctx, cptr.size()));
+    OSRC_TRY(d_cidx.alloc(ctx, cidx.size()));
+    OSRC_TRY(d_gl.alloc(ctx, 32));
+    OSRC_TRY(pb->d_nr_val.alloc(ctx, 4 * (size_t)nnz));
+    double gl[32] = {0};
+    gauss_legendre01(pb->p.n_ss, gl, gl + 16);
+    OSRC_CK(cudaMemcpyAsync(d_pairs.p, pairs.data(), np * sizeof(NearPair), cudaMemcpyHostToDevice, st));
+    OSRC_CK(cudaMemcpyAsync(d_cptr.p, cptr.data(), cptr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    OSRC_CK(cudaMemcpyAsync(d_cidx.p, cidx.data(), cidx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    OSRC_CK(cudaMemcpyAsync(d_gl.p, gl, sizeof(gl), cudaMemcpyHostToDevice, st));
+    NearConst c{pb->p.k_ext, pb->p.k_int, pb->p.rho_ratio, pb->p.n_ss};
+    const long long blocks = (np + NEAR_WARPS - 1) / NEAR_WARPS;
+    if (blocks > 0) {
+        near_ss_kernel<<<(unsigned)blocks, 32 * NEAR_WARPS, 0, st>>>(
+            d_pairs.p, np, m->d_verts.p, m->d_tris.p, pb->d_tgeo.p, d_gl.p, c, d_buf.p);
+        pb->launches++;
+        OSRC_CK(cudaGetLastError());
+    }
+    if (nnz > 0) {
+        near_csr_kernel<<<(nnz + 255) / 256, 256, 0, st>>>(nnz, d_cptr.p, d_cidx.p, d_buf.p,
+                                                           pb->d_nr_val.p);
+        pb->launches++;
+        OSRC_CK(cudaGetLastError());
+    }
+    // the temporaries are released when this function returns: finish first
+    OSRC_CK(cudaStreamSynchronize(st));
+    return OSRC_OK;
+}
+
+int dense_assemble(osrc_problem *pb, cudaStream_t st) {
+    osrc_mesh *m = pb->mesh;
+    const int nv = pb->nv, nt = pb->nt;
+    const size_t n2 = 2 * (size_t)nv;
+    OSRC_TRY(pb->d_dense.alloc(m->ctx, n2 * n2));
+    OSRC_CK(cudaMemsetAsync(pb->d_dense.p, 0, n2 * n2 * sizeof(double2), st));
+    NearConst c{pb->p.k_ext, pb->p.k_int, pb->p.rho_ratio, pb->p.n_ss};
+    const long long npair = (long long)nt * nt;
+    dense_far_kernel<<<(unsigned)((npair + 127) / 128), 128, 0, st>>>(
+        nv, nt, m->d_verts.p, m->d_tris.p, pb->d_tgeo.p, c, pb->d_dense.p);
+    pb->launches++;
+    dense_add_near_kernel<<<(nv + 127) / 128, 128, 0, st>>>(nv, pb->d_nr_ptr.p, pb->d_nr_col.p,
+                                                            pb->d_nr_val.p, pb->d_dense.p);
+    pb->launches++;
+    OSRC_CK(cudaGetLastError());
+    return OSRC_OK;
+}
+
+int dense_apply(osrc_problem *pb, const double2 *x, double2 *y, cudaStream_t st) {
+    const int n = 2 * pb->nv;
+    dense_gemv_kernel<<<(n + 7) / 8, 256, 0, st>>>(n, pb->d_dense.p, x, y);
+    pb->launches++;
+    OSRC_CK(cudaGetLastError());
+    return OSRC_OK;
+}

@@ -1,0 +1,389 @@
+// k_sparse.cu -- P1 mass M and Laplace-Beltrami stiffness S (CSR, FP64), the
+// mass preconditioner M^-1 (Sec. 2.4) and the OSRC preconditioner (Sec. 2.6,
+// 2.7) by batched Krylov solves.
+//
+// Every inner system has the form (alpha M + beta S) w = f on the shared
+// vertex-graph pattern.  One thread-block cluster (up to 8 CTAs) solves one
+// system: each CTA owns a contiguous block of rows, the SpMV reads the search
+// direction of the other CTAs from global memory after a cluster barrier,
+// and dot products are reduced over the cluster through distributed shared
+// memory, so a solve needs no host round trip and no grid-wide barrier.
+// Rows owned by other CTAs are read with L2-only loads (__ldcg) after the
+// cluster barrier, so no stale L1 line of an earlier iteration is used.
+// Systems with real SPD matrices (M) use Hermitian CG; the complex-symmetric
+// shifted OSRC systems use COCG (conjugate orthogonal CG, van der Vorst &
+// Melissen 1990) with the unconjugated bilinear form x^T y.  Both are
+// Jacobi-preconditioned and stop at |r| <= tol |f|.  All loops are bounded by
+// the iteration cap; every CTA of a cluster takes the same branch because
+// the decisions are made from cluster-reduced values summed in rank order.
+#include <cooperative_groups.h>
+
+#include "osrc_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+__global__ void ms_element_kernel(int nt, const double *__restrict__ tgeo,
+                                  const double *__restrict__ verts, const int *__restrict__ tris,
+                                  double *__restrict__ bm, double *__restrict__ bs) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const double *g = tgeo + 16 * (size_t)t;
+    const double area = g[0];
+    // grad phi_a = curl phi_a x n has the same length, and grad.grad = curl.curl
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const double *ca = g + 4 + 3 * a, *cb = g + 4 + 3 * b;
+            bm[9 * (size_t)t + 3 * a + b] = area / 12.0 * (a == b ? 2.0 : 1.0);
+            bs[9 * (size_t)t + 3 * a + b] = area * (ca[0] * cb[0] + ca[1] * cb[1] + ca[2] * cb[2]);
+        }
+}
+
+__global__ void csr_sum_kernel(int nnz, const int *__restrict__ cptr, const int *__restrict__ cidx,
+                               const double *__restrict__ bm, const double *__restrict__ bs,
+                               double *__restrict__ M, double *__restrict__ S) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    double m = 0.0, s = 0.0;
+    for (int k = cptr[e]; k < cptr[e + 1]; ++k) {
+        m += bm[cidx[k]];
+        s += bs[cidx[k]];
+    }
+    M[e] = m;
+    S[e] = s;
+}
+
+constexpr int KRY_THREADS = 256;
+constexpr int KRY_MAX_SYS = 40;
+
+struct KrySys {
+    double2 alpha, beta;  // system matrix alpha M + beta S
+    const double2 *f;     // right-hand side
+    double2 *x;           // solution
+    int conj;             // 1: Hermitian CG, 0: COCG
+};
+
+struct KryBatch {
+    int nsys;
+    KrySys s[KRY_MAX_SYS];
+};
+
+__device__ __forceinline__ double2 dot_term(double2 a, double2 b, int conj) {
+    // conj: conj(a) b, else a b
+    return conj ? cd(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x) : cmul(a, b);
+}
+
+// Sum of three doubles over the block; result valid in every thread.
+__device__ void block_sum3(double v[3], double *red /* [3][32] */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k < 3; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    __syncthreads();
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) red[32 * k + wid] = v[k];
+    __syncthreads();
+    for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += red[32 * k + w];
+        v[k] = s;
+    }
+}
+
+// Cluster-wide sum: every CTA publishes its block sums in `slot` and reads
+// all CTAs' slots in rank order after a cluster barrier.
+__device__ void cluster_sum3(cg::cluster_group &cl, double v[3], double *slot) {
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) slot[k] = v[k];
+    cl.sync();
+    const unsigned cs = cl.num_blocks();
+    double s[3] = {0.0, 0.0, 0.0};
+    for (unsigned r = 0; r < cs; ++r) {
+        const double *rem = cl.map_shared_rank(slot, r);
+        for (int k = 0; k < 3; ++k) s[k] += rem[k];
+    }
+    for (int k = 0; k < 3; ++k) v[k] = s[k];
+}
+
+__global__ void __launch_bounds__(KRY_THREADS)
+kry_kernel(KryBatch batch, int n, const int *__restrict__ ptr, const int *__restrict__ col,
+           const double *__restrict__ M, const double *__restrict__ S, double2 *__restrict__ work,
+           double tol, int maxit, int *__restrict__ stat, double *__restrict__ res_out) {
+    __shared__ double red[96];
+    __shared__ double slotA[4], slotB[4], slotC[4];
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned cs = cl.num_blocks();
+    const unsigned rank = cl.block_rank();
+    const int sid = blockIdx.x / cs;
+    const KrySys sy = batch.s[sid];
+    const int rows = (n + cs - 1) / cs;
+    const int r0 = min(n, (int)rank * rows), r1 = min(n, r0 + rows);
+    double2 *r = work + (5 * (size_t)sid + 0) * n;
+    double2 *z = work + (5 * (size_t)sid + 1) * n;
+    double2 *p = work + (5 * (size_t)sid + 2) * n;
+    double2 *q = work + (5 * (size_t)sid + 3) * n;
+    double2 *dinv = work + (5 * (size_t)sid + 4) * n;
+    double2 *x = sy.x;
+    const int cj = sy.conj;
+
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        double md = 0.0, sd = 0.0;
+        for (int e = ptr[i]; e < ptr[i + 1]; ++e)
+            if (col[e] == i) { md = M[e]; sd = S[e]; }
+        const double2 d = cadd(cscale(sy.alpha, md), cscale(sy.beta, sd));
+        const double2 di = cdiv(cd(1.0, 0.0), d);
+        const double2 b = sy.f[i];
+        dinv[i] = di;
+        x[i] = cd(0.0, 0.0);
+        r[i] = b;
+        const double2 zi = cmul(di, b);
+        z[i] = zi;
+        p[i] = zi;
+        const double2 t = dot_term(b, zi, cj);
+        v[0] += t.x;
+        v[1] += t.y;
+        v[2] += cabs2(b);
+    }
+    block_sum3(v, red);
+    cluster_sum3(cl, v, slotA);
+    double2 rho = cd(v[0], v[1]);
+    const double bb = v[2];
+    double rr = bb;
+    int its = 0, status = 0;  // status 0 running/converged, 1 not converged, 2 breakdown
+    if (bb == 0.0) {
+        rr = 0.0;
+    } else {
+        cl.sync();  // p complete everywhere
+        status = 1;
+        for (int it = 1; it <= maxit; ++it) {
+            double w[3] = {0.0, 0.0, 0.0};
+            for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+                double2 acc = cd(0.0, 0.0);
+                for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+                    const double2 a = cadd(cscale(sy.alpha, M[e]), cscale(sy.beta, S[e]));
+                    acc = cadd(acc, cmul(a, __ldcg(&p[col[e]])));
+                }
+                q[i] = acc;
+                const double2 t = dot_term(p[i], acc, cj);
+                w[0] += t.x;
+                w[1] += t.y;
+            }
+            block_sum3(w, red);
+            cluster_sum3(cl, w, slotB);
+            const double2 pq = cd(w[0], w[1]);
+            if (!(cabs2(pq) > 0.0)) { status = 2; its = it; break; }
+            const double2 al = cdiv(rho, pq);
+            double u[3] = {0.0, 0.0, 0.0};
+            for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+                x[i] = cadd(x[i], cmul(al, p[i]));
+                const double2 ri = csub(r[i], cmul(al, q[i]));
+                r[i] = ri;
+                const double2 zi = cmul(dinv[i], ri);
+                z[i] = zi;
+                const double2 t = dot_term(ri, zi, cj);
+                u[0] += t.x;
+                u[1] += t.y;
+                u[2] += cabs2(ri);
+            }
+            block_sum3(u, red);
+            cluster_sum3(cl, u, slotC);
+            rr = u[2];
+            its = it;
+            if (rr <= tol * tol * bb) { status = 0; break; }
+            const double2 rn = cd(u[0], u[1]);
+            if (!(cabs2(rho) > 0.0)) { status = 2; break; }
+            const double2 be = cdiv(rn, rho);
+            rho = rn;
+            for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) p[i] = cadd(z[i], cmul(be, p[i]));
+            cl.sync();
+        }
+    }
+    cl.sync();  // keep shared memory alive until every CTA has read it
+    if (rank == 0 && threadIdx.x == 0) {
+        stat[sid] = status == 0 ? its : (status == 1 ? -its : -1000000 - its);
+        res_out[sid] = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    }
+}
+
+// fD = -S u1 / k_eps^2, fN = M u2
+__global__ void osrc_rhs_kernel(int n, const int *__restrict__ ptr, const int *__restrict__ col,
+                                const double *__restrict__ M, const double *__restrict__ S,
+                                const double2 *__restrict__ u, double2 mske2,
+                                double2 *__restrict__ fD, double2 *__restrict__ fN) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 a = cd(0, 0), b = cd(0, 0);
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+        const int j = col[e];
+        a = cadd(a, cscale(u[j], S[e]));
+        b = cadd(b, cscale(u[n + j], M[e]));
+    }
+    fD[i] = cmul(mske2, a);
+    fN[i] = b;
+}
+
+struct OsrcComb {
+    int np;
+    double2 ik, iik;  // i k and 1/(i k)
+    double2 C0, g0;
+    double2 A[16], g[16];
+};
+
+// y1 = i k [C0 u1 + sum_j A_j w_j],  y2 = [g0 v0 + sum_j g_j v_j] / (i k)
+__global__ void osrc_combine_kernel(int n, OsrcComb c, const double2 *__restrict__ u,
+                                    const double2 *__restrict__ sol, double2 *__restrict__ y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 a = cmul(c.C0, u[i]);
+    for (int j = 0; j < c.np; ++j) a = cadd(a, cmul(c.A[j], sol[(size_t)j * n + i]));
+    double2 b = cmul(c.g0, sol[(size_t)c.np * n + i]);
+    for (int j = 0; j < c.np; ++j) b = cadd(b, cmul(c.g[j], sol[(size_t)(c.np + 1 + j) * n + i]));
+    y[i] = cmul(c.ik, a);
+    y[n + i] = cmul(c.iik, b);
+}
+
+int cluster_size_for(int n) {
+    int cs = (n + 2047) / 2048;
+    if (cs < 1) cs = 1;
+    if (cs > 8) cs = 8;
+    return cs;
+}
+
+int launch_kry(osrc_problem *pb, const KryBatch &batch, cudaStream_t st) {
+    const int n = pb->nv;
+    const int cs = cluster_size_for(n);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(batch.nsys * cs, 1, 1);
+    cfg.blockDim = dim3(KRY_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    OSRC_CK(cudaLaunchKernelEx(&cfg, kry_kernel, batch, n, (const int *)pb->d_ms_ptr.p,
+                               (const int *)pb->d_ms_col.p, (const double *)pb->d_M.p,
+                               (const double *)pb->d_S.p, pb->d_kry.p, pb->p.inner_tol,
+                               pb->p.inner_maxit, pb->d_kry_stat.p, pb->d_kry_res.p));
+    pb->launches++;
+    return OSRC_OK;
+}
+
+// Reads back the inner solver status (one small copy; the caller's stream is
+// synchronised) and turns non-convergence into a status code.
+int check_kry(osrc_problem *pb, int nsys, cudaStream_t st) {
+    int stat[KRY_MAX_SYS];
+    OSRC_CK(cudaMemcpyAsync(stat, pb->d_kry_stat.p, nsys * sizeof(int), cudaMemcpyDeviceToHost, st));
+    OSRC_CK(cudaStreamSynchronize(st));
+    int worst = 0;
+    for (int i = 0; i < nsys; ++i) {
+        if (stat[i] <= -1000000) return OSRC_BREAKDOWN;
+        if (stat[i] < 0) return OSRC_NOT_CONVERGED;
+        if (stat[i] > worst) worst = stat[i];
+    }
+    if (worst > pb->inner_last_max) pb->inner_last_max = worst;
+    return OSRC_OK;
+}
+
+}  // namespace
+
+int ms_build(osrc_problem *pb, const std::vector<int> &cptr, const std::vector<int> &cidx,
+             cudaStream_t st) {
+    osrc_mesh *m = pb->mesh;
+    osrc_ctx *ctx = m->ctx;
+    const int nt = pb->nt, nnz = pb->ms_nnz;
+    DBuf<double> bm, bs;
+    DBuf<int> d_cptr, d_cidx;
+    OSRC_TRY(bm.alloc(ctx, 9 * (size_t)nt));
+    OSRC_TRY(bs.alloc(ctx, 9 * (size_t)nt));
+    OSRC_TRY(d_cptr.alloc(ctx, cptr.size()));
+    OSRC_TRY(d_cidx.alloc(ctx, cidx.size()));
+    OSRC_TRY(pb->d_M.alloc(ctx, nnz));
+    OSRC_TRY(pb->d_S.alloc(ctx, nnz));
+    OSRC_CK(cudaMemcpyAsync(d_cptr.p, cptr.data(), cptr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    OSRC_CK(cudaMemcpyAsync(d_cidx.p, cidx.data(), cidx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    ms_element_kernel<<<(nt + 127) / 128, 128, 0, st>>>(nt, pb->d_tgeo.p, m->d_verts.p, m->d_tris.p,
+                                                        bm.p, bs.p);
+    csr_sum_kernel<<<(nnz + 255) / 256, 256, 0, st>>>(nnz, d_cptr.p, d_cidx.p, bm.p, bs.p, pb->d_M.p,
+                                                      pb->d_S.p);
+    pb->launches += 2;
+    OSRC_CK(cudaGetLastError());
+    // inner solver workspace: 2 N_Pade + 1 systems of 5 vectors, plus rhs and solutions
+    const int nsys = 2 * pb->p.n_pade + 1;
+    OSRC_TRY(pb->d_kry.alloc(ctx, 5 * (size_t)(nsys > 2 ? nsys : 2) * pb->nv));
+    OSRC_TRY(pb->d_kry_rhs.alloc(ctx, (size_t)(2 + nsys) * pb->nv));
+    OSRC_TRY(pb->d_kry_stat.alloc(ctx, KRY_MAX_SYS));
+    OSRC_TRY(pb->d_kry_res.alloc(ctx, KRY_MAX_SYS));
+    OSRC_CK(cudaStreamSynchronize(st));
+    return OSRC_OK;
+}
+
+int mass_solve(osrc_problem *pb, const double2 *x, double2 *y, cudaStream_t st) {
+    const int n = pb->nv;
+    KryBatch b{};
+    b.nsys = 2;
+    for (int k = 0; k < 2; ++k) {
+        b.s[k].alpha = cd(1.0, 0.0);
+        b.s[k].beta = cd(0.0, 0.0);
+        b.s[k].f = x + (size_t)k * n;
+        b.s[k].x = y + (size_t)k * n;
+        b.s[k].conj = 1;
+    }
+    OSRC_TRY(launch_kry(pb, b, st));
+    return check_kry(pb, 2, st);
+}
+
+int osrc_precond(osrc_problem *pb, const double2 *x, double2 *y, cudaStream_t st) {
+    const int n = pb->nv, np = pb->p.n_pade;
+    const double2 ke2 = cmul(pb->k_eps, pb->k_eps);
+    const double2 inv_ke2 = cdiv(cd(1.0, 0.0), ke2);
+    double2 *fD = pb->d_kry_rhs.p, *fN = fD + n, *sol = fN + n;
+    osrc_rhs_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, pb->d_ms_ptr.p, pb->d_ms_col.p, pb->d_M.p,
+                                                     pb->d_S.p, x, cscale(inv_ke2, -1.0), fD, fN);
+    pb->launches++;
+    KryBatch b{};
+    b.nsys = 2 * np + 1;
+    for (int j = 0; j < np; ++j) {  // DtN: (M - B_j S / k_eps^2) w_j = fD
+        KrySys &s = b.s[j];
+        s.alpha = cd(1.0, 0.0);
+        s.beta = cscale(cmul(pb->B[j], inv_ke2), -1.0);
+        s.f = fD;
+        s.x = sol + (size_t)j * n;
+        s.conj = 0;
+    }
+    {   // NtD, (1 + X)^-1 part: (M - S / k_eps^2) v0 = fN
+        KrySys &s = b.s[np];
+        s.alpha = cd(1.0, 0.0);
+        s.beta = cscale(inv_ke2, -1.0);
+        s.f = fN;
+        s.x = sol + (size_t)np * n;
+        s.conj = 0;
+    }
+    for (int j = 0; j < np; ++j) {  // NtD: (M - B_j S / k_eps^2) v_j = fN
+        KrySys &s = b.s[np + 1 + j];
+        s.alpha = cd(1.0, 0.0);
+        s.beta = cscale(cmul(pb->B[j], inv_ke2), -1.0);
+        s.f = fN;
+        s.x = sol + (size_t)(np + 1 + j) * n;
+        s.conj = 0;
+    }
+    OSRC_TRY(launch_kry(pb, b, st));
+    OsrcComb c{};
+    c.np = np;
+    c.ik = cd(0.0, pb->k_osrc);
+    c.iik = cd(0.0, -1.0 / pb->k_osrc);
+    c.C0 = pb->C0;
+    c.g0 = pb->g0;
+    for (int j = 0; j < np; ++j) {
+        c.A[j] = pb->A[j];
+        c.g[j] = pb->g[j];
+    }
+    osrc_combine_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, c, x, sol, y);
+    pb->launches++;
+    OSRC_CK(cudaGetLastError());
+    return check_kry(pb, b.nsys, st);
+}

@@ -1,0 +1,708 @@
+// osrc_api.cu -- the C ABI (include/osrc_pmchwt.h): contexts, meshes,
+// problems, operator applies and the GMRES driver.  Host code here builds
+// the mesh topology (incidence, touching triangle pairs, CSR patterns and
+// the deterministic contribution lists that the device kernels sum); all
+// arithmetic of the method runs in the kernels of k_*.cu.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+
+#include "osrc_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// errors and memory accounting
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+void osrc_set_error(const std::string &msg) { g_last_error = msg; }
+
+extern "C" const char *osrc_status_string(int s) {
+    switch (s) {
+        case OSRC_OK: return "OSRC_OK";
+        case OSRC_INVALID_ARG: return "OSRC_INVALID_ARG";
+        case OSRC_OUT_OF_MEMORY: return "OSRC_OUT_OF_MEMORY";
+        case OSRC_CUDA_ERROR: return "OSRC_CUDA_ERROR";
+        case OSRC_NOT_CONVERGED: return "OSRC_NOT_CONVERGED";
+        case OSRC_BREAKDOWN: return "OSRC_BREAKDOWN";
+        case OSRC_TIMEOUT: return "OSRC_TIMEOUT";
+        case OSRC_UNSUPPORTED: return "OSRC_UNSUPPORTED";
+        default: return "OSRC_UNKNOWN_STATUS";
+    }
+}
+
+int ctx_alloc(osrc_ctx *ctx, void **p, size_t bytes) {
+    *p = nullptr;
+    if (ctx->budget && ctx->used + bytes > ctx->budget) {
+        osrc_set_error("device memory budget exceeded");
+        return OSRC_OUT_OF_MEMORY;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        *p = nullptr;
+        osrc_set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return OSRC_OUT_OF_MEMORY;
+    }
+    ctx->used += bytes;
+    return OSRC_OK;
+}
+
+void ctx_free(osrc_ctx *ctx, void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    ctx->used -= bytes;
+}
+
+extern "C" void osrc_params_default(osrc_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->k_ext = 1.0;
+    p->k_int = 1.0;
+    p->rho_ratio = 1.0;
+    p->n_pade = 4;
+    p->theta = M_PI / 3.0;
+    p->damping_R = 0.0;
+    p->osrc_side = 1;
+    p->n_ss = 4;
+    p->precision = OSRC_FP32_MATFREE;
+    p->inner_tol = 1e-10;
+    p->inner_maxit = 2000;
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" int osrc_create(osrc_ctx **out, int device, size_t budget) {
+    if (!out) return OSRC_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    OSRC_CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return OSRC_INVALID_ARG;
+    OSRC_CK(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    OSRC_CK(cudaGetDeviceProperties(&prop, device));
+    if (prop.major < 10) {
+        osrc_set_error("this library is built for sm_103a (GB300)");
+        return OSRC_UNSUPPORTED;
+    }
+    osrc_ctx *c = new osrc_ctx;
+    c->device = device;
+    c->budget = budget;
+    *out = c;
+    return OSRC_OK;
+}
+
+extern "C" void osrc_destroy(osrc_ctx *ctx) { delete ctx; }
+extern "C" size_t osrc_mem_used(const osrc_ctx *ctx) { return ctx ? ctx->used : 0; }
+
+// ---------------------------------------------------------------------------
+// mesh
+// ---------------------------------------------------------------------------
+extern "C" int osrc_mesh_validate(const double *verts, int32_t nv, const int32_t *tris, int32_t nt) {
+    if (!verts || !tris || nv < 4 || nt < 4) {
+        osrc_set_error("mesh needs at least 4 vertices and 4 triangles");
+        return OSRC_INVALID_ARG;
+    }
+    for (long long i = 0; i < 3LL * nv; ++i)
+        if (!std::isfinite(verts[i])) {
+            osrc_set_error("non-finite vertex coordinate");
+            return OSRC_INVALID_ARG;
+        }
+    std::vector<char> used(nv, 0);
+    std::unordered_map<uint64_t, int> edges;
+    edges.reserve(3 * (size_t)nt * 2);
+    for (int t = 0; t < nt; ++t) {
+        const int a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
+        if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv) {
+            osrc_set_error("triangle index out of range");
+            return OSRC_INVALID_ARG;
+        }
+        if (a == b || b == c || a == c) {
+            osrc_set_error("triangle with a repeated vertex");
+            return OSRC_INVALID_ARG;
+        }
+        used[a] = used[b] = used[c] = 1;
+        const double *P0 = verts + 3 * a, *P1 = verts + 3 * b, *P2 = verts + 3 * c;
+        double e1[3], e2[3];
+        for (int j = 0; j < 3; ++j) {
+            e1[j] = P1[j] - P0[j];
+            e2[j] = P2[j] - P0[j];
+        }
+        const double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
+                     cz = e1[0] * e2[1] - e1[1] * e2[0];
+        const double l1 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+        const double l2 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+        const double a2 = cx * cx + cy * cy + cz * cz;
+        if (!(a2 > 1e-24 * l1 * l2) || l1 == 0.0 || l2 == 0.0) {
+            osrc_set_error("zero-area triangle");
+            return OSRC_INVALID_ARG;
+        }
+        const int vv[3] = {a, b, c};
+        for (int k = 0; k < 3; ++k) {
+            const uint64_t key = ((uint64_t)(uint32_t)vv[k] << 32) | (uint32_t)vv[(k + 1) % 3];
+            if (++edges[key] > 1) {
+                osrc_set_error("directed edge used twice: inconsistent orientation or non-manifold");
+                return OSRC_INVALID_ARG;
+            }
+        }
+    }
+    for (const auto &kv : edges) {
+        const uint64_t rev = (kv.first << 32) | (kv.first >> 32);
+        if (edges.find(rev) == edges.end()) {
+            osrc_set_error("open mesh: an edge has no opposite triangle");
+            return OSRC_INVALID_ARG;
+        }
+    }
+    for (int i = 0; i < nv; ++i)
+        if (!used[i]) {
+            osrc_set_error("vertex not used by any triangle");
+            return OSRC_INVALID_ARG;
+        }
+    return OSRC_OK;
+}
+
+extern "C" int osrc_mesh_create(osrc_ctx *ctx, const double *verts, int32_t nv,
+                                const int32_t *tris, int32_t nt, osrc_mesh **out) {
+    if (!ctx || !out) return OSRC_INVALID_ARG;
+    *out = nullptr;
+    OSRC_TRY(osrc_mesh_validate(verts, nv, tris, nt));
+    OSRC_CK(cudaSetDevice(ctx->device));
+    osrc_mesh *m = new osrc_mesh;
+    m->ctx = ctx;
+    m->nv = nv;
+    m->nt = nt;
+    m->verts.assign(verts, verts + 3 * (size_t)nv);
+    m->tris.assign(tris, tris + 3 * (size_t)nt);
+    // vertex -> (3 t + local) incidence, in triangle order
+    m->vt_ptr.assign(nv + 1, 0);
+    for (int k = 0; k < 3 * nt; ++k) m->vt_ptr[tris[k] + 1]++;
+    for (int i = 0; i < nv; ++i) m->vt_ptr[i + 1] += m->vt_ptr[i];
+    m->vt_idx.assign(3 * (size_t)nt, 0);
+    {
+        std::vector<int> fill(m->vt_ptr.begin(), m->vt_ptr.end() - 1);
+        for (int k = 0; k < 3 * nt; ++k) m->vt_idx[fill[tris[k]]++] = k;
+    }
+    // mean edge length over unique edges
+    double sum = 0.0;
+    long long cnt = 0;
+    for (int t = 0; t < nt; ++t)
+        for (int k = 0; k < 3; ++k) {
+            const int a = tris[3 * t + k], b = tris[3 * t + (k + 1) % 3];
+            if (a < b) {
+                double d2 = 0.0;
+                for (int j = 0; j < 3; ++j) {
+                    const double d = verts[3 * a + j] - verts[3 * b + j];
+                    d2 += d * d;
+                }
+                sum += std::sqrt(d2);
+                ++cnt;
+            }
+        }
+    m->mean_edge = cnt ? sum / cnt : 0.0;
+    int s;
+    if ((s = m->d_verts.alloc(ctx, 3 * (size_t)nv)) || (s = m->d_tris.alloc(ctx, 3 * (size_t)nt)) ||
+        (s = m->d_vt_ptr.alloc(ctx, nv + 1)) || (s = m->d_vt_idx.alloc(ctx, 3 * (size_t)nt))) {
+        delete m;
+        return s;
+    }
+    cudaError_t e = cudaMemcpy(m->d_verts.p, verts, 3 * (size_t)nv * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_tris.p, tris, 3 * (size_t)nt * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_vt_ptr.p, m->vt_ptr.data(), (nv + 1) * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_vt_idx.p, m->vt_idx.data(), 3 * (size_t)nt * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        osrc_set_error(std::string("mesh upload: ") + cudaGetErrorString(e));
+        delete m;
+        return OSRC_CUDA_ERROR;
+    }
+    *out = m;
+    return OSRC_OK;
+}
+
+extern "C" void osrc_mesh_destroy(osrc_mesh *m) { delete m; }
+extern "C" double osrc_mesh_mean_edge(const osrc_mesh *m) { return m ? m->mean_edge : 0.0; }
+
+// ---------------------------------------------------------------------------
+// problem set-up: topology on the host, numerics on the device
+// ---------------------------------------------------------------------------
+namespace {
+
+// Shared-vertex type of triangles t, s and the local orders that put the
+// shared vertices first (same order in both), packed 2 bits per index.
+int touch_case(const int *t, const int *s, int &perm) {
+    int pt[3], ps[3], n = 0;
+    bool ut[3] = {false, false, false}, us[3] = {false, false, false};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            if (t[a] == s[b]) {
+                pt[n] = a;
+                ps[n] = b;
+                ut[a] = us[b] = true;
+                ++n;
+            }
+    if (n == 0) return 0;
+    int kt = n, ks = n;
+    for (int a = 0; a < 3; ++a) if (!ut[a]) pt[kt++] = a;
+    for (int b = 0; b < 3; ++b) if (!us[b]) ps[ks++] = b;
+    perm = 0;
+    for (int a = 0; a < 3; ++a) perm |= (pt[a] << (2 * a)) | (ps[a] << (6 + 2 * a));
+    return n;
+}
+
+// Counting sort of (position, index) contributions into CSR-like lists.
+void bucket(int nbuckets, const std::vector<int> &pos, const std::vector<int> &idx,
+            std::vector<int> &ptr, std::vector<int> &out) {
+    ptr.assign(nbuckets + 1, 0);
+    for (int p : pos) ptr[p + 1]++;
+    for (int i = 0; i < nbuckets; ++i) ptr[i + 1] += ptr[i];
+    out.assign(pos.size(), 0);
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+    for (size_t k = 0; k < pos.size(); ++k) out[fill[pos[k]]++] = idx[k];
+}
+
+int find_col(const std::vector<int> &ptr, const std::vector<int> &col, int i, int j) {
+    auto b = col.begin() + ptr[i], e = col.begin() + ptr[i + 1];
+    auto it = std::lower_bound(b, e, j);
+    return (it != e && *it == j) ? (int)(it - col.begin()) : -1;
+}
+
+void pade_coefficients(int np, double theta, std::complex<double> &C0,
+                       std::vector<std::complex<double>> &A, std::vector<std::complex<double>> &B) {
+    using cdbl = std::complex<double>;
+    const cdbl I(0.0, 1.0);
+    const cdbl z0 = std::exp(-I * theta) - 1.0;
+    cdbl R0 = 1.0;
+    A.resize(np);
+    B.resize(np);
+    for (int j = 1; j <= np; ++j) {
+        const double sj = std::sin(j * M_PI / (2.0 * np + 1.0));
+        const double aj = 2.0 / (2.0 * np + 1.0) * sj * sj;
+        const double cj = std::cos(j * M_PI / (2.0 * np + 1.0));
+        const double bj = cj * cj;
+        const cdbl den = 1.0 + bj * z0;
+        R0 += aj * z0 / den;
+        A[j - 1] = std::exp(-0.5 * I * theta) * aj / (den * den);
+        B[j - 1] = std::exp(-I * theta) * bj / den;
+    }
+    C0 = std::exp(0.5 * I * theta) * R0;
+}
+
+}  // namespace
+
+extern "C" int osrc_problem_create(osrc_mesh *mesh, const osrc_params *prm, osrc_problem **out,
+                                   void *stream) {
+    if (!mesh || !prm || !out) return OSRC_INVALID_ARG;
+    *out = nullptr;
+    const osrc_params &p = *prm;
+    if (!(p.k_ext > 0.0) || !(p.k_int > 0.0) || !std::isfinite(p.k_ext) || !std::isfinite(p.k_int) ||
+        !(p.rho_ratio > 0.0) || !std::isfinite(p.rho_ratio) || p.n_pade < 1 || p.n_pade > 16 ||
+        p.n_ss < 2 || p.n_ss > 12 || !(p.inner_tol > 0.0) || p.inner_tol > 1e-4 ||
+        p.inner_maxit < 1 || (p.precision != OSRC_FP32_MATFREE && p.precision != OSRC_FP64_DENSE) ||
+        (p.osrc_side != 0 && p.osrc_side != 1) || !std::isfinite(p.theta)) {
+        osrc_set_error("invalid problem parameters");
+        return OSRC_INVALID_ARG;
+    }
+    osrc_ctx *ctx = mesh->ctx;
+    OSRC_CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    osrc_problem *pb = new osrc_problem;
+    pb->mesh = mesh;
+    pb->p = p;
+    pb->nv = mesh->nv;
+    pb->nt = mesh->nt;
+    pb->npts = 6 * mesh->nt;
+    int s = OSRC_OK;
+    const int nv = pb->nv, nt = pb->nt;
+    const int *tris = mesh->tris.data();
+    do {
+        if ((s = far_setup_geometry(pb, st))) break;
+        // ---- touching triangle pairs ----------------------------------------
+        std::vector<NearPair> pairs;
+        pairs.reserve(14 * (size_t)nt);
+        std::vector<int> cand;
+        for (int t = 0; t < nt; ++t) {
+            cand.clear();
+            for (int a = 0; a < 3; ++a) {
+                const int v = tris[3 * t + a];
+                for (int e = mesh->vt_ptr[v]; e < mesh->vt_ptr[v + 1]; ++e) cand.push_back(mesh->vt_idx[e] / 3);
+            }
+            std::sort(cand.begin(), cand.end());
+            cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+            for (int sidx : cand) {
+                int perm = 0;
+                const int kase = touch_case(tris + 3 * t, tris + 3 * sidx, perm);
+                if (kase > 0) pairs.push_back(NearPair{t, sidx, kase, perm});
+            }
+        }
+        // ---- near CSR pattern: vertex pairs of touching triangles -------------
+        std::vector<int> nptr(nv + 1, 0), ncol;
+        {
+            std::vector<std::vector<int>> rowsets(nv);
+            for (const NearPair &pr : pairs)
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) rowsets[tris[3 * pr.t + a]].push_back(tris[3 * pr.s + b]);
+            for (int i = 0; i < nv; ++i) {
+                auto &r = rowsets[i];
+                std::sort(r.begin(), r.end());
+                r.erase(std::unique(r.begin(), r.end()), r.end());
+                nptr[i + 1] = nptr[i] + (int)r.size();
+            }
+            ncol.reserve(nptr[nv]);
+            for (int i = 0; i < nv; ++i) ncol.insert(ncol.end(), rowsets[i].begin(), rowsets[i].end());
+        }
+        pb->near_nnz = nptr[nv];
+        std::vector<int> cpos, cidx;
+        cpos.reserve(9 * pairs.size());
+        cidx.reserve(9 * pairs.size());
+        for (size_t k = 0; k < pairs.size(); ++k)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    cpos.push_back(find_col(nptr, ncol, tris[3 * pairs[k].t + a], tris[3 * pairs[k].s + b]));
+                    cidx.push_back((int)(9 * k + 3 * a + b));
+                }
+        std::vector<int> cptr, clist;
+        bucket(pb->near_nnz, cpos, cidx, cptr, clist);
+        if ((s = pb->d_nr_ptr.alloc(ctx, nv + 1)) || (s = pb->d_nr_col.alloc(ctx, ncol.size()))) break;
+        if (cudaMemcpy(pb->d_nr_ptr.p, nptr.data(), (nv + 1) * sizeof(int), cudaMemcpyHostToDevice) ||
+            cudaMemcpy(pb->d_nr_col.p, ncol.data(), ncol.size() * sizeof(int), cudaMemcpyHostToDevice)) {
+            s = OSRC_CUDA_ERROR;
+            break;
+        }
+        if ((s = near_build(pb, pairs, cptr, clist, st))) break;
+        // ---- mass / stiffness CSR (1-ring) -------------------------------------
+        std::vector<int> mptr(nv + 1, 0), mcol;
+        {
+            std::vector<std::vector<int>> rowsets(nv);
+            for (int t = 0; t < nt; ++t)
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) rowsets[tris[3 * t + a]].push_back(tris[3 * t + b]);
+            for (int i = 0; i < nv; ++i) {
+                auto &r = rowsets[i];
+                std::sort(r.begin(), r.end());
+                r.erase(std::unique(r.begin(), r.end()), r.end());
+                mptr[i + 1] = mptr[i] + (int)r.size();
+            }
+            for (int i = 0; i < nv; ++i) mcol.insert(mcol.end(), rowsets[i].begin(), rowsets[i].end());
+        }
+        pb->ms_nnz = mptr[nv];
+        cpos.clear();
+        cidx.clear();
+        for (int t = 0; t < nt; ++t)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    cpos.push_back(find_col(mptr, mcol, tris[3 * t + a], tris[3 * t + b]));
+                    cidx.push_back(9 * t + 3 * a + b);
+                }
+        bucket(pb->ms_nnz, cpos, cidx, cptr, clist);
+        if ((s = pb->d_ms_ptr.alloc(ctx, nv + 1)) || (s = pb->d_ms_col.alloc(ctx, mcol.size()))) break;
+        if (cudaMemcpy(pb->d_ms_ptr.p, mptr.data(), (nv + 1) * sizeof(int), cudaMemcpyHostToDevice) ||
+            cudaMemcpy(pb->d_ms_col.p, mcol.data(), mcol.size() * sizeof(int), cudaMemcpyHostToDevice)) {
+            s = OSRC_CUDA_ERROR;
+            break;
+        }
+        if ((s = ms_build(pb, cptr, clist, st))) break;
+        // ---- OSRC constants (Sec. 2.6) ------------------------------------------
+        pb->k_osrc = p.osrc_side == 1 ? p.k_int : p.k_ext;
+        const double R = p.damping_R > 0.0 ? p.damping_R : mesh->mean_edge;
+        const std::complex<double> ke =
+            pb->k_osrc * (1.0 + std::complex<double>(0.0, 0.4) * std::pow(pb->k_osrc * R, -2.0 / 3.0));
+        pb->k_eps = cd(ke.real(), ke.imag());
+        std::complex<double> C0;
+        std::vector<std::complex<double>> A, B;
+        pade_coefficients(p.n_pade, p.theta, C0, A, B);
+        pb->C0 = cd(C0.real(), C0.imag());
+        std::complex<double> g0 = C0;
+        pb->A.resize(p.n_pade);
+        pb->B.resize(p.n_pade);
+        pb->g.resize(p.n_pade);
+        for (int j = 0; j < p.n_pade; ++j) {
+            const std::complex<double> gj = A[j] / (1.0 - B[j]);
+            g0 -= gj;
+            pb->A[j] = cd(A[j].real(), A[j].imag());
+            pb->B[j] = cd(B[j].real(), B[j].imag());
+            pb->g[j] = cd(gj.real(), gj.imag());
+        }
+        pb->g0 = cd(g0.real(), g0.imag());
+        // ---- workspace ------------------------------------------------------------
+        if ((s = pb->d_tmp2.alloc(ctx, 4 * (size_t)nv))) break;
+        if ((s = pb->d_scalars.alloc(ctx, 64))) break;
+        if (p.precision == OSRC_FP64_DENSE && (s = dense_assemble(pb, st))) break;
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            s = OSRC_CUDA_ERROR;
+            break;
+        }
+    } while (0);
+    if (s != OSRC_OK) {
+        delete pb;
+        return s;
+    }
+    *out = pb;
+    return OSRC_OK;
+}
+
+extern "C" void osrc_problem_destroy(osrc_problem *pb) {
+    if (!pb) return;
+    if (pb->h_res) cudaFreeHost(pb->h_res);
+    delete pb;
+}
+
+extern "C" int osrc_problem_nv(const osrc_problem *pb) { return pb ? pb->nv : 0; }
+extern "C" long long osrc_launch_count(const osrc_problem *pb) { return pb ? pb->launches : 0; }
+extern "C" long long osrc_near_pairs(const osrc_problem *pb) { return pb ? pb->near_pairs : 0; }
+extern "C" long long osrc_near_nnz(const osrc_problem *pb) { return pb ? pb->near_nnz : 0; }
+
+// ---------------------------------------------------------------------------
+// right-hand sides
+// ---------------------------------------------------------------------------
+static int rhs_common(osrc_problem *pb, const double *src, int nrhs, void *b, void *stream, int kind) {
+    if (!pb || !src || !b || nrhs < 1) return OSRC_INVALID_ARG;
+    OSRC_CK(cudaSetDevice(pb->mesh->ctx->device));
+    for (int r = 0; r < nrhs; ++r) {
+        const double *s3 = src + 3 * r;
+        if (!std::isfinite(s3[0]) || !std::isfinite(s3[1]) || !std::isfinite(s3[2])) return OSRC_INVALID_ARG;
+        if (kind == 0 && std::fabs(s3[0] * s3[0] + s3[1] * s3[1] + s3[2] * s3[2] - 1.0) > 1e-9)
+            return OSRC_INVALID_ARG;
+        OSRC_TRY(rhs_build(pb, kind, s3, (double2 *)b + 2 * (size_t)pb->nv * r, (cudaStream_t)stream));
+    }
+    return OSRC_OK;
+}
+
+extern "C" int osrc_rhs_planewave(osrc_problem *pb, const double *dirs, int nrhs, void *b, void *stream) {
+    return rhs_common(pb, dirs, nrhs, b, stream, 0);
+}
+
+extern "C" int osrc_rhs_pointsource(osrc_problem *pb, const double *srcs, int nrhs, void *b, void *stream) {
+    return rhs_common(pb, srcs, nrhs, b, stream, 1);
+}
+
+// ---------------------------------------------------------------------------
+// operators
+// ---------------------------------------------------------------------------
+static int apply_one(osrc_problem *pb, const double2 *x, double2 *y, int form, int part, cudaStream_t st) {
+    double2 *dst = form == OSRC_STRONG ? pb->d_tmp2.p : y;
+    if (pb->p.precision == OSRC_FP64_DENSE) {
+        if (part != OSRC_PART_ALL) return OSRC_UNSUPPORTED;
+        OSRC_TRY(dense_apply(pb, x, dst, st));
+    } else {
+        OSRC_TRY(far_apply(pb, x, dst, part, st));
+    }
+    if (form == OSRC_STRONG) OSRC_TRY(mass_solve(pb, dst, y, st));
+    return OSRC_OK;
+}
+
+extern "C" int osrc_pmchwt_apply(osrc_problem *pb, const void *x, void *y, int nrhs, int form,
+                                 int part, void *stream) {
+    if (!pb || !x || !y || nrhs < 1 || (form != OSRC_WEAK && form != OSRC_STRONG) || part < 1 || part > 3)
+        return OSRC_INVALID_ARG;
+    if (x == y) return OSRC_INVALID_ARG;
+    OSRC_CK(cudaSetDevice(pb->mesh->ctx->device));
+    const size_t n = 2 * (size_t)pb->nv;
+    for (int r = 0; r < nrhs; ++r)
+        OSRC_TRY(apply_one(pb, (const double2 *)x + n * r, (double2 *)y + n * r, form, part,
+                           (cudaStream_t)stream));
+    return OSRC_OK;
+}
+
+extern "C" int osrc_mass_solve(osrc_problem *pb, const void *x, void *y, int nrhs, void *stream) {
+    if (!pb || !x || !y || nrhs < 1 || x == y) return OSRC_INVALID_ARG;
+    OSRC_CK(cudaSetDevice(pb->mesh->ctx->device));
+    const size_t n = 2 * (size_t)pb->nv;
+    for (int r = 0; r < nrhs; ++r)
+        OSRC_TRY(mass_solve(pb, (const double2 *)x + n * r, (double2 *)y + n * r, (cudaStream_t)stream));
+    return OSRC_OK;
+}
+
+extern "C" int osrc_precond_apply(osrc_problem *pb, const void *x, void *y, int nrhs, void *stream) {
+    if (!pb || !x || !y || nrhs < 1 || x == y) return OSRC_INVALID_ARG;
+    OSRC_CK(cudaSetDevice(pb->mesh->ctx->device));
+    const size_t n = 2 * (size_t)pb->nv;
+    for (int r = 0; r < nrhs; ++r)
+        OSRC_TRY(osrc_precond(pb, (const double2 *)x + n * r, (double2 *)y + n * r, (cudaStream_t)stream));
+    return OSRC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// GMRES (Sec. 3.1): no restart, x0 = 0, preconditioned relative residual
+// ---------------------------------------------------------------------------
+namespace {
+
+struct PhaseTimer {
+    cudaEvent_t ev[4];
+    bool ok = false;
+    PhaseTimer() {
+        ok = true;
+        for (auto &e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) ok = false;
+    }
+    ~PhaseTimer() {
+        for (auto &e : ev) cudaEventDestroy(e);
+    }
+};
+
+int ensure_gmres_workspace(osrc_problem *pb, int maxit) {
+    osrc_ctx *ctx = pb->mesh->ctx;
+    const size_t n = 2 * (size_t)pb->nv;
+    if (pb->basis_cap < maxit) {
+        pb->d_basis.release();
+        pb->d_h.release();
+        pb->d_givens.release();
+        OSRC_TRY(pb->d_basis.alloc(ctx, (size_t)(maxit + 1) * n));
+        OSRC_TRY(pb->d_h.alloc(ctx, (size_t)(maxit + 1) * maxit));
+        OSRC_TRY(pb->d_givens.alloc(ctx, 4 * (size_t)(maxit + 1) + 2 * (size_t)(maxit + 1)));
+        pb->basis_cap = maxit;
+    }
+    if (!pb->d_w.p) {
+        OSRC_TRY(pb->d_w.alloc(ctx, n));
+        OSRC_TRY(pb->d_y.alloc(ctx, n));
+        OSRC_TRY(pb->d_cvec.alloc(ctx, n));
+        OSRC_TRY(pb->d_b1.alloc(ctx, n));
+        OSRC_TRY(pb->d_x1.alloc(ctx, n));
+    }
+    if (!pb->h_res) OSRC_CK(cudaMallocHost((void **)&pb->h_res, 8 * sizeof(double)));
+    return OSRC_OK;
+}
+
+// w = P M^-1 B v; timings accumulated into info
+int precond_matvec(osrc_problem *pb, const double2 *v, double2 *w, cudaStream_t st, PhaseTimer &tm,
+                   double &ms_mv, double &ms_pc) {
+    double2 *t1 = pb->d_tmp2.p;            // B v
+    double2 *t2 = pb->d_y.p;               // M^-1 B v
+    if (tm.ok) cudaEventRecord(tm.ev[0], st);
+    if (pb->p.precision == OSRC_FP64_DENSE) {
+        OSRC_TRY(dense_apply(pb, v, t1, st));
+    } else {
+        OSRC_TRY(far_apply(pb, v, t1, OSRC_PART_ALL, st));
+    }
+    if (tm.ok) cudaEventRecord(tm.ev[1], st);
+    OSRC_TRY(mass_solve(pb, t1, t2, st));
+    OSRC_TRY(osrc_precond(pb, t2, w, st));
+    if (tm.ok) {
+        cudaEventRecord(tm.ev[2], st);
+        cudaEventSynchronize(tm.ev[2]);
+        float a = 0.f, b = 0.f;
+        cudaEventElapsedTime(&a, tm.ev[0], tm.ev[1]);
+        cudaEventElapsedTime(&b, tm.ev[1], tm.ev[2]);
+        ms_mv += a;
+        ms_pc += b;
+    }
+    return OSRC_OK;
+}
+
+int gmres_one(osrc_problem *pb, const double2 *b, double2 *x, double tol, int maxit, cudaStream_t st,
+              osrc_solve_info &info, PhaseTimer &tm) {
+    const int n = 2 * pb->nv;
+    const int ldh = maxit + 1;
+    double2 *V = pb->d_basis.p, *H = pb->d_h.p, *gv = pb->d_givens.p;
+    double *sc = pb->d_scalars.p;
+    // c = P M^-1 b
+    OSRC_TRY(mass_solve(pb, b, pb->d_y.p, st));
+    OSRC_TRY(osrc_precond(pb, pb->d_y.p, pb->d_cvec.p, st));
+    OSRC_TRY(vec_norm(pb, pb->d_cvec.p, n, sc, st));
+    OSRC_CK(cudaMemcpyAsync(pb->h_res, sc, sizeof(double), cudaMemcpyDeviceToHost, st));
+    OSRC_CK(cudaStreamSynchronize(st));
+    const double beta = pb->h_res[0];
+    if (!(beta > 0.0) || !std::isfinite(beta)) {
+        OSRC_CK(cudaMemsetAsync(x, 0, n * sizeof(double2), st));
+        info.iterations = 0;
+        info.precond_residual = 0.0;
+        return std::isfinite(beta) ? OSRC_OK : OSRC_INVALID_ARG;
+    }
+    OSRC_TRY(vec_scale_copy(pb, pb->d_cvec.p, sc, V, n, st));
+    OSRC_CK(cudaMemsetAsync(H, 0, (size_t)ldh * maxit * sizeof(double2), st));
+    OSRC_CK(cudaMemsetAsync(gv, 0, 4 * (size_t)ldh * sizeof(double2), st));
+    const double2 g0 = cd(beta, 0.0);
+    OSRC_CK(cudaMemcpyAsync(gv + 2 * ldh, &g0, sizeof(double2), cudaMemcpyHostToDevice, st));
+    double res = 1.0;
+    int j = 0;
+    bool conv = false;
+    double2 *h2 = gv + 4 * ldh;  // second-pass projections
+    for (j = 0; j < maxit; ++j) {
+        double2 *w = pb->d_w.p;
+        OSRC_TRY(precond_matvec(pb, V + (size_t)j * n, w, st, tm, info.ms_matvec, info.ms_precond));
+        if (tm.ok) cudaEventRecord(tm.ev[0], st);
+        double2 *hc = H + (size_t)ldh * j;
+        // classical Gram-Schmidt, twice
+        OSRC_TRY(vec_dots_conj(pb, V, j + 1, w, n, hc, st));
+        OSRC_TRY(vec_update(pb, V, j + 1, hc, w, n, st));
+        OSRC_TRY(vec_dots_conj(pb, V, j + 1, w, n, h2, st));
+        OSRC_TRY(vec_update(pb, V, j + 1, h2, w, n, st));
+        OSRC_TRY(vec_axpby(pb, cd(1, 0), hc, cd(1, 0), h2, hc, j + 1, st));
+        OSRC_TRY(vec_norm(pb, w, n, sc + 1, st));
+        OSRC_CK(cudaMemcpyAsync(hc + j + 1, sc + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        OSRC_CK(cudaMemsetAsync((double *)(hc + j + 1) + 1, 0, sizeof(double), st));
+        OSRC_TRY(vec_scale_copy(pb, w, sc + 1, V + (size_t)(j + 1) * n, n, st));
+        OSRC_TRY(gmres_givens(pb, j, ldh, H, gv, sc + 2, beta, st));
+        OSRC_CK(cudaMemcpyAsync(pb->h_res, sc + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (tm.ok) cudaEventRecord(tm.ev[1], st);
+        OSRC_CK(cudaStreamSynchronize(st));
+        if (tm.ok) {
+            float a = 0.f;
+            cudaEventElapsedTime(&a, tm.ev[0], tm.ev[1]);
+            info.ms_arnoldi += a;
+        }
+        res = pb->h_res[0];
+        if (!std::isfinite(res)) return OSRC_BREAKDOWN;
+        if (res <= tol) {
+            conv = true;
+            ++j;
+            break;
+        }
+    }
+    OSRC_TRY(gmres_finish(pb, j, ldh, H, gv, V, x, n, st));
+    info.iterations = j;
+    info.precond_residual = res;
+    info.total_iterations += j;
+    if (!conv) info.converged = 0;
+    return OSRC_OK;
+}
+
+}  // namespace
+
+extern "C" int osrc_gmres_solve(osrc_problem *pb, const void *b, void *x, int nrhs, double tol, int maxit,
+                                int flags, osrc_solve_info *info_out, void *stream) {
+    if (!pb || !b || !x || nrhs < 1 || !(tol > 0.0) || maxit < 1 || maxit > 100000) return OSRC_INVALID_ARG;
+    OSRC_CK(cudaSetDevice(pb->mesh->ctx->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = (cudaStream_t)stream;
+    OSRC_TRY(ensure_gmres_workspace(pb, maxit));
+    const int n = 2 * pb->nv;
+    osrc_solve_info info{};
+    info.converged = 1;
+    PhaseTimer tm;
+    pb->inner_last_max = 0;
+    const bool host = (flags & OSRC_HOST_BUFFERS) != 0;
+    for (int r = 0; r < nrhs; ++r) {
+        const double2 *br;
+        double2 *xr;
+        if (host) {
+            OSRC_CK(cudaMemcpyAsync(pb->d_b1.p, (const double2 *)b + (size_t)n * r, n * sizeof(double2),
+                                    cudaMemcpyHostToDevice, st));
+            br = pb->d_b1.p;
+            xr = pb->d_x1.p;
+        } else {
+            br = (const double2 *)b + (size_t)n * r;
+            xr = (double2 *)x + (size_t)n * r;
+        }
+        OSRC_TRY(gmres_one(pb, br, xr, tol, maxit, st, info, tm));
+        // true weak residual |b - B x| / |b|
+        double *sc = pb->d_scalars.p;
+        double2 *t = pb->d_w.p;
+        if (pb->p.precision == OSRC_FP64_DENSE) OSRC_TRY(dense_apply(pb, xr, t, st));
+        else OSRC_TRY(far_apply(pb, xr, t, OSRC_PART_ALL, st));
+        OSRC_TRY(vec_axpby(pb, cd(1, 0), br, cd(-1, 0), t, t, n, st));
+        OSRC_TRY(vec_norm(pb, t, n, sc + 4, st));
+        OSRC_TRY(vec_norm(pb, br, n, sc + 5, st));
+        OSRC_CK(cudaMemcpyAsync(pb->h_res + 4, sc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (host)
+            OSRC_CK(cudaMemcpyAsync((double2 *)x + (size_t)n * r, xr, n * sizeof(double2),
+                                    cudaMemcpyDeviceToHost, st));
+        OSRC_CK(cudaStreamSynchronize(st));
+        info.true_residual = pb->h_res[5] > 0 ? pb->h_res[4] / pb->h_res[5] : 0.0;
+    }
+    info.inner_iterations_max = pb->inner_last_max;
+    info.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (info_out) *info_out = info;
+    return info.converged ? OSRC_OK : OSRC_NOT_CONVERGED;
+}

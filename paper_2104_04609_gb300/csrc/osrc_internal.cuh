@@ -1,0 +1,192 @@
+// osrc_internal.cuh -- internal state and kernel launchers of the GB300 OSRC
+// PMCHWT library.  Not part of the ABI (see include/osrc_pmchwt.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/osrc_pmchwt.h"
+
+// ---------------------------------------------------------------------------
+// error handling: every CUDA call is checked; failures become status codes
+// ---------------------------------------------------------------------------
+#define OSRC_CK(call)                                                       \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) {                                            \
+            osrc_set_error(std::string(#call) + ": " + cudaGetErrorString(e_)); \
+            return (e_ == cudaErrorMemoryAllocation) ? OSRC_OUT_OF_MEMORY   \
+                                                     : OSRC_CUDA_ERROR;     \
+        }                                                                   \
+    } while (0)
+
+#define OSRC_TRY(expr)                 \
+    do {                               \
+        int s_ = (expr);               \
+        if (s_ != OSRC_OK) return s_;  \
+    } while (0)
+
+void osrc_set_error(const std::string &msg);
+
+// ---------------------------------------------------------------------------
+// complex helpers (double2 / float2 as complex numbers)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ double2 cd(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return cd(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return cd(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return cd(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return cd(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return cd(a.x, -a.y); }
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    double d = b.x * b.x + b.y * b.y;
+    return cd((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// ---------------------------------------------------------------------------
+// handles
+// ---------------------------------------------------------------------------
+struct osrc_ctx {
+    int device = 0;
+    size_t budget = 0;  // 0 = unlimited
+    size_t used = 0;
+};
+
+int ctx_alloc(osrc_ctx *ctx, void **p, size_t bytes);
+void ctx_free(osrc_ctx *ctx, void *p, size_t bytes);
+
+// A device buffer whose size is accounted to a context.
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    osrc_ctx *ctx = nullptr;
+    int alloc(osrc_ctx *c, size_t count) {
+        release();
+        ctx = c;
+        n = count;
+        if (count == 0) return OSRC_OK;
+        return ctx_alloc(ctx, (void **)&p, count * sizeof(T));
+    }
+    void release() {
+        if (p) ctx_free(ctx, p, n * sizeof(T));
+        p = nullptr;
+        n = 0;
+    }
+    ~DBuf() { release(); }
+};
+
+struct osrc_mesh {
+    osrc_ctx *ctx = nullptr;
+    int nv = 0, nt = 0;
+    std::vector<double> verts;       // nv x 3
+    std::vector<int> tris;           // nt x 3
+    std::vector<int> vt_ptr, vt_idx; // vertex -> (3*triangle + local) incidence
+    double mean_edge = 0.0;
+    DBuf<double> d_verts;
+    DBuf<int> d_tris, d_vt_ptr, d_vt_idx;
+};
+
+// Touching triangle pair for the Sauter-Schwab kernel.
+struct NearPair {
+    int t, s;      // test, source triangle
+    int kase;      // 1 vertex, 2 edge, 3 identical
+    int perm;      // pt[0..2] | ps[0..2] << 6, 2 bits each
+};
+
+struct osrc_problem {
+    osrc_mesh *mesh = nullptr;
+    osrc_params p{};
+    int nv = 0, nt = 0, npts = 0;
+    long long launches = 0;
+
+    // ---- far field (FP32): static geometry -----------------------------
+    DBuf<float4> d_pt;   // [6nt]  point x, y, z, quadrature weight * area
+    DBuf<float4> d_tn;   // [nt]   outward normal, plane offset n.P0
+    DBuf<int4> d_tv;     // [nt]   vertex indices
+    // ---- far field: per-apply workspace ----------------------------------
+    DBuf<float4> d_sA, d_sB;  // [6nt] source points: (y, psi.re), (psi.im, phi.re, phi.im, 0)
+    DBuf<float4> d_sC;        // [nt]  c_sigma components 0, 1 (complex)
+    DBuf<float2> d_sC2;       // [nt]  c_sigma component 2
+    DBuf<float> d_part;       // [nsplit][6nt][10] per test point partial sums
+    int nsplit = 1;
+    // ---- FP64 per-triangle geometry: area, normal, curls of the hat functions
+    DBuf<double> d_tgeo;      // [nt][16]
+    // ---- near field CSR (vertex pairs of touching triangles), FP64 --------
+    long long near_pairs = 0;
+    int near_nnz = 0;
+    DBuf<int> d_nr_ptr, d_nr_col;
+    DBuf<double2> d_nr_val;   // [nnz][4]: blocks (1,1) (1,2) (2,1) (2,2)
+    // ---- sparse mass / stiffness (1-ring CSR), FP64 ----------------------
+    int ms_nnz = 0;
+    DBuf<int> d_ms_ptr, d_ms_col;
+    DBuf<double> d_M, d_S;
+    // ---- dense FP64 system (OSRC_FP64_DENSE) -------------------------------
+    DBuf<double2> d_dense;    // [2nv][2nv] row-major
+    // ---- OSRC constants (Sec. 2.6) -------------------------------------------
+    double k_osrc = 0.0;
+    double2 k_eps{};
+    double2 C0{}, g0{};
+    std::vector<double2> A, B, g;
+    // ---- inner solver workspace ------------------------------------------------
+    DBuf<double2> d_kry;      // batched CG/COCG vectors
+    DBuf<double2> d_kry_rhs;  // right-hand sides of the shifted systems
+    DBuf<double2> d_tmp2;     // [2][2nv] temporaries
+    DBuf<int> d_kry_stat;     // per-system iteration count / status
+    DBuf<double> d_kry_res;   // per-system final relative residual
+    int inner_last_max = 0;
+    // ---- GMRES workspace --------------------------------------------------------
+    DBuf<double2> d_basis;    // (maxit+1) x 2nv
+    int basis_cap = 0;
+    DBuf<double2> d_h;        // Hessenberg (maxit+1) x maxit, column-major
+    DBuf<double2> d_givens;   // cs (as .x), sn, g vectors
+    DBuf<double> d_scalars;   // reduction scratch
+    DBuf<double2> d_w, d_y, d_x1, d_b1, d_cvec;  // 2nv vectors
+    DBuf<double> h_pinned_dummy;
+    double *h_res = nullptr;  // pinned host word for the residual estimate
+};
+
+// ---------------------------------------------------------------------------
+// kernel launchers (each returns an osrc_status; all work on `st`)
+// ---------------------------------------------------------------------------
+// far field (k_far.cu)
+int far_setup_geometry(osrc_problem *pb, cudaStream_t st);
+int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStream_t st);
+
+// near field (k_near.cu)
+int near_build(osrc_problem *pb, const std::vector<NearPair> &pairs,
+               const std::vector<int> &contrib_ptr, const std::vector<int> &contrib_idx,
+               cudaStream_t st);
+
+// dense FP64 (k_near.cu)
+int dense_assemble(osrc_problem *pb, cudaStream_t st);
+int dense_apply(osrc_problem *pb, const double2 *x, double2 *y, cudaStream_t st);
+
+// sparse M, S and the inner solvers (k_sparse.cu)
+int ms_build(osrc_problem *pb, const std::vector<int> &contrib_ptr,
+             const std::vector<int> &contrib_idx, cudaStream_t st);
+int mass_solve(osrc_problem *pb, const double2 *x, double2 *y, cudaStream_t st);
+int osrc_precond(osrc_problem *pb, const double2 *x, double2 *y, cudaStream_t st);
+
+// GMRES helpers (k_gmres.cu)
+int vec_dots_conj(osrc_problem *pb, const double2 *V, int nvec, const double2 *w, int n,
+                  double2 *out, cudaStream_t st);
+int vec_update(osrc_problem *pb, const double2 *V, int nvec, const double2 *h, double2 *w,
+               int n, cudaStream_t st);
+int vec_norm(osrc_problem *pb, const double2 *w, int n, double *out, cudaStream_t st);
+int vec_scale_copy(osrc_problem *pb, const double2 *w, const double *nrm, double2 *out,
+                   int n, cudaStream_t st);
+int gmres_givens(osrc_problem *pb, int j, int ldh, double2 *H, double2 *gv, double *res_out,
+                 double beta_norm_for_rel, cudaStream_t st);
+int gmres_finish(osrc_problem *pb, int j, int ldh, const double2 *H, const double2 *gv,
+                 const double2 *V, double2 *x, int n, cudaStream_t st);
+int vec_axpby(osrc_problem *pb, double2 a, const double2 *x, double2 b, const double2 *y,
+              double2 *out, int n, cudaStream_t st);
+
+// right-hand sides (k_rhs.cu)
+int rhs_build(osrc_problem *pb, int kind, const double *src3, double2 *b, cudaStream_t st);

@@ -1,0 +1,82 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every symbol that include/osrc_pmchwt.h declares, and rejects invalid meshes
+on the host (osrc_mesh_validate does no device work)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2104_04609_gb300 import build as libbuild
+    from paper_2104_04609_gb300 import binding
+
+    libbuild.build()
+    return binding.lib()
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "osrc_pmchwt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(osrc_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_symbols_exported(lib):
+    from paper_2104_04609_gb300 import binding
+
+    names = _declared_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in binding.SIGNATURES, f"binding misses {n}"
+
+
+def test_status_strings(lib):
+    from paper_2104_04609_gb300 import binding as B
+
+    assert B.osrc_status_string(0) == "OSRC_OK"
+    assert B.osrc_status_string(4) == "OSRC_NOT_CONVERGED"
+    assert B.osrc_status_string(99) == "OSRC_UNKNOWN_STATUS"
+
+
+def test_params_default(lib):
+    from paper_2104_04609_gb300 import binding as B
+
+    p = B.osrc_params_default()
+    assert p.n_pade == 4 and abs(p.theta - np.pi / 3) < 1e-15 and p.osrc_side == 1
+    assert p.inner_tol <= 1e-8
+
+
+def test_mesh_validation(lib):
+    from paper_2104_04609_gb300 import binding as B
+    from paper_2104_04609_gb300.inputs import icosphere
+
+    v, t = icosphere(1)
+    assert B.osrc_mesh_validate(v, t) == B.OSRC_OK
+    bad = t.copy(); bad[0, 0] = v.shape[0]            # index out of range
+    assert B.osrc_mesh_validate(v, bad) == B.OSRC_INVALID_ARG
+    bad = t.copy(); bad[0, 1] = bad[0, 0]             # repeated vertex
+    assert B.osrc_mesh_validate(v, bad) == B.OSRC_INVALID_ARG
+    bad = t.copy(); bad[3] = bad[3][[0, 2, 1]]        # flipped orientation
+    assert B.osrc_mesh_validate(v, bad) == B.OSRC_INVALID_ARG
+    assert B.osrc_mesh_validate(v, t[:-1]) == B.OSRC_INVALID_ARG   # open surface
+    vv = v.copy(); vv[5] = np.nan
+    assert B.osrc_mesh_validate(vv, t) == B.OSRC_INVALID_ARG
+    vv = v.copy(); a, b, c = t[0]; vv[c] = vv[a] * 0.5 + vv[b] * 0.5   # zero area
+    assert B.osrc_mesh_validate(vv, t) == B.OSRC_INVALID_ARG
+    assert B.osrc_mesh_validate(np.zeros((0, 3)), np.zeros((0, 3), np.int32)) == B.OSRC_INVALID_ARG
+    vx = np.vstack([v, [[5.0, 5.0, 5.0]]])            # unreferenced vertex
+    assert B.osrc_mesh_validate(vx, t) == B.OSRC_INVALID_ARG
+
+
+def test_input_meshes_valid(lib):
+    from paper_2104_04609_gb300 import binding as B
+    from paper_2104_04609_gb300.inputs import ellipsoid, icosphere, bumpy_ellipsoid
+
+    for v, t in (icosphere(3), ellipsoid(500), bumpy_ellipsoid(800)):
+        assert B.osrc_mesh_validate(v, t) == B.OSRC_OK
+        assert t.shape[0] == 2 * v.shape[0] - 4
