@@ -1,0 +1,427 @@
+#!/usr/bin/env python
+"""Benchmark: OSRC-preconditioned PMCHWT solves/s on one GB300.
+
+Workload (one step = one solve): unit sphere, level-5 icosphere (10242
+vertices, 20480 flat triangles), k_ext = 20, k_int = 26, rho_int/rho_ext =
+1.5, unit plane wave along +z (other directions on other ranks), P1 Galerkin,
+FP32 matrix-free far field + FP64 Sauter-Schwab near-field CSR, OSRC with
+N_Pade = 4 and theta = pi/3 (interior wavenumber), GMRES without restart to a
+preconditioned relative residual of 1e-5.  The right-hand side is resident
+in HBM when the timed region starts; the problem set-up (near field, mass and
+stiffness matrices, Pade constants) is resident state built before it.  L2
+is flushed (a 512 MiB buffer is written) before every timed solve.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on a bounded row sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "sphere10242"
+METRIC = "OSRC-PMCHWT solves/s to 1e-5 residual"
+UNIT = "solves/s"
+TOL = 1e-5
+# nominal FP32 flops of one far-field point pair evaluated at both wavenumbers
+FLOPS_PER_PAIR = 176
+# GMRES iterations of this workload (measured on the GPU path; the oracle's
+# unrestarted GMRES needs the same count within +-2 at smaller sizes): used
+# to turn the oracle's sampled matvec rate into solves/s
+REF_ITERATIONS = 47
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; no data-path collective)
+# --------------------------------------------------------------------------
+class Dist:
+    def __init__(self, want_cuda=True):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+
+            backend = "nccl" if (want_cuda and torch.cuda.is_available()) else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg is not None:
+            self.pg.barrier()
+
+    def max(self, v):
+        if self.pg is None:
+            return v
+        import torch
+
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v):
+        if self.pg is None:
+            return v
+        import torch
+
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpus):
+        self.gpus = gpus
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    idx = int(parts[0])
+                except ValueError:
+                    continue
+                if idx not in self.gpus:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    pass
+                for n, v in zip(names[1:], parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p))
+        except Exception:
+            return None
+    return None
+
+
+def run_ours(args, D):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    if D.rank == 0 or D.world == 1:
+        __graft_entry__.build()
+    D.barrier()
+    from paper_2104_04609_gb300 import binding as B
+    from paper_2104_04609_gb300.inputs import plane_wave_dirs, workload
+
+    torch.cuda.set_device(D.local)
+    dev = torch.device("cuda", D.local)
+    W = workload(WORKLOAD)
+    t_setup = time.perf_counter()
+    S = B.Solver(W["verts"], W["tris"], W["k_ext"], W["k_int"], W["rho_ratio"], device=D.local)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    d = np.array([[0.0, 0.0, 1.0]]) if D.rank == 0 else plane_wave_dirs(1, seed=100 + D.rank)
+    b = S.rhs_planewave(d)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    for _ in range(args.warmup):
+        x, info = S.solve(b, tol=TOL, maxit=1000)
+    torch.cuda.synchronize()
+
+    B.osrc_profile_enable(S.pb, True)
+    launches0 = S.launches()
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clocks = ClockSampler(list(range(max(1, D.world))) if D.rank == 0 else [])
+    D.barrier()
+    torch.cuda.synchronize()
+    if D.rank == 0:
+        clocks.start()
+    infos = []
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        x, info = S.solve(b, tol=TOL, maxit=1000)
+        evs[k][1].record(stream)
+        infos.append(info.as_dict())
+    torch.cuda.synchronize()
+    D.barrier()
+    clk = clocks.stop() if D.rank == 0 else None
+    launches = S.launches() - launches0
+    far_n, far_ms = B.osrc_far_kernel_stats(S.pb)
+    B.osrc_profile_enable(S.pb, False)
+    step_ms = [a.elapsed_time(e) for a, e in evs]
+    total_ms = D.max(sum(step_ms))
+    solves = D.sum(args.steps)
+    value = solves / (total_ms / 1000.0)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    n2 = 2 * S.nv
+    hb = torch.empty((1, n2), dtype=torch.complex128, pin_memory=True)
+    hb.copy_(b.cpu())
+    hx = torch.empty((1, n2), dtype=torch.complex128, pin_memory=True)
+    hbn, hxn = hb.numpy(), hx.numpy()
+    B.osrc_gmres_solve(S.pb, hbn, hxn, 1, TOL, 1000, host_buffers=True)
+    D.barrier()
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.osrc_gmres_solve(S.pb, hbn, hxn, 1, TOL, 1000, host_buffers=True)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_total = D.max(sum(e2e_t))
+    e2e_value = solves / e2e_total
+    sol_diff = float(np.linalg.norm(hxn.ravel() - x.cpu().numpy().ravel()) /
+                     np.linalg.norm(x.cpu().numpy().ravel()))
+
+    far_pairs = B.osrc_far_pairs(S.pb)
+    far_avg_ms = far_ms / max(far_n, 1)
+    achieved = FLOPS_PER_PAIR * far_pairs / (far_avg_ms * 1e-3) / 1e12
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    mean_info = {k: infos[-1][k] for k in ("iterations", "precond_residual", "true_residual",
+                                           "inner_iterations_max")}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": D.world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": "sphere10242: unit sphere, level-5 icosphere, 10242 vertices / 20480 "
+                        "triangles, k_ext 20, k_int 26, rho ratio 1.5, plane wave +z",
+            "path": "FP32 matrix-free far field + FP64 Sauter-Schwab near CSR (n_ss 4), "
+                    "FP64 CG mass solve and batched COCG OSRC (N_Pade 4, theta pi/3, tol 1e-10), "
+                    "FP64 CGS2 GMRES without restart",
+            "tol": TOL, "rhs_per_rank": 1, "l2": "flushed (512 MiB write) before every step",
+            "setup_s": round(t_setup, 3), "parallelism": f"replicas x{D.world}",
+            **mean_info,
+        },
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n2 * 16,
+                "d2h_bytes_per_step": n2 * 16, "solution_rel_diff_vs_device_run": sol_diff},
+        "gpu_launches": int(launches),
+        "roofline": {
+            "bound": "alu", "kernel": "far_kernel",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None,
+            "flops_per_unit": FLOPS_PER_PAIR, "units_per_launch": far_pairs,
+            "avg_launch_ms": far_avg_ms, "launches_timed": far_n,
+            "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
+                          f"{sm_max:.0f} MHz (derived; no FP32 entry in MEASURED_PEAKS.json)",
+        },
+    }
+    peaks = measured_peaks()
+    if peaks is not None:
+        out["measured_peaks_file"] = True
+    S.close()
+    return out, (infos[-1]["iterations"] if infos else REF_ITERATIONS)
+
+
+# --------------------------------------------------------------------------
+# oracle timing (CPU baseline and the reference arm)
+# --------------------------------------------------------------------------
+class OracleTimer:
+    """Times the FP64 CPU oracle on rows of the same matvec: each row of the
+    permuted PMCHWT matrix at both wavenumbers, assembled and applied."""
+
+    def __init__(self):
+        import numpy as np
+
+        import oracle as O
+        from paper_2104_04609_gb300.inputs import workload
+
+        self.O = O
+        self.W = workload(WORKLOAD)
+        self.nv = self.W["verts"].shape[0]
+        rng = np.random.default_rng(0)
+        self.x = rng.standard_normal(2 * self.nv) + 1j * rng.standard_normal(2 * self.nv)
+        self.rng = np.random.default_rng(1)
+        self.threads = O.lib().orc_num_threads()
+        self.t_osrc = None
+
+    def rows(self, nrows):
+        W = self.W
+        rows = self.rng.choice(self.nv, nrows, replace=False)
+        t0 = time.perf_counter()
+        R1, R2 = self.O.pmchwt_rows(W["verts"], W["tris"], W["k_ext"], W["k_int"],
+                                    W["rho_ratio"], rows, nss=4)
+        _ = R1 @ self.x, R2 @ self.x
+        return time.perf_counter() - t0
+
+    def osrc_time(self):
+        """One strong-form mass solve + OSRC apply with the oracle's sparse LU."""
+        if self.t_osrc is None:
+            import numpy as np
+
+            W = self.W
+            O = self.O
+            M, Sm = O.mass_stiffness(W["verts"], W["tris"])
+            R = O.mean_edge_length(W["verts"], W["tris"])
+            ke = O.damped_wavenumber(W["k_int"], R)
+            solver = O._ShiftedSolver(M, Sm)
+            u = self.x
+            O.osrc_apply(M, Sm, u[: self.nv], u[self.nv:], W["k_int"], ke, 4, math.pi / 3, solver)
+            t0 = time.perf_counter()
+            y = O.strong_apply(M, u)
+            O.osrc_apply(M, Sm, y[: self.nv], y[self.nv:], W["k_int"], ke, 4, math.pi / 3, solver)
+            self.t_osrc = time.perf_counter() - t0
+        return self.t_osrc
+
+    def calibrate(self, seconds):
+        t = self.rows(8)
+        per_row = t / 8
+        return max(8, min(self.nv, int(seconds / max(per_row, 1e-6))))
+
+    def solves_per_s(self, nrows, t_rows, iterations):
+        t_matvec = t_rows / nrows * self.nv
+        t_solve = (iterations + 1) * t_matvec + iterations * self.osrc_time()
+        return 1.0 / t_solve
+
+
+def cpu_baseline(iterations, seconds):
+    T = OracleTimer()
+    n = T.calibrate(seconds)
+    t = T.rows(n)
+    v = T.solves_per_s(n, t, iterations)
+    return {"value": v, "unit": UNIT, "cores": T.threads, "kind": "oracle",
+            "sample": f"{n} of {T.nv} rows of one permuted-PMCHWT matvec (both wavenumbers, "
+                      f"6x6 rule + Sauter-Schwab n_ss 4) in {t:.1f} s, plus one sparse-LU "
+                      f"mass solve + OSRC apply; scaled to (iterations + 1) matvecs and "
+                      f"{iterations} preconditioner applies per solve ({iterations} GMRES "
+                      f"iterations)"}
+
+
+def run_reference(args, D):
+    if D.world > 1 and D.rank != 0:
+        return None
+    import __graft_entry__
+
+    from oracle import build as orcbuild
+
+    orcbuild.build()
+    T = OracleTimer()
+    per_step = max(1.0, min(args.cpu_seconds, 20.0))
+    n = T.calibrate(per_step)
+    for _ in range(args.warmup):
+        T.rows(max(8, n // 8))
+    times = [T.rows(n) for _ in range(args.steps)]
+    vals = [T.solves_per_s(n, t, REF_ITERATIONS) for t in times]
+    value = statistics.mean(vals)
+    ms_per_step = 1000.0 / value
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": D.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": "sphere10242: unit sphere, level-5 icosphere, 10242 vertices / "
+                               "20480 triangles, k_ext 20, k_int 26, rho ratio 1.5, plane wave +z",
+                   "path": "FP64 CPU oracle (C + OpenMP, numpy/scipy)", "tol": TOL},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": T.threads, "kind": "oracle",
+                         "sample": f"each step: {n} of {T.nv} rows of one matvec, scaled to "
+                                   f"{REF_ITERATIONS + 1} matvecs + {REF_ITERATIONS} "
+                                   f"preconditioner applies per solve"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        D = Dist(want_cuda=False)
+        out = run_reference(args, D)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        D.close()
+        return
+    D = Dist(want_cuda=True)
+    out, iters = run_ours(args, D)
+    if D.rank == 0:
+        if D.world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(iters, args.cpu_seconds)
+        print(json.dumps(out), flush=True)
+    D.close()
+
+
+if __name__ == "__main__":
+    main()

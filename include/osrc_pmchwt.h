@@ -189,6 +189,16 @@ int osrc_gmres_solve(osrc_problem *pb, const void *b, void *x, int nrhs, double 
 /* ---- introspection ---------------------------------------------------------------- */
 /* Number of kernel launches the library has issued on this problem so far. */
 long long osrc_launch_count(const osrc_problem *pb);
+/* Enables (on != 0) or disables CUDA-event timing of the far-field kernel
+ * launches of this problem; enabling resets the statistics. */
+int osrc_profile_enable(osrc_problem *pb, int on);
+/* Far-field kernel statistics since profiling was enabled: number of
+ * launches and their summed device time in ms (events recorded on the
+ * launching stream around each launch).  Waits for the last timed launch. */
+int osrc_far_kernel_stats(osrc_problem *pb, long long *launches, double *total_ms);
+/* Number of far-field point pairs one apply evaluates: 36 x (number of
+ * triangle pairs sharing no vertex). */
+long long osrc_far_pairs(const osrc_problem *pb);
 /* Number of touching triangle pairs (near-field pairs) and near CSR blocks. */
 long long osrc_near_pairs(const osrc_problem *pb);
 long long osrc_near_nnz(const osrc_problem *pb);

@@ -96,6 +96,10 @@ SIGNATURES = {
                                         ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(osrc_solve_info), _VP]),
     "osrc_launch_count": (ctypes.c_longlong, [_VP]),
+    "osrc_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "osrc_far_kernel_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong),
+                                             ctypes.POINTER(ctypes.c_double)]),
+    "osrc_far_pairs": (ctypes.c_longlong, [_VP]),
     "osrc_near_pairs": (ctypes.c_longlong, [_VP]),
     "osrc_near_nnz": (ctypes.c_longlong, [_VP]),
 }
@@ -271,6 +275,22 @@ def osrc_gmres_solve(pb, b, x, nrhs=1, tol=1e-5, maxit=500, host_buffers=False,
 
 def osrc_launch_count(pb):
     return lib().osrc_launch_count(pb)
+
+
+def osrc_profile_enable(pb, on=True):
+    _check(lib().osrc_profile_enable(pb, 1 if on else 0), "osrc_profile_enable")
+
+
+def osrc_far_kernel_stats(pb):
+    n = ctypes.c_longlong()
+    ms = ctypes.c_double()
+    _check(lib().osrc_far_kernel_stats(pb, ctypes.byref(n), ctypes.byref(ms)),
+           "osrc_far_kernel_stats")
+    return n.value, ms.value
+
+
+def osrc_far_pairs(pb):
+    return lib().osrc_far_pairs(pb)
 
 
 def osrc_near_pairs(pb):

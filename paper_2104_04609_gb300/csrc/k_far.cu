@@ -362,6 +362,18 @@ int far_setup_geometry(osrc_problem *pb, cudaStream_t st) {
     return OSRC_OK;
 }
 
+// Adds the duration of the last timed far-kernel launch to the statistics.
+int far_prof_collect(osrc_problem *pb) {
+    if (!pb->prof_pending) return OSRC_OK;
+    OSRC_CK(cudaEventSynchronize(pb->prof_ev[1]));
+    float ms = 0.f;
+    OSRC_CK(cudaEventElapsedTime(&ms, pb->prof_ev[0], pb->prof_ev[1]));
+    pb->prof_ms += ms;
+    pb->prof_launches++;
+    pb->prof_pending = false;
+    return OSRC_OK;
+}
+
 int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStream_t st) {
     osrc_mesh *m = pb->mesh;
     const int nt = pb->nt, nv = pb->nv, npts = pb->npts;
@@ -386,10 +398,18 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
         const int ns = pb->nsplit;
         const int tps = (nt + ns - 1) / ns;
         dim3 grid((npts + FAR_THREADS - 1) / FAR_THREADS, ns);
+        if (pb->prof_on) {
+            OSRC_TRY(far_prof_collect(pb));
+            OSRC_CK(cudaEventRecord(pb->prof_ev[0], st));
+        }
         far_kernel<<<grid, FAR_THREADS, 0, st>>>(pb->d_pt.p, pb->d_tn.p, pb->d_tv.p, pb->d_sA.p,
                                                  pb->d_sB.p, pb->d_sC.p, pb->d_sC2.p, nt, npts,
                                                  tps, c, pb->d_part.p);
         pb->launches++;
+        if (pb->prof_on) {
+            OSRC_CK(cudaEventRecord(pb->prof_ev[1], st));
+            pb->prof_pending = true;
+        }
     }
     gather_kernel<<<(nv + 127) / 128, 128, 0, st>>>(
         nv, npts, pb->nsplit, m->d_vt_ptr.p, m->d_vt_idx.p, pb->d_tgeo.p, pb->d_part.p, use_far,

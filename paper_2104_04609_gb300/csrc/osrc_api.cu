@@ -445,11 +445,38 @@ extern "C" int osrc_problem_create(osrc_mesh *mesh, const osrc_params *prm, osrc
 extern "C" void osrc_problem_destroy(osrc_problem *pb) {
     if (!pb) return;
     if (pb->h_res) cudaFreeHost(pb->h_res);
+    for (auto &e : pb->prof_ev)
+        if (e) cudaEventDestroy(e);
     delete pb;
 }
 
 extern "C" int osrc_problem_nv(const osrc_problem *pb) { return pb ? pb->nv : 0; }
 extern "C" long long osrc_launch_count(const osrc_problem *pb) { return pb ? pb->launches : 0; }
+extern "C" int osrc_profile_enable(osrc_problem *pb, int on) {
+    if (!pb) return OSRC_INVALID_ARG;
+    OSRC_CK(cudaSetDevice(pb->mesh->ctx->device));
+    for (auto &e : pb->prof_ev)
+        if (!e) OSRC_CK(cudaEventCreate(&e));
+    if (pb->prof_pending) OSRC_TRY(far_prof_collect(pb));
+    pb->prof_on = on != 0;
+    pb->prof_launches = 0;
+    pb->prof_ms = 0.0;
+    return OSRC_OK;
+}
+
+extern "C" int osrc_far_kernel_stats(osrc_problem *pb, long long *launches, double *total_ms) {
+    if (!pb || !launches || !total_ms) return OSRC_INVALID_ARG;
+    OSRC_CK(cudaSetDevice(pb->mesh->ctx->device));
+    OSRC_TRY(far_prof_collect(pb));
+    *launches = pb->prof_launches;
+    *total_ms = pb->prof_ms;
+    return OSRC_OK;
+}
+
+extern "C" long long osrc_far_pairs(const osrc_problem *pb) {
+    return pb ? 36LL * ((long long)pb->nt * pb->nt - pb->near_pairs) : 0;
+}
+
 extern "C" long long osrc_near_pairs(const osrc_problem *pb) { return pb ? pb->near_pairs : 0; }
 extern "C" long long osrc_near_nnz(const osrc_problem *pb) { return pb ? pb->near_nnz : 0; }
 

@@ -149,7 +149,14 @@ struct osrc_problem {
     DBuf<double2> d_w, d_y, d_x1, d_b1, d_cvec;  // 2nv vectors
     DBuf<double> h_pinned_dummy;
     double *h_res = nullptr;  // pinned host word for the residual estimate
+    // ---- far-kernel event timing -------------------------------------------------
+    bool prof_on = false, prof_pending = false;
+    cudaEvent_t prof_ev[2] = {nullptr, nullptr};
+    long long prof_launches = 0;
+    double prof_ms = 0.0;
 };
+
+int far_prof_collect(osrc_problem *pb);
 
 // ---------------------------------------------------------------------------
 // kernel launchers (each returns an osrc_status; all work on `st`)
