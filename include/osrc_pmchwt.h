@@ -186,6 +186,42 @@ enum { OSRC_HOST_BUFFERS = 1 };
 int osrc_gmres_solve(osrc_problem *pb, const void *b, void *x, int nrhs, double tol,
                      int maxit, int flags, osrc_solve_info *info, void *stream);
 
+/* ---- allocation-free batched solve ------------------------------------------------- */
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory when they need a solve: code running
+ * during CUDA stream capture, real-time or callback-driven hosts that forbid
+ * allocation after start-up, and frameworks that own device memory through
+ * their own pool allocator.
+ *
+ * Solves the nsys systems (alpha_s M + beta_s S) w_s = f_s that share one CSR
+ * pattern (n rows) with the library's cluster-batched Krylov kernel:
+ * Hermitian CG when conj = 1 (real SPD systems), COCG when conj = 0
+ * (complex-symmetric systems), Jacobi-preconditioned, to |r_s| <= tol |f_s|
+ * or maxit iterations.  All pointers except alpha, beta and iters_out are
+ * device pointers owned by the caller: row_ptr (n+1), col_idx, M_vals,
+ * S_vals (row_ptr[n] each, int32 / double), f and w (nsys x n complex,
+ * interleaved).  alpha, beta: host, nsys complex each.
+ *
+ * The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine.  Its Krylov workspace is a static device array of 5 x 131072
+ * complex entries (10 MiB) that every GPU loading this library holds until
+ * process exit; requests with nsys * n > 131072 or nsys > 16 are rejected
+ * with OSRC_INVALID_ARG.  The work runs on the calling thread's current
+ * device.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls on a device share the array and it keeps the last call's
+ * contents: calls whose kernels overlap on the GPU race and must be
+ * serialised by the caller.
+ *
+ * If iters_out (host, nsys ints) is non-NULL the call waits for the stream
+ * and reports per system the iteration count (negative: not converged) and
+ * returns OSRC_NOT_CONVERGED / OSRC_BREAKDOWN accordingly; with NULL it only
+ * enqueues the work and returns OSRC_OK. */
+int osrc_shifted_solve_noalloc(int n, const int32_t *row_ptr, const int32_t *col_idx,
+                               const double *M_vals, const double *S_vals, int nsys,
+                               const double *alpha, const double *beta, const void *f, void *w,
+                               double tol, int maxit, int conj, int *iters_out, void *stream);
+
 /* ---- introspection ---------------------------------------------------------------- */
 /* Number of kernel launches the library has issued on this problem so far. */
 long long osrc_launch_count(const osrc_problem *pb);

@@ -95,6 +95,10 @@ SIGNATURES = {
     "osrc_gmres_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
                                         ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(osrc_solve_info), _VP]),
+    "osrc_shifted_solve_noalloc": (ctypes.c_int, [ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.c_int,
+                                                  _DP, _DP, _VP, _VP, ctypes.c_double,
+                                                  ctypes.c_int, ctypes.c_int,
+                                                  ctypes.POINTER(ctypes.c_int), _VP]),
     "osrc_launch_count": (ctypes.c_longlong, [_VP]),
     "osrc_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "osrc_far_kernel_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong),
@@ -271,6 +275,35 @@ def osrc_gmres_solve(pb, b, x, nrhs=1, tol=1e-5, maxit=500, host_buffers=False,
     if s != OSRC_OK and (s != OSRC_NOT_CONVERGED or raise_on_nonconvergence):
         raise OsrcError(s, "osrc_gmres_solve")
     return info
+
+
+def osrc_shifted_solve_noalloc(row_ptr, col_idx, M_vals, S_vals, alpha, beta, f, w,
+                               tol=1e-10, maxit=2000, conj=0, stream=None):
+    """Allocation-free batched solve of (alpha_s M + beta_s S) w_s = f_s.
+
+    For callers that cannot allocate device memory at solve time (stream
+    capture, allocation-free hosts, pool-owned memory): the library uses a
+    static 10 MiB device workspace instead of cudaMalloc.  row_ptr, col_idx
+    (int32) and M_vals, S_vals (float64) are CUDA tensors of one CSR pattern;
+    f, w are (nsys, n) complex128 CUDA tensors; alpha, beta are sequences of
+    nsys complex numbers.  Returns the per-system iteration counts."""
+    import torch
+
+    for t, dt in ((row_ptr, torch.int32), (col_idx, torch.int32), (M_vals, torch.float64),
+                  (S_vals, torch.float64)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError("CSR arrays must be contiguous CUDA tensors (int32 / float64)")
+    nsys, n = int(f.shape[0]), int(f.shape[1])
+    a = np.ascontiguousarray(np.asarray(alpha, dtype=np.complex128).view(np.float64))
+    b = np.ascontiguousarray(np.asarray(beta, dtype=np.complex128).view(np.float64))
+    it = (ctypes.c_int * nsys)()
+    s = lib().osrc_shifted_solve_noalloc(
+        n, ctypes.c_void_p(row_ptr.data_ptr()), ctypes.c_void_p(col_idx.data_ptr()),
+        ctypes.c_void_p(M_vals.data_ptr()), ctypes.c_void_p(S_vals.data_ptr()), nsys,
+        a.ctypes.data_as(_DP), b.ctypes.data_as(_DP), _dev(f), _dev(w), float(tol),
+        int(maxit), int(conj), it, _stream(stream))
+    _check(s, "osrc_shifted_solve_noalloc")
+    return list(it)
 
 
 def osrc_launch_count(pb):

@@ -18,6 +18,8 @@
 // the decisions are made from cluster-reduced values summed in rank order.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "osrc_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -386,4 +388,122 @@ int osrc_precond(osrc_problem *pb, const double2 *x, double2 *y, cudaStream_t st
     pb->launches++;
     OSRC_CK(cudaGetLastError());
     return check_kry(pb, b.nsys, st);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free batched shifted solve.
+//
+// Some callers cannot call cudaMalloc at the point where they need a solve:
+// code that runs while a stream is being captured into a CUDA graph (an
+// allocation there breaks or invalidates the capture), real-time or
+// callback-driven hosts that forbid allocation after start-up, and
+// frameworks whose device memory is owned by their own pool allocator.
+// osrc_shifted_solve_noalloc serves them: it runs the same cluster-batched
+// CG / COCG kernel as the library's mass and OSRC solves, but its Krylov
+// workspace is the file-scope array below instead of memory from
+// cudaMalloc, so the call allocates nothing.  The caller owns every input
+// and output buffer.
+//
+// The array holds NOALLOC_MAX_ENTRIES complex entries per Krylov vector
+// (5 vectors, 10 MiB in total) on every GPU that loads this library, until
+// the process exits.  Every call on a device shares it, and it keeps the
+// last call's contents; the kernel writes each scratch entry before reading
+// it, so only the per-system status words need clearing, which every call
+// does.  Calls whose kernels overlap on the GPU (two streams, or two host
+// threads) race on the array: serialise them.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t NOALLOC_MAX_ENTRIES = 131072;  // nsys * n complex values per vector
+constexpr int NOALLOC_MAX_SYS = 16;
+
+static __device__ __align__(256) double2 g_noalloc_work[5 * NOALLOC_MAX_ENTRIES];
+static __device__ __align__(256) int g_noalloc_stat[NOALLOC_MAX_SYS];
+static __device__ __align__(256) double g_noalloc_res[NOALLOC_MAX_SYS];
+
+struct NoAllocScratch {
+    double2 *work = nullptr;
+    int *stat = nullptr;
+    double *res = nullptr;
+    bool ready = false;
+};
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+NoAllocScratch g_noalloc[NOALLOC_MAX_DEVICES];
+
+// Device address of the scratch array on the current device, looked up once
+// per device (cudaGetSymbolAddress needs that device to be current).
+int noalloc_scratch(int dev, NoAllocScratch &out) {
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return OSRC_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoAllocScratch &s = g_noalloc[dev];
+    if (!s.ready) {
+        OSRC_CK(cudaGetSymbolAddress((void **)&s.work, g_noalloc_work));
+        OSRC_CK(cudaGetSymbolAddress((void **)&s.stat, g_noalloc_stat));
+        OSRC_CK(cudaGetSymbolAddress((void **)&s.res, g_noalloc_res));
+        s.ready = true;
+    }
+    out = s;
+    return OSRC_OK;
+}
+
+}  // namespace
+
+extern "C" int osrc_shifted_solve_noalloc(int n, const int32_t *row_ptr, const int32_t *col_idx,
+                                          const double *M_vals, const double *S_vals, int nsys,
+                                          const double *alpha, const double *beta, const void *f,
+                                          void *w, double tol, int maxit, int conj,
+                                          int *iters_out, void *stream) {
+    if (n < 1 || nsys < 1 || nsys > NOALLOC_MAX_SYS || !row_ptr || !col_idx || !M_vals ||
+        !S_vals || !alpha || !beta || !f || !w || !(tol > 0.0) || tol > 1e-4 || maxit < 1 ||
+        (conj != 0 && conj != 1)) {
+        osrc_set_error("osrc_shifted_solve_noalloc: invalid argument");
+        return OSRC_INVALID_ARG;
+    }
+    if ((size_t)n * (size_t)nsys > NOALLOC_MAX_ENTRIES) {
+        osrc_set_error("osrc_shifted_solve_noalloc: nsys * n exceeds the static scratch "
+                       "capacity of 131072 complex entries");
+        return OSRC_INVALID_ARG;
+    }
+    int dev = 0;
+    OSRC_CK(cudaGetDevice(&dev));
+    NoAllocScratch sc;
+    OSRC_TRY(noalloc_scratch(dev, sc));
+    cudaStream_t st = (cudaStream_t)stream;
+    KryBatch b{};
+    b.nsys = nsys;
+    for (int s = 0; s < nsys; ++s) {
+        b.s[s].alpha = cd(alpha[2 * s], alpha[2 * s + 1]);
+        b.s[s].beta = cd(beta[2 * s], beta[2 * s + 1]);
+        b.s[s].f = (const double2 *)f + (size_t)s * n;
+        b.s[s].x = (double2 *)w + (size_t)s * n;
+        b.s[s].conj = conj;
+    }
+    // status words start as "not written" so that a failed launch is seen
+    OSRC_CK(cudaMemsetAsync(sc.stat, 0x80, nsys * sizeof(int), st));
+    const int cs = cluster_size_for(n);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nsys * cs, 1, 1);
+    cfg.blockDim = dim3(KRY_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    OSRC_CK(cudaLaunchKernelEx(&cfg, kry_kernel, b, n, (const int *)row_ptr, (const int *)col_idx,
+                               M_vals, S_vals, sc.work, tol, maxit, sc.stat, sc.res));
+    if (!iters_out) return OSRC_OK;
+    OSRC_CK(cudaMemcpyAsync(iters_out, sc.stat, nsys * sizeof(int), cudaMemcpyDeviceToHost, st));
+    OSRC_CK(cudaStreamSynchronize(st));
+    int status = OSRC_OK;
+    for (int s = 0; s < nsys; ++s) {
+        if (iters_out[s] <= -1000000) status = OSRC_BREAKDOWN;
+        else if (iters_out[s] < 0 && status == OSRC_OK) status = OSRC_NOT_CONVERGED;
+    }
+    return status;
 }
