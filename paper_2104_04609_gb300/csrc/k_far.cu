@@ -134,20 +134,90 @@ struct FarConst {
     float dk0, dk1;    // k0^2 and k1^2 / rho: weights of the D normal term
 };
 
-__device__ __forceinline__ void kahan_add(float &sum, float &comp, float v) {
-    const float y = v - comp;
-    const float t = sum + y;
-    comp = (t - sum) - y;
-    sum = t;
+// Accumulators of one test point: tile sums of u1, u2 (complex) and of the
+// curl vector A (3 complex), and the per-source-triangle sums T1 = sum_q Hs
+// phi_q, U = sum_q Gk phi_q, T3 = sum_q w_q Gd.
+struct PointAcc {
+    float u1r, u1i, u2r, u2i, axr, axi, ayr, ayi, azr, azi;
+    float t1r, t1i, ur, ui, t3r, t3i;
+};
+
+// e^{i k r}: for |k r| below a few hundred radians the MUFU sine/cosine
+// take the argument directly (their own reduction has the same FP32 rounding
+// as an explicit one); REDUCE folds k r / (2 pi) to [-1/2, 1/2] first.
+template <bool REDUCE>
+__device__ __forceinline__ void phasor(float r, float k, float krev, float &s, float &c) {
+    if (REDUCE) {
+        const float t = r * krev;
+        __sincosf(6.28318530717958647692f * (t - rintf(t)), &s, &c);
+    } else {
+        __sincosf(k * r, &s, &c);
+    }
 }
 
-// One thread per test point p (test triangle p / 6, rule point p % 6).
-// Output part[(split * 10 + c) * npts + p], c = u1 (re, im), u2 (re, im),
-// A (x re, x im, y re, y im, z re, z im):
+// One point pair (test point x, source point A/B), both wavenumbers.
+template <bool REDUCE>
+__device__ __forceinline__ void far_pair(const float4 &x, float xnx, const float4 &A,
+                                         const float4 &B, float ynx, float wq,
+                                         const FarConst &c, PointAcc &P) {
+    const float dx = x.x - A.x, dy = x.y - A.y, dz = x.z - A.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float ri = rsqrtf(r2);
+    const float r = r2 * ri;
+    const float ri3 = ri * ri * ri;
+    const float dnx = xnx - ynx;  // (x - y).n_x
+    float s0, c0, s1, c1;
+    phasor<REDUCE>(r, c.k0, c.k0r, s0, c0);
+    phasor<REDUCE>(r, c.k1, c.k1r, s1, c1);
+    const float kr0 = c.k0 * r, kr1 = c.k1 * r;
+    // G combinations (without 1/(4 pi)): V block (G0 + rho G1), D normal
+    // term (k0^2 G0 + k1^2/rho G1), D curl term (G0 + G1/rho)
+    const float gpr = (c0 + c.rho * c1) * ri, gpi = (s0 + c.rho * s1) * ri;
+    const float gkr = (c.dk0 * c0 + c.dk1 * c1) * ri, gki = (c.dk0 * s0 + c.dk1 * s1) * ri;
+    const float wr = wq * ri;
+    P.t3r += (c0 + c.irho * c1) * wr;
+    P.t3i += (s0 + c.irho * s1) * wr;
+    // H0 + H1 with H = e^{ikr} (i k r - 1) / r^3
+    const float hsr = (-c0 - kr0 * s0 - c1 - kr1 * s1) * ri3;
+    const float hsi = (kr0 * c0 - s0 + kr1 * c1 - s1) * ri3;
+    const float psr = A.w, psi = B.x, phr = B.y, phi = B.z;
+    P.u1r += gpr * psr - gpi * psi;
+    P.u1i += gpr * psi + gpi * psr;
+    P.t1r += hsr * phr - hsi * phi;
+    P.t1i += hsr * phi + hsi * phr;
+    const float hxr = hsr * dnx, hxi = hsi * dnx;
+    P.u2r += hxr * psr - hxi * psi;
+    P.u2i += hxr * psi + hxi * psr;
+    P.ur += gkr * phr - gki * phi;
+    P.ui += gkr * phi + gki * phr;
+}
+
+// Per (test point, source triangle) epilogue: the factors that are constant
+// over the source triangle.
+__device__ __forceinline__ void far_tri_epilogue(PointAcc &P, float xny, float nxny, const float4 &C,
+                                                 const float2 &C2) {
+    P.u1r += xny * P.t1r;
+    P.u1i += xny * P.t1i;
+    P.u2r -= nxny * P.ur;
+    P.u2i -= nxny * P.ui;
+    P.axr += P.t3r * C.x - P.t3i * C.y;
+    P.axi += P.t3r * C.y + P.t3i * C.x;
+    P.ayr += P.t3r * C.z - P.t3i * C.w;
+    P.ayi += P.t3r * C.w + P.t3i * C.z;
+    P.azr += P.t3r * C2.x - P.t3i * C2.y;
+    P.azi += P.t3r * C2.y + P.t3i * C2.x;
+}
+
+// One thread per pair of test points (2j, 2j+1) of test triangle 2j / 6; the
+// two points share every shared-memory load, the touching test, n_x.n_y and
+// y.n_x.  Output part[(split * 10 + c) * npts + p], c = u1 (re, im), u2 (re,
+// im), A (x re, x im, y re, y im, z re, z im):
 //   u1 = sum [ (G0 + rho G1) psi_q + (x.n_y - h_y)(H0 + H1) phi_q ]
 //   u2 = sum [ (H0 + H1)(x - y).n_x psi_q - (n_x.n_y)(k0^2 G0 + k1^2/rho G1) phi_q ]
 //   A  = sum_s (sum_q w_q (G0 + G1/rho)) c_s
 // with G, H here without the factor 1/(4 pi) (applied in the gather).
+// Sums run per 64-triangle tile, then tile sums are added to running sums.
+template <bool REDUCE>
 __global__ void __launch_bounds__(FAR_THREADS)
 far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ tn,
            const int4 *__restrict__ tv, const float4 *__restrict__ sA,
@@ -161,21 +231,23 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ tn,
     __shared__ float2 shC2[FAR_TS];
     __shared__ int4 shV[FAR_TS];
 
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int split = blockIdx.y;
     const int s_begin = split * tris_per_split;
     const int s_end = min(nt, s_begin + tris_per_split);
-    const bool active = p < npts;
-    const int tau = active ? p / 6 : 0;
-    const float4 xp = pt[active ? p : 0];
+    const bool active = 2 * j < npts;
+    const int p0 = active ? 2 * j : 0;
+    const int tau = p0 / 6;
+    const float4 xa = pt[p0], xb = pt[p0 + 1];
     const float4 n4 = tn[tau];
     const int4 vt = tv[tau];
-    const float nxx = n4.x, nxy = n4.y, nxz = n4.z;
+    const float xnxa = xa.x * n4.x + xa.y * n4.y + xa.z * n4.z;
+    const float xnxb = xb.x * n4.x + xb.y * n4.y + xb.z * n4.z;
     const float W1 = (float)kQw1, W2 = (float)kQw2;
 
-    float acc[10], cmp[10];
+    float run[20];
 #pragma unroll
-    for (int i = 0; i < 10; ++i) acc[i] = cmp[i] = 0.f;
+    for (int i = 0; i < 20; ++i) run[i] = 0.f;
 
     for (int t0 = s_begin; t0 < s_end; t0 += FAR_TS) {
         const int cnt = min(FAR_TS, s_end - t0);
@@ -192,8 +264,7 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ tn,
         }
         __syncthreads();
 
-        float u1r = 0.f, u1i = 0.f, u2r = 0.f, u2i = 0.f;
-        float axr = 0.f, axi = 0.f, ayr = 0.f, ayi = 0.f, azr = 0.f, azi = 0.f;
+        PointAcc Pa = {}, Pb = {};
         for (int s = 0; s < cnt; ++s) {
             const int4 vs = shV[s];
             const bool touch = (vs.x == vt.x) | (vs.x == vt.y) | (vs.x == vt.z) |
@@ -201,78 +272,38 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ tn,
                                (vs.z == vt.x) | (vs.z == vt.y) | (vs.z == vt.z);
             if (touch) continue;
             const float4 ns = shN[s];
-            const float xny = xp.x * ns.x + xp.y * ns.y + xp.z * ns.z - ns.w;
-            const float nxny = nxx * ns.x + nxy * ns.y + nxz * ns.z;
-            float t1r = 0.f, t1i = 0.f, ur = 0.f, ui = 0.f, t3r = 0.f, t3i = 0.f;
+            const float xnya = xa.x * ns.x + xa.y * ns.y + xa.z * ns.z - ns.w;
+            const float xnyb = xb.x * ns.x + xb.y * ns.y + xb.z * ns.z - ns.w;
+            const float nxny = n4.x * ns.x + n4.y * ns.y + n4.z * ns.z;
+            Pa.t1r = Pa.t1i = Pa.ur = Pa.ui = Pa.t3r = Pa.t3i = 0.f;
+            Pb.t1r = Pb.t1i = Pb.ur = Pb.ui = Pb.t3r = Pb.t3i = 0.f;
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
                 const float4 A = shA[6 * s + q];
                 const float4 B = shB[6 * s + q];
-                const float dx = xp.x - A.x, dy = xp.y - A.y, dz = xp.z - A.z;
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                const float ri = rsqrtf(r2);
-                const float r = r2 * ri;
-                const float ri3 = ri * ri * ri;
-                const float dnx = dx * nxx + dy * nxy + dz * nxz;
-                // e^{i k r}: reduce k r / (2 pi) to [-1/2, 1/2] revolutions first
-                float s0, c0, s1, c1;
-                {
-                    const float t = r * c.k0r;
-                    __sincosf(6.28318530717958647692f * (t - rintf(t)), &s0, &c0);
-                }
-                {
-                    const float t = r * c.k1r;
-                    __sincosf(6.28318530717958647692f * (t - rintf(t)), &s1, &c1);
-                }
-                const float kr0 = c.k0 * r, kr1 = c.k1 * r;
-                const float g0r = c0 * ri, g0i = s0 * ri;
-                const float g1r = c1 * ri, g1i = s1 * ri;
-                const float hsr = (-c0 - kr0 * s0 - c1 - kr1 * s1) * ri3;
-                const float hsi = (kr0 * c0 - s0 + kr1 * c1 - s1) * ri3;
-                const float gpr = g0r + c.rho * g1r, gpi = g0i + c.rho * g1i;
-                const float gdr = g0r + c.irho * g1r, gdi = g0i + c.irho * g1i;
-                const float gkr = c.dk0 * g0r + c.dk1 * g1r, gki = c.dk0 * g0i + c.dk1 * g1i;
-                const float psr = A.w, psi = B.x, phr = B.y, phi = B.z;
-                u1r += gpr * psr - gpi * psi;
-                u1i += gpr * psi + gpi * psr;
-                t1r += hsr * phr - hsi * phi;
-                t1i += hsr * phi + hsi * phr;
-                const float hxr = hsr * dnx, hxi = hsi * dnx;
-                u2r += hxr * psr - hxi * psi;
-                u2i += hxr * psi + hxi * psr;
-                ur += gkr * phr - gki * phi;
-                ui += gkr * phi + gki * phr;
+                const float ynx = A.x * n4.x + A.y * n4.y + A.z * n4.z;
                 const float wq = q < 3 ? W1 : W2;
-                t3r += gdr * wq;
-                t3i += gdi * wq;
+                far_pair<REDUCE>(xa, xnxa, A, B, ynx, wq, c, Pa);
+                far_pair<REDUCE>(xb, xnxb, A, B, ynx, wq, c, Pb);
             }
-            u1r += xny * t1r;
-            u1i += xny * t1i;
-            u2r -= nxny * ur;
-            u2i -= nxny * ui;
             const float4 C = shC[s];
             const float2 C2 = shC2[s];
-            axr += t3r * C.x - t3i * C.y;
-            axi += t3r * C.y + t3i * C.x;
-            ayr += t3r * C.z - t3i * C.w;
-            ayi += t3r * C.w + t3i * C.z;
-            azr += t3r * C2.x - t3i * C2.y;
-            azi += t3r * C2.y + t3i * C2.x;
+            far_tri_epilogue(Pa, xnya, nxny, C, C2);
+            far_tri_epilogue(Pb, xnyb, nxny, C, C2);
         }
-        kahan_add(acc[0], cmp[0], u1r);
-        kahan_add(acc[1], cmp[1], u1i);
-        kahan_add(acc[2], cmp[2], u2r);
-        kahan_add(acc[3], cmp[3], u2i);
-        kahan_add(acc[4], cmp[4], axr);
-        kahan_add(acc[5], cmp[5], axi);
-        kahan_add(acc[6], cmp[6], ayr);
-        kahan_add(acc[7], cmp[7], ayi);
-        kahan_add(acc[8], cmp[8], azr);
-        kahan_add(acc[9], cmp[9], azi);
+        run[0] += Pa.u1r; run[1] += Pa.u1i; run[2] += Pa.u2r; run[3] += Pa.u2i;
+        run[4] += Pa.axr; run[5] += Pa.axi; run[6] += Pa.ayr; run[7] += Pa.ayi;
+        run[8] += Pa.azr; run[9] += Pa.azi;
+        run[10] += Pb.u1r; run[11] += Pb.u1i; run[12] += Pb.u2r; run[13] += Pb.u2i;
+        run[14] += Pb.axr; run[15] += Pb.axi; run[16] += Pb.ayr; run[17] += Pb.ayi;
+        run[18] += Pb.azr; run[19] += Pb.azi;
     }
     if (active) {
 #pragma unroll
-        for (int i = 0; i < 10; ++i) part[((size_t)split * 10 + i) * npts + p] = acc[i];
+        for (int i = 0; i < 10; ++i) {
+            part[((size_t)split * 10 + i) * npts + p0] = run[i];
+            part[((size_t)split * 10 + i) * npts + p0 + 1] = run[10 + i];
+        }
     }
 }
 
@@ -349,15 +380,29 @@ int far_setup_geometry(osrc_problem *pb, cudaStream_t st) {
     // split the source range so that the grid covers the GPU several times
     int dev = m->ctx->device, sms = 0, per_sm = 0;
     OSRC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    OSRC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far_kernel, FAR_THREADS, 0));
+    OSRC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far_kernel<false>, FAR_THREADS, 0));
     if (per_sm < 1) per_sm = 1;
-    const int bx = (pb->npts + FAR_THREADS - 1) / FAR_THREADS;
+    const int bx = (pb->npts / 2 + FAR_THREADS - 1) / FAR_THREADS;
     const int slots = sms * per_sm;
     int ns = (4 * slots + bx - 1) / bx;
     const int max_ns = (nt + FAR_TS - 1) / FAR_TS;
     if (ns > max_ns) ns = max_ns;
     if (ns < 1) ns = 1;
     pb->nsplit = ns;
+    // largest phase k r over the mesh (bounding-box diagonal): beyond 64 pi
+    // radians the explicit reduction to [-1/2, 1/2] revolutions is used
+    {
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int i = 0; i < m->nv; ++i)
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = fmin(lo[d], m->verts[3 * i + d]);
+                hi[d] = fmax(hi[d], m->verts[3 * i + d]);
+            }
+        const double diag = sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                                 (hi[2] - lo[2]) * (hi[2] - lo[2]));
+        const double kmax = fmax(pb->p.k_ext, pb->p.k_int);
+        pb->far_reduce = kmax * diag > 64.0 * 3.14159265358979323846;
+    }
     OSRC_TRY(pb->d_part.alloc(m->ctx, (size_t)ns * 10 * pb->npts));
     return OSRC_OK;
 }
@@ -397,14 +442,19 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
         c.dk1 = (float)(k1 * k1 / rho);
         const int ns = pb->nsplit;
         const int tps = (nt + ns - 1) / ns;
-        dim3 grid((npts + FAR_THREADS - 1) / FAR_THREADS, ns);
+        dim3 grid((npts / 2 + FAR_THREADS - 1) / FAR_THREADS, ns);
         if (pb->prof_on) {
             OSRC_TRY(far_prof_collect(pb));
             OSRC_CK(cudaEventRecord(pb->prof_ev[0], st));
         }
-        far_kernel<<<grid, FAR_THREADS, 0, st>>>(pb->d_pt.p, pb->d_tn.p, pb->d_tv.p, pb->d_sA.p,
-                                                 pb->d_sB.p, pb->d_sC.p, pb->d_sC2.p, nt, npts,
-                                                 tps, c, pb->d_part.p);
+        if (pb->far_reduce)
+            far_kernel<true><<<grid, FAR_THREADS, 0, st>>>(pb->d_pt.p, pb->d_tn.p, pb->d_tv.p,
+                                                           pb->d_sA.p, pb->d_sB.p, pb->d_sC.p,
+                                                           pb->d_sC2.p, nt, npts, tps, c, pb->d_part.p);
+        else
+            far_kernel<false><<<grid, FAR_THREADS, 0, st>>>(pb->d_pt.p, pb->d_tn.p, pb->d_tv.p,
+                                                            pb->d_sA.p, pb->d_sB.p, pb->d_sC.p,
+                                                            pb->d_sC2.p, nt, npts, tps, c, pb->d_part.p);
         pb->launches++;
         if (pb->prof_on) {
             OSRC_CK(cudaEventRecord(pb->prof_ev[1], st));

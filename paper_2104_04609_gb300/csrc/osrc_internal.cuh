@@ -115,6 +115,7 @@ struct osrc_problem {
     DBuf<float2> d_sC2;       // [nt]  c_sigma component 2
     DBuf<float> d_part;       // [nsplit][6nt][10] per test point partial sums
     int nsplit = 1;
+    bool far_reduce = false;  // explicit phase reduction for large k r
     // ---- FP64 per-triangle geometry: area, normal, curls of the hat functions
     DBuf<double> d_tgeo;      // [nt][16]
     // ---- near field CSR (vertex pairs of touching triangles), FP64 --------

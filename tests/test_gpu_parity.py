@@ -78,6 +78,21 @@ def test_far_field_parity(B, small, small_ref):
         assert np.abs(y - ref).max() < 1e-5 * np.abs(ref).max()
 
 
+def test_far_field_parity_large_phase(B, small):
+    """k r up to ~250 rad: the kernel switches to its explicitly reduced
+    phase; FP32 phase error grows like |k r| 2^-24, hence 3e-5."""
+    v, t, S0 = small
+    k0, k1 = 40.0, 70.0
+    S = B.Solver(v, t, k0, k1, RHO)
+    try:
+        far = O.pmchwt_matrix(v, t, k0, k1, RHO, nss=S.params.n_ss, part=1)
+        x = _rand(2 * v.shape[0], 17)
+        y = _apply(B, S, x, part=B.OSRC_PART_FAR)
+        assert _rel(y, far @ x) < 3e-5
+    finally:
+        S.close()
+
+
 def test_near_field_parity(B, small, small_ref):
     v, t, S = small
     _, near, _, _ = small_ref
