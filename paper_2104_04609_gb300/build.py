@@ -16,6 +16,10 @@ LIB = os.path.join(OUT, "libosrc_pmchwt.so")
 SOURCES = ["osrc_api.cu", "k_far.cu", "k_near.cu", "k_sparse.cu", "k_gmres.cu", "k_rhs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+# per-file flags: the FP32 far-field kernel flushes FP32 subnormals (its
+# values are far from the subnormal range), which removes subnormal handling
+# around the MUFU reciprocal square root and sine / cosine
+FILE_FLAGS = {"k_far.cu": ["-ftz=true"]}
 
 
 def _nvcc():
@@ -27,7 +31,7 @@ def _nvcc():
 
 def _deps():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "osrc_internal.cuh"),
+    files += [os.path.abspath(__file__), os.path.join(CSRC, "osrc_internal.cuh"),
               os.path.join(os.path.dirname(HERE), "include", "osrc_pmchwt.h")]
     return files
 
@@ -42,7 +46,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *FILE_FLAGS.get(src, []), *extra, "-c",
+               os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -595,7 +595,6 @@ int ensure_gmres_workspace(osrc_problem *pb, int maxit) {
 int precond_matvec(osrc_problem *pb, const double2 *v, double2 *w, cudaStream_t st, PhaseTimer &tm,
                    double &ms_mv, double &ms_pc) {
     double2 *t1 = pb->d_tmp2.p;            // B v
-    double2 *t2 = pb->d_y.p;               // M^-1 B v
     if (tm.ok) cudaEventRecord(tm.ev[0], st);
     if (pb->p.precision == OSRC_FP64_DENSE) {
         OSRC_TRY(dense_apply(pb, v, t1, st));
@@ -603,8 +602,7 @@ int precond_matvec(osrc_problem *pb, const double2 *v, double2 *w, cudaStream_t 
         OSRC_TRY(far_apply(pb, v, t1, OSRC_PART_ALL, st));
     }
     if (tm.ok) cudaEventRecord(tm.ev[1], st);
-    OSRC_TRY(mass_solve(pb, t1, t2, st));
-    OSRC_TRY(osrc_precond(pb, t2, w, st));
+    OSRC_TRY(osrc_precond_fused(pb, t1, w, st));
     if (tm.ok) {
         cudaEventRecord(tm.ev[2], st);
         cudaEventSynchronize(tm.ev[2]);
@@ -624,8 +622,7 @@ int gmres_one(osrc_problem *pb, const double2 *b, double2 *x, double tol, int ma
     double2 *V = pb->d_basis.p, *H = pb->d_h.p, *gv = pb->d_givens.p;
     double *sc = pb->d_scalars.p;
     // c = P M^-1 b
-    OSRC_TRY(mass_solve(pb, b, pb->d_y.p, st));
-    OSRC_TRY(osrc_precond(pb, pb->d_y.p, pb->d_cvec.p, st));
+    OSRC_TRY(osrc_precond_fused(pb, b, pb->d_cvec.p, st));
     OSRC_TRY(vec_norm(pb, pb->d_cvec.p, n, sc, st));
     OSRC_CK(cudaMemcpyAsync(pb->h_res, sc, sizeof(double), cudaMemcpyDeviceToHost, st));
     OSRC_CK(cudaStreamSynchronize(st));

@@ -180,6 +180,7 @@ int ms_build(osrc_problem *pb, const std::vector<int> &contrib_ptr,
              const std::vector<int> &contrib_idx, cudaStream_t st);
 int mass_solve(osrc_problem *pb, const double2 *x, double2 *y, cudaStream_t st);
 int osrc_precond(osrc_problem *pb, const double2 *x, double2 *y, cudaStream_t st);
+int osrc_precond_fused(osrc_problem *pb, const double2 *y, double2 *z, cudaStream_t st);
 
 // GMRES helpers (k_gmres.cu)
 int vec_dots_conj(osrc_problem *pb, const double2 *V, int nvec, const double2 *w, int n,
