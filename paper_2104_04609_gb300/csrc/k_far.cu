@@ -87,13 +87,19 @@ __global__ void far_geom_kernel(const double *__restrict__ verts, const int *__r
     g[13] = g[14] = g[15] = 0.0;
 }
 
-// Source densities of one apply: psi_q = w_q |s| sum_b lambda_b(q) psi_b, the
-// same for phi, and c_s = |s| sum_b phi_b curl phi_b (complex 3-vector).
+// Source data of one apply, duplicated into (value, value) pairs so that
+// the far kernel's packed FP32 instructions (two test points per thread)
+// take them as operands without extra moves:
+//   sP0 = (-y.x, -y.x, -y.y, -y.y)   sP1 = (-y.z, -y.z, psi.re, psi.re)
+//   sP2 = (psi.im, psi.im, phi.re, phi.re)   sP3 = (phi.im, phi.im)
+// with psi_q = w_q |s| sum_b lambda_b(q) psi_b (the same for phi), and per
+// triangle c_s = |s| sum_b phi_b curl phi_b as sC[j] = (c_j.re, c_j.re,
+// c_j.im, c_j.im).
 __global__ void far_prep_kernel(const double2 *__restrict__ x, int nv, int nt,
                                 const int *__restrict__ tris, const float4 *__restrict__ pt,
-                                const double *__restrict__ tgeo, float4 *__restrict__ sA,
-                                float4 *__restrict__ sB, float4 *__restrict__ sC,
-                                float2 *__restrict__ sC2) {
+                                const double *__restrict__ tgeo, float4 *__restrict__ sP0,
+                                float4 *__restrict__ sP1, float4 *__restrict__ sP2,
+                                float2 *__restrict__ sP3, float4 *__restrict__ sC) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
     double2 ps[3], ph[3];
@@ -114,121 +120,129 @@ __global__ void far_prep_kernel(const double2 *__restrict__ x, int nv, int nt,
             f = cadd(f, cscale(ph[a], b[a]));
         }
         const float4 p = pt[6 * t + q];
-        sA[6 * t + q] = make_float4(p.x, p.y, p.z, (float)(W * s.x));
-        sB[6 * t + q] = make_float4((float)(W * s.y), (float)(W * f.x), (float)(W * f.y), 0.f);
+        const float psr = (float)(W * s.x), psi = (float)(W * s.y);
+        const float phr = (float)(W * f.x), phi = (float)(W * f.y);
+        const size_t k = 6 * (size_t)t + q;
+        sP0[k] = make_float4(-p.x, -p.x, -p.y, -p.y);
+        sP1[k] = make_float4(-p.z, -p.z, psr, psr);
+        sP2[k] = make_float4(psi, psi, phr, phr);
+        sP3[k] = make_float2(phi, phi);
     }
-    double2 cv[3];
     for (int j = 0; j < 3; ++j) {
-        cv[j] = cd(0, 0);
-        for (int a = 0; a < 3; ++a) cv[j] = cadd(cv[j], cscale(ph[a], g[4 + 3 * a + j]));
-        cv[j] = cscale(cv[j], area);
+        double2 cv = cd(0, 0);
+        for (int a = 0; a < 3; ++a) cv = cadd(cv, cscale(ph[a], g[4 + 3 * a + j]));
+        cv = cscale(cv, area);
+        sC[3 * (size_t)t + j] = make_float4((float)cv.x, (float)cv.x, (float)cv.y, (float)cv.y);
     }
-    sC[t] = make_float4((float)cv[0].x, (float)cv[0].y, (float)cv[1].x, (float)cv[1].y);
-    sC2[t] = make_float2((float)cv[2].x, (float)cv[2].y);
 }
 
-struct FarConst {
-    float k0, k1;      // wavenumbers
-    float k0r, k1r;    // k / (2 pi): phase in revolutions per unit length
-    float rho, irho;   // V and D block weights of the interior operators
-    float dk0, dk1;    // k0^2 and k1^2 / rho: weights of the D normal term
+typedef float2 f2;
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ f2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ f2 neg2(f2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ f2 dup2(float a) { return make_float2(a, a); }
+
+// Constants as (value, value) pairs for the packed instructions.
+struct FarConst2 {
+    f2 k0, k1, k0r, k1r, rho, irho, dk0, dk1;
 };
 
-// Accumulators of one test point: tile sums of u1, u2 (complex) and of the
-// curl vector A (3 complex), and the per-source-triangle sums T1 = sum_q Hs
-// phi_q, U = sum_q Gk phi_q, T3 = sum_q w_q Gd.
-struct PointAcc {
-    float u1r, u1i, u2r, u2i, axr, axi, ayr, ayi, azr, azi;
-    float t1r, t1i, ur, ui, t3r, t3i;
+// Accumulators of the two test points of a thread, packed (point a, point b):
+// tile sums of u1, u2 (complex) and of the curl vector A (3 complex), and
+// the per-source-triangle sums T1 = sum_q Hs phi_q, U = sum_q Gk phi_q,
+// T3 = sum_q w_q Gd.
+struct PairAcc {
+    f2 u1r, u1i, u2r, u2i, axr, axi, ayr, ayi, azr, azi;
+    f2 t1r, t1i, ur, ui, t3r, t3i;
 };
 
-// e^{i k r}: for |k r| below a few hundred radians the MUFU sine/cosine
-// take the argument directly (their own reduction has the same FP32 rounding
-// as an explicit one); REDUCE folds k r / (2 pi) to [-1/2, 1/2] first.
+// e^{i k r} for one point: for |k r| below 64 pi the MUFU sine / cosine take
+// the argument directly (their own reduction has the same FP32 rounding as an
+// explicit one); REDUCE folds k r / (2 pi) to [-1/2, 1/2] revolutions first.
 template <bool REDUCE>
-__device__ __forceinline__ void phasor(float r, float k, float krev, float &s, float &c) {
+__device__ __forceinline__ void phasor1(float kr, float r, float krev, float &s, float &c) {
     if (REDUCE) {
         const float t = r * krev;
         __sincosf(6.28318530717958647692f * (t - rintf(t)), &s, &c);
     } else {
-        __sincosf(k * r, &s, &c);
+        __sincosf(kr, &s, &c);
     }
 }
 
-// One point pair (test point x, source point A/B), both wavenumbers.
+// One source point against the two test points of the thread, both
+// wavenumbers, packed FP32 arithmetic.  P0..P3 hold the duplicated source
+// data; (nx2, ny2, nz2) the test-triangle normal; wq2 the rule weight.
 template <bool REDUCE>
-__device__ __forceinline__ void far_pair(const float4 &x, float xnx, const float4 &A,
-                                         const float4 &B, float ynx, float wq,
-                                         const FarConst &c, PointAcc &P) {
-    const float dx = x.x - A.x, dy = x.y - A.y, dz = x.z - A.z;
-    const float r2 = dx * dx + dy * dy + dz * dz;
-    const float ri = rsqrtf(r2);
-    const float r = r2 * ri;
-    const float ri3 = ri * ri * ri;
-    const float dnx = xnx - ynx;  // (x - y).n_x
-    float s0, c0, s1, c1;
-    phasor<REDUCE>(r, c.k0, c.k0r, s0, c0);
-    phasor<REDUCE>(r, c.k1, c.k1r, s1, c1);
-    const float kr0 = c.k0 * r, kr1 = c.k1 * r;
+__device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 &P0, const float4 &P1,
+                                          const float4 &P2, const f2 &P3, f2 nx2, f2 ny2, f2 nz2,
+                                          f2 wq2, const FarConst2 &c, PairAcc &A) {
+    const f2 dx = add2(X, lo2(P0)), dy = add2(Y, hi2(P0)), dz = add2(Z, lo2(P1));
+    f2 r2 = mul2(dx, dx);
+    r2 = fma2(dy, dy, r2);
+    r2 = fma2(dz, dz, r2);
+    const f2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const f2 r = mul2(r2, ri);
+    const f2 ri2 = mul2(ri, ri);
+    const f2 ri3 = mul2(ri2, ri);
+    f2 dnx = mul2(dx, nx2);  // (x - y).n_x
+    dnx = fma2(dy, ny2, dnx);
+    dnx = fma2(dz, nz2, dnx);
+    const f2 kr0 = mul2(r, c.k0), kr1 = mul2(r, c.k1);
+    f2 s0, c0, s1, c1;
+    phasor1<REDUCE>(kr0.x, r.x, c.k0r.x, s0.x, c0.x);
+    phasor1<REDUCE>(kr0.y, r.y, c.k0r.y, s0.y, c0.y);
+    phasor1<REDUCE>(kr1.x, r.x, c.k1r.x, s1.x, c1.x);
+    phasor1<REDUCE>(kr1.y, r.y, c.k1r.y, s1.y, c1.y);
     // G combinations (without 1/(4 pi)): V block (G0 + rho G1), D normal
     // term (k0^2 G0 + k1^2/rho G1), D curl term (G0 + G1/rho)
-    const float gpr = (c0 + c.rho * c1) * ri, gpi = (s0 + c.rho * s1) * ri;
-    const float gkr = (c.dk0 * c0 + c.dk1 * c1) * ri, gki = (c.dk0 * s0 + c.dk1 * s1) * ri;
-    const float wr = wq * ri;
-    P.t3r += (c0 + c.irho * c1) * wr;
-    P.t3i += (s0 + c.irho * s1) * wr;
-    // H0 + H1 with H = e^{ikr} (i k r - 1) / r^3
-    const float hsr = (-c0 - kr0 * s0 - c1 - kr1 * s1) * ri3;
-    const float hsi = (kr0 * c0 - s0 + kr1 * c1 - s1) * ri3;
-    const float psr = A.w, psi = B.x, phr = B.y, phi = B.z;
-    P.u1r += gpr * psr - gpi * psi;
-    P.u1i += gpr * psi + gpi * psr;
-    P.t1r += hsr * phr - hsi * phi;
-    P.t1i += hsr * phi + hsi * phr;
-    const float hxr = hsr * dnx, hxi = hsi * dnx;
-    P.u2r += hxr * psr - hxi * psi;
-    P.u2i += hxr * psi + hxi * psr;
-    P.ur += gkr * phr - gki * phi;
-    P.ui += gkr * phi + gki * phr;
+    const f2 gpr = mul2(fma2(c.rho, c1, c0), ri), gpi = mul2(fma2(c.rho, s1, s0), ri);
+    const f2 gkr = mul2(fma2(c.dk1, c1, mul2(c.dk0, c0)), ri);
+    const f2 gki = mul2(fma2(c.dk1, s1, mul2(c.dk0, s0)), ri);
+    const f2 wr = mul2(wq2, ri);
+    A.t3r = fma2(fma2(c.irho, c1, c0), wr, A.t3r);
+    A.t3i = fma2(fma2(c.irho, s1, s0), wr, A.t3i);
+    // H0 + H1, H = e^{ikr} (i k r - 1) / r^3:
+    //   re = -(c0 + kr0 s0 + c1 + kr1 s1) / r^3,  im = (kr0 c0 + kr1 c1 - s0 - s1) / r^3
+    const f2 pr = fma2(kr1, s1, fma2(kr0, s0, add2(c0, c1)));
+    const f2 qi = fma2(kr1, c1, fma2(kr0, c0, neg2(add2(s0, s1))));
+    const f2 hsr = mul2(pr, neg2(ri3)), hsi = mul2(qi, ri3);
+    const f2 psr = hi2(P1), psi = lo2(P2), phr = hi2(P2), phi = P3;
+    A.u1r = fma2(gpr, psr, fma2(neg2(gpi), psi, A.u1r));
+    A.u1i = fma2(gpr, psi, fma2(gpi, psr, A.u1i));
+    A.t1r = fma2(hsr, phr, fma2(neg2(hsi), phi, A.t1r));
+    A.t1i = fma2(hsr, phi, fma2(hsi, phr, A.t1i));
+    const f2 hxr = mul2(hsr, dnx), hxi = mul2(hsi, dnx);
+    A.u2r = fma2(hxr, psr, fma2(neg2(hxi), psi, A.u2r));
+    A.u2i = fma2(hxr, psi, fma2(hxi, psr, A.u2i));
+    A.ur = fma2(gkr, phr, fma2(neg2(gki), phi, A.ur));
+    A.ui = fma2(gkr, phi, fma2(gki, phr, A.ui));
 }
 
-// Per (test point, source triangle) epilogue: the factors that are constant
-// over the source triangle.
-__device__ __forceinline__ void far_tri_epilogue(PointAcc &P, float xny, float nxny, const float4 &C,
-                                                 const float2 &C2) {
-    P.u1r += xny * P.t1r;
-    P.u1i += xny * P.t1i;
-    P.u2r -= nxny * P.ur;
-    P.u2i -= nxny * P.ui;
-    P.axr += P.t3r * C.x - P.t3i * C.y;
-    P.axi += P.t3r * C.y + P.t3i * C.x;
-    P.ayr += P.t3r * C.z - P.t3i * C.w;
-    P.ayi += P.t3r * C.w + P.t3i * C.z;
-    P.azr += P.t3r * C2.x - P.t3i * C2.y;
-    P.azi += P.t3r * C2.y + P.t3i * C2.x;
-}
-
-// One thread per pair of test points (2j, 2j+1) of test triangle 2j / 6; the
-// two points share every shared-memory load, the touching test, n_x.n_y and
-// y.n_x.  Output part[(split * 10 + c) * npts + p], c = u1 (re, im), u2 (re,
-// im), A (x re, x im, y re, y im, z re, z im):
+// One thread per pair of test points (2j, 2j+1) of test triangle 2j / 6,
+// packed into the two lanes of FP32x2 instructions.  Output
+// part[(split * 10 + c) * npts + p], c = u1 (re, im), u2 (re, im),
+// A (x re, x im, y re, y im, z re, z im):
 //   u1 = sum [ (G0 + rho G1) psi_q + (x.n_y - h_y)(H0 + H1) phi_q ]
 //   u2 = sum [ (H0 + H1)(x - y).n_x psi_q - (n_x.n_y)(k0^2 G0 + k1^2/rho G1) phi_q ]
 //   A  = sum_s (sum_q w_q (G0 + G1/rho)) c_s
-// with G, H here without the factor 1/(4 pi) (applied in the gather).
-// Sums run per 64-triangle tile, then tile sums are added to running sums.
+// with G, H here without the factor 1/(4 pi) (applied in the gather).  Sums
+// run per 64-triangle tile, then tile sums are added to running sums.
 template <bool REDUCE>
 __global__ void __launch_bounds__(FAR_THREADS)
 far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ tn,
-           const int4 *__restrict__ tv, const float4 *__restrict__ sA,
-           const float4 *__restrict__ sB, const float4 *__restrict__ sC,
-           const float2 *__restrict__ sC2, int nt, int npts, int tris_per_split,
-           FarConst c, float *__restrict__ part) {
-    __shared__ float4 shA[FAR_TS * 6];
-    __shared__ float4 shB[FAR_TS * 6];
+           const int4 *__restrict__ tv, const float4 *__restrict__ sP0,
+           const float4 *__restrict__ sP1, const float4 *__restrict__ sP2,
+           const float2 *__restrict__ sP3, const float4 *__restrict__ sC, int nt, int npts,
+           int tris_per_split, FarConst2 c, float *__restrict__ part) {
+    __shared__ float4 shP0[FAR_TS * 6];
+    __shared__ float4 shP1[FAR_TS * 6];
+    __shared__ float4 shP2[FAR_TS * 6];
+    __shared__ float2 shP3[FAR_TS * 6];
     __shared__ float4 shN[FAR_TS];
-    __shared__ float4 shC[FAR_TS];
-    __shared__ float2 shC2[FAR_TS];
+    __shared__ float4 shC[FAR_TS * 3];
     __shared__ int4 shV[FAR_TS];
 
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -239,32 +253,35 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ tn,
     const int p0 = active ? 2 * j : 0;
     const int tau = p0 / 6;
     const float4 xa = pt[p0], xb = pt[p0 + 1];
+    const f2 X = make_float2(xa.x, xb.x), Y = make_float2(xa.y, xb.y), Z = make_float2(xa.z, xb.z);
     const float4 n4 = tn[tau];
     const int4 vt = tv[tau];
-    const float xnxa = xa.x * n4.x + xa.y * n4.y + xa.z * n4.z;
-    const float xnxb = xb.x * n4.x + xb.y * n4.y + xb.z * n4.z;
-    const float W1 = (float)kQw1, W2 = (float)kQw2;
+    const f2 nx2 = dup2(n4.x), ny2 = dup2(n4.y), nz2 = dup2(n4.z);
+    const f2 W1 = dup2((float)kQw1), W2 = dup2((float)kQw2);
 
-    float run[20];
+    f2 run[10];
 #pragma unroll
-    for (int i = 0; i < 20; ++i) run[i] = 0.f;
+    for (int i = 0; i < 10; ++i) run[i] = make_float2(0.f, 0.f);
 
     for (int t0 = s_begin; t0 < s_end; t0 += FAR_TS) {
         const int cnt = min(FAR_TS, s_end - t0);
         __syncthreads();
         for (int i = threadIdx.x; i < cnt * 6; i += blockDim.x) {
-            shA[i] = sA[6 * t0 + i];
-            shB[i] = sB[6 * t0 + i];
+            shP0[i] = sP0[6 * t0 + i];
+            shP1[i] = sP1[6 * t0 + i];
+            shP2[i] = sP2[6 * t0 + i];
+            shP3[i] = sP3[6 * t0 + i];
         }
+        for (int i = threadIdx.x; i < cnt * 3; i += blockDim.x) shC[i] = sC[3 * t0 + i];
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
             shN[i] = tn[t0 + i];
-            shC[i] = sC[t0 + i];
-            shC2[i] = sC2[t0 + i];
             shV[i] = tv[t0 + i];
         }
         __syncthreads();
 
-        PointAcc Pa = {}, Pb = {};
+        PairAcc A;
+        A.u1r = A.u1i = A.u2r = A.u2i = make_float2(0.f, 0.f);
+        A.axr = A.axi = A.ayr = A.ayi = A.azr = A.azi = make_float2(0.f, 0.f);
         for (int s = 0; s < cnt; ++s) {
             const int4 vs = shV[s];
             const bool touch = (vs.x == vt.x) | (vs.x == vt.y) | (vs.x == vt.z) |
@@ -272,37 +289,38 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ tn,
                                (vs.z == vt.x) | (vs.z == vt.y) | (vs.z == vt.z);
             if (touch) continue;
             const float4 ns = shN[s];
-            const float xnya = xa.x * ns.x + xa.y * ns.y + xa.z * ns.z - ns.w;
-            const float xnyb = xb.x * ns.x + xb.y * ns.y + xb.z * ns.z - ns.w;
+            // (x - y).n_y = x.n_y - n_y.P0 is constant over the source triangle
+            const f2 xny = fma2(Z, dup2(ns.z), fma2(Y, dup2(ns.y), fma2(X, dup2(ns.x), dup2(-ns.w))));
             const float nxny = n4.x * ns.x + n4.y * ns.y + n4.z * ns.z;
-            Pa.t1r = Pa.t1i = Pa.ur = Pa.ui = Pa.t3r = Pa.t3i = 0.f;
-            Pb.t1r = Pb.t1i = Pb.ur = Pb.ui = Pb.t3r = Pb.t3i = 0.f;
+            A.t1r = A.t1i = A.ur = A.ui = A.t3r = A.t3i = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                const float4 A = shA[6 * s + q];
-                const float4 B = shB[6 * s + q];
-                const float ynx = A.x * n4.x + A.y * n4.y + A.z * n4.z;
-                const float wq = q < 3 ? W1 : W2;
-                far_pair<REDUCE>(xa, xnxa, A, B, ynx, wq, c, Pa);
-                far_pair<REDUCE>(xb, xnxb, A, B, ynx, wq, c, Pb);
-            }
-            const float4 C = shC[s];
-            const float2 C2 = shC2[s];
-            far_tri_epilogue(Pa, xnya, nxny, C, C2);
-            far_tri_epilogue(Pb, xnyb, nxny, C, C2);
+            for (int q = 0; q < 6; ++q)
+                far_pair2<REDUCE>(X, Y, Z, shP0[6 * s + q], shP1[6 * s + q], shP2[6 * s + q],
+                                  shP3[6 * s + q], nx2, ny2, nz2, q < 3 ? W1 : W2, c, A);
+            const f2 nn = dup2(-nxny);
+            A.u1r = fma2(xny, A.t1r, A.u1r);
+            A.u1i = fma2(xny, A.t1i, A.u1i);
+            A.u2r = fma2(nn, A.ur, A.u2r);
+            A.u2i = fma2(nn, A.ui, A.u2i);
+            const float4 Cx = shC[3 * s], Cy = shC[3 * s + 1], Cz = shC[3 * s + 2];
+            A.axr = fma2(A.t3r, lo2(Cx), fma2(neg2(A.t3i), hi2(Cx), A.axr));
+            A.axi = fma2(A.t3r, hi2(Cx), fma2(A.t3i, lo2(Cx), A.axi));
+            A.ayr = fma2(A.t3r, lo2(Cy), fma2(neg2(A.t3i), hi2(Cy), A.ayr));
+            A.ayi = fma2(A.t3r, hi2(Cy), fma2(A.t3i, lo2(Cy), A.ayi));
+            A.azr = fma2(A.t3r, lo2(Cz), fma2(neg2(A.t3i), hi2(Cz), A.azr));
+            A.azi = fma2(A.t3r, hi2(Cz), fma2(A.t3i, lo2(Cz), A.azi));
         }
-        run[0] += Pa.u1r; run[1] += Pa.u1i; run[2] += Pa.u2r; run[3] += Pa.u2i;
-        run[4] += Pa.axr; run[5] += Pa.axi; run[6] += Pa.ayr; run[7] += Pa.ayi;
-        run[8] += Pa.azr; run[9] += Pa.azi;
-        run[10] += Pb.u1r; run[11] += Pb.u1i; run[12] += Pb.u2r; run[13] += Pb.u2i;
-        run[14] += Pb.axr; run[15] += Pb.axi; run[16] += Pb.ayr; run[17] += Pb.ayi;
-        run[18] += Pb.azr; run[19] += Pb.azi;
+        run[0] = add2(run[0], A.u1r); run[1] = add2(run[1], A.u1i);
+        run[2] = add2(run[2], A.u2r); run[3] = add2(run[3], A.u2i);
+        run[4] = add2(run[4], A.axr); run[5] = add2(run[5], A.axi);
+        run[6] = add2(run[6], A.ayr); run[7] = add2(run[7], A.ayi);
+        run[8] = add2(run[8], A.azr); run[9] = add2(run[9], A.azi);
     }
     if (active) {
 #pragma unroll
         for (int i = 0; i < 10; ++i) {
-            part[((size_t)split * 10 + i) * npts + p0] = run[i];
-            part[((size_t)split * 10 + i) * npts + p0 + 1] = run[10 + i];
+            part[((size_t)split * 10 + i) * npts + p0] = run[i].x;
+            part[((size_t)split * 10 + i) * npts + p0 + 1] = run[i].y;
         }
     }
 }
@@ -369,10 +387,11 @@ int far_setup_geometry(osrc_problem *pb, cudaStream_t st) {
     OSRC_TRY(pb->d_tn.alloc(m->ctx, nt));
     OSRC_TRY(pb->d_tv.alloc(m->ctx, nt));
     OSRC_TRY(pb->d_tgeo.alloc(m->ctx, 16 * (size_t)nt));
-    OSRC_TRY(pb->d_sA.alloc(m->ctx, 6 * (size_t)nt));
-    OSRC_TRY(pb->d_sB.alloc(m->ctx, 6 * (size_t)nt));
-    OSRC_TRY(pb->d_sC.alloc(m->ctx, nt));
-    OSRC_TRY(pb->d_sC2.alloc(m->ctx, nt));
+    OSRC_TRY(pb->d_sP0.alloc(m->ctx, 6 * (size_t)nt));
+    OSRC_TRY(pb->d_sP1.alloc(m->ctx, 6 * (size_t)nt));
+    OSRC_TRY(pb->d_sP2.alloc(m->ctx, 6 * (size_t)nt));
+    OSRC_TRY(pb->d_sP3.alloc(m->ctx, 6 * (size_t)nt));
+    OSRC_TRY(pb->d_sC.alloc(m->ctx, 3 * (size_t)nt));
     far_geom_kernel<<<(nt + 127) / 128, 128, 0, st>>>(m->d_verts.p, m->d_tris.p, nt, pb->d_pt.p,
                                                       pb->d_tn.p, pb->d_tv.p, pb->d_tgeo.p);
     pb->launches++;
@@ -426,20 +445,21 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
     const int use_near = (part & OSRC_PART_NEAR) ? 1 : 0;
     if (use_far) {
         far_prep_kernel<<<(nt + 127) / 128, 128, 0, st>>>(x, nv, nt, m->d_tris.p, pb->d_pt.p,
-                                                          pb->d_tgeo.p, pb->d_sA.p, pb->d_sB.p,
-                                                          pb->d_sC.p, pb->d_sC2.p);
+                                                          pb->d_tgeo.p, pb->d_sP0.p, pb->d_sP1.p,
+                                                          pb->d_sP2.p, pb->d_sP3.p, pb->d_sC.p);
         pb->launches++;
-        FarConst c;
         const double k0 = pb->p.k_ext, k1 = pb->p.k_int, rho = pb->p.rho_ratio;
         const double inv2pi = 0.15915494309189533577;
-        c.k0 = (float)k0;
-        c.k1 = (float)k1;
-        c.k0r = (float)(k0 * inv2pi);
-        c.k1r = (float)(k1 * inv2pi);
-        c.rho = (float)rho;
-        c.irho = (float)(1.0 / rho);
-        c.dk0 = (float)(k0 * k0);
-        c.dk1 = (float)(k1 * k1 / rho);
+        auto d2 = [](double v) { return make_float2((float)v, (float)v); };
+        FarConst2 c;
+        c.k0 = d2(k0);
+        c.k1 = d2(k1);
+        c.k0r = d2(k0 * inv2pi);
+        c.k1r = d2(k1 * inv2pi);
+        c.rho = d2(rho);
+        c.irho = d2(1.0 / rho);
+        c.dk0 = d2(k0 * k0);
+        c.dk1 = d2(k1 * k1 / rho);
         const int ns = pb->nsplit;
         const int tps = (nt + ns - 1) / ns;
         dim3 grid((npts / 2 + FAR_THREADS - 1) / FAR_THREADS, ns);
@@ -449,12 +469,14 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
         }
         if (pb->far_reduce)
             far_kernel<true><<<grid, FAR_THREADS, 0, st>>>(pb->d_pt.p, pb->d_tn.p, pb->d_tv.p,
-                                                           pb->d_sA.p, pb->d_sB.p, pb->d_sC.p,
-                                                           pb->d_sC2.p, nt, npts, tps, c, pb->d_part.p);
+                                                           pb->d_sP0.p, pb->d_sP1.p, pb->d_sP2.p,
+                                                           pb->d_sP3.p, pb->d_sC.p, nt, npts, tps, c,
+                                                           pb->d_part.p);
         else
             far_kernel<false><<<grid, FAR_THREADS, 0, st>>>(pb->d_pt.p, pb->d_tn.p, pb->d_tv.p,
-                                                            pb->d_sA.p, pb->d_sB.p, pb->d_sC.p,
-                                                            pb->d_sC2.p, nt, npts, tps, c, pb->d_part.p);
+                                                            pb->d_sP0.p, pb->d_sP1.p, pb->d_sP2.p,
+                                                            pb->d_sP3.p, pb->d_sC.p, nt, npts, tps, c,
+                                                            pb->d_part.p);
         pb->launches++;
         if (pb->prof_on) {
             OSRC_CK(cudaEventRecord(pb->prof_ev[1], st));
