@@ -87,19 +87,23 @@ __global__ void far_geom_kernel(const double *__restrict__ verts, const int *__r
     g[13] = g[14] = g[15] = 0.0;
 }
 
-// Source data of one apply, duplicated into (value, value) pairs so that
-// the far kernel's packed FP32 instructions (two test points per thread)
-// take them as operands without extra moves:
-//   sP0 = (-y.x, -y.x, -y.y, -y.y)   sP1 = (-y.z, -y.z, psi.re, psi.re)
-//   sP2 = (psi.im, psi.im, phi.re, phi.re)   sP3 = (phi.im, phi.im)
-// with psi_q = w_q |s| sum_b lambda_b(q) psi_b (the same for phi), and per
-// triangle c_s = |s| sum_b phi_b curl phi_b as sC[j] = (c_j.re, c_j.re,
-// c_j.im, c_j.im).
+// Source data of one apply, duplicated into (value, value) pairs and stored
+// with both signs, so that the far kernel's packed FP32 instructions (two
+// test points per thread) take every operand of a complex multiply-add
+// straight from shared memory, without moves or negations:
+//   sP[5k]   = (-y.x, -y.x, -y.y, -y.y)     sP[5k+1] = (-y.z, -y.z, psi.re, psi.re)
+//   sP[5k+2] = (psi.im, psi.im, -psi.re, -psi.re)
+//   sP[5k+3] = (-psi.im, -psi.im, phi.re, phi.re)
+//   sP[5k+4] = (phi.im, phi.im, -phi.re, -phi.re)   sP5[k] = (-phi.im, -phi.im)
+// with psi_q = w_q |s| sum_b lambda_b(q) psi_b (the same for phi); per
+// triangle c_s = |s| sum_b phi_b curl phi_b as
+//   sC[5t] = (cx.re, cx.re, cx.im, cx.im)   sC[5t+1] = (-cx.im, -cx.im, cy.re, cy.re)
+//   sC[5t+2] = (cy.im, cy.im, -cy.im, -cy.im)   sC[5t+3] = (cz.re, cz.re, cz.im, cz.im)
+//   sC[5t+4] = (-cz.im, -cz.im, 0, 0)
 __global__ void far_prep_kernel(const double2 *__restrict__ x, int nv, int nt,
                                 const int *__restrict__ tris, const float4 *__restrict__ pt,
-                                const double *__restrict__ tgeo, float4 *__restrict__ sP0,
-                                float4 *__restrict__ sP1, float4 *__restrict__ sP2,
-                                float2 *__restrict__ sP3, float4 *__restrict__ sC) {
+                                const double *__restrict__ tgeo, float4 *__restrict__ sP,
+                                float2 *__restrict__ sP5, float4 *__restrict__ sC) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
     double2 ps[3], ph[3];
@@ -123,17 +127,27 @@ __global__ void far_prep_kernel(const double2 *__restrict__ x, int nv, int nt,
         const float psr = (float)(W * s.x), psi = (float)(W * s.y);
         const float phr = (float)(W * f.x), phi = (float)(W * f.y);
         const size_t k = 6 * (size_t)t + q;
-        sP0[k] = make_float4(-p.x, -p.x, -p.y, -p.y);
-        sP1[k] = make_float4(-p.z, -p.z, psr, psr);
-        sP2[k] = make_float4(psi, psi, phr, phr);
-        sP3[k] = make_float2(phi, phi);
+        float4 *d = sP + 5 * k;
+        d[0] = make_float4(-p.x, -p.x, -p.y, -p.y);
+        d[1] = make_float4(-p.z, -p.z, psr, psr);
+        d[2] = make_float4(psi, psi, -psr, -psr);
+        d[3] = make_float4(-psi, -psi, phr, phr);
+        d[4] = make_float4(phi, phi, -phr, -phr);
+        sP5[k] = make_float2(-phi, -phi);
     }
+    float cr[3], ci[3];
     for (int j = 0; j < 3; ++j) {
         double2 cv = cd(0, 0);
         for (int a = 0; a < 3; ++a) cv = cadd(cv, cscale(ph[a], g[4 + 3 * a + j]));
-        cv = cscale(cv, area);
-        sC[3 * (size_t)t + j] = make_float4((float)cv.x, (float)cv.x, (float)cv.y, (float)cv.y);
+        cr[j] = (float)(cv.x * area);
+        ci[j] = (float)(cv.y * area);
     }
+    float4 *c = sC + 5 * (size_t)t;
+    c[0] = make_float4(cr[0], cr[0], ci[0], ci[0]);
+    c[1] = make_float4(-ci[0], -ci[0], cr[1], cr[1]);
+    c[2] = make_float4(ci[1], ci[1], -ci[1], -ci[1]);
+    c[3] = make_float4(cr[2], cr[2], ci[2], ci[2]);
+    c[4] = make_float4(-ci[2], -ci[2], 0.f, 0.f);
 }
 
 typedef float2 f2;
@@ -147,12 +161,12 @@ __device__ __forceinline__ f2 dup2(float a) { return make_float2(a, a); }
 
 // Constants as (value, value) pairs for the packed instructions.
 struct FarConst2 {
-    f2 k0, k1, k0r, k1r, rho, irho, dk0, dk1;
+    f2 k0, k1, nk0, nk1, k0r, k1r, rho, irho, dk0, dk1;
 };
 
 // Accumulators of the two test points of a thread, packed (point a, point b):
 // tile sums of u1, u2 (complex) and of the curl vector A (3 complex), and
-// the per-source-triangle sums T1 = sum_q Hs phi_q, U = sum_q Gk phi_q,
+// the per-source-triangle sums T1n = -sum_q Hs phi_q, U = sum_q Gk phi_q,
 // T3 = sum_q w_q Gd.
 struct PairAcc {
     f2 u1r, u1i, u2r, u2i, axr, axi, ayr, ayi, azr, azi;
@@ -173,13 +187,14 @@ __device__ __forceinline__ void phasor1(float kr, float r, float krev, float &s,
 }
 
 // One source point against the two test points of the thread, both
-// wavenumbers, packed FP32 arithmetic.  P0..P3 hold the duplicated source
-// data; (nx2, ny2, nz2) the test-triangle normal; wq2 the rule weight.
+// wavenumbers, packed FP32 arithmetic.  P[0..4], P5 hold the signed
+// duplicated source data; (mnx, mny, mnz) is the negated test-triangle
+// normal; wq2 the rule weight.
 template <bool REDUCE>
-__device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 &P0, const float4 &P1,
-                                          const float4 &P2, const f2 &P3, f2 nx2, f2 ny2, f2 nz2,
-                                          f2 wq2, const FarConst2 &c, PairAcc &A) {
-    const f2 dx = add2(X, lo2(P0)), dy = add2(Y, hi2(P0)), dz = add2(Z, lo2(P1));
+__device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, const f2 &P5, f2 mnx,
+                                          f2 mny, f2 mnz, f2 wq2, const FarConst2 &c, PairAcc &A) {
+    const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3], P4 = P[4];
+    const f2 dx = add2(X, lo2(P0)), dy = add2(Y, hi2(P0)), dz = add2(Z, lo2(P1));  // x - y
     f2 r2 = mul2(dx, dx);
     r2 = fma2(dy, dy, r2);
     r2 = fma2(dz, dz, r2);
@@ -187,38 +202,41 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 &P0, co
     const f2 r = mul2(r2, ri);
     const f2 ri2 = mul2(ri, ri);
     const f2 ri3 = mul2(ri2, ri);
-    f2 dnx = mul2(dx, nx2);  // (x - y).n_x
-    dnx = fma2(dy, ny2, dnx);
-    dnx = fma2(dz, nz2, dnx);
+    f2 dnxn = mul2(dx, mnx);  // (y - x).n_x
+    dnxn = fma2(dy, mny, dnxn);
+    dnxn = fma2(dz, mnz, dnxn);
     const f2 kr0 = mul2(r, c.k0), kr1 = mul2(r, c.k1);
+    const f2 nkr0 = mul2(r, c.nk0), nkr1 = mul2(r, c.nk1);
     f2 s0, c0, s1, c1;
     phasor1<REDUCE>(kr0.x, r.x, c.k0r.x, s0.x, c0.x);
     phasor1<REDUCE>(kr0.y, r.y, c.k0r.y, s0.y, c0.y);
     phasor1<REDUCE>(kr1.x, r.x, c.k1r.x, s1.x, c1.x);
     phasor1<REDUCE>(kr1.y, r.y, c.k1r.y, s1.y, c1.y);
-    // G combinations (without 1/(4 pi)): V block (G0 + rho G1), D normal
-    // term (k0^2 G0 + k1^2/rho G1), D curl term (G0 + G1/rho)
+    const f2 psr = hi2(P1), psi = lo2(P2), mpsr = hi2(P2), mpsi = lo2(P3);
+    const f2 phr = hi2(P3), phi = lo2(P4), mphr = hi2(P4), mphi = P5;
+    // V block (G0 + rho G1) psi, without 1/(4 pi)
     const f2 gpr = mul2(fma2(c.rho, c1, c0), ri), gpi = mul2(fma2(c.rho, s1, s0), ri);
+    A.u1r = fma2(gpr, psr, fma2(gpi, mpsi, A.u1r));
+    A.u1i = fma2(gpr, psi, fma2(gpi, psr, A.u1i));
+    // D normal term (k0^2 G0 + k1^2/rho G1) phi
     const f2 gkr = mul2(fma2(c.dk1, c1, mul2(c.dk0, c0)), ri);
     const f2 gki = mul2(fma2(c.dk1, s1, mul2(c.dk0, s0)), ri);
+    A.ur = fma2(gkr, phr, fma2(gki, mphi, A.ur));
+    A.ui = fma2(gkr, phi, fma2(gki, phr, A.ui));
+    // D curl term: sum_q w_q (G0 + G1/rho)
     const f2 wr = mul2(wq2, ri);
     A.t3r = fma2(fma2(c.irho, c1, c0), wr, A.t3r);
     A.t3i = fma2(fma2(c.irho, s1, s0), wr, A.t3i);
-    // H0 + H1, H = e^{ikr} (i k r - 1) / r^3:
-    //   re = -(c0 + kr0 s0 + c1 + kr1 s1) / r^3,  im = (kr0 c0 + kr1 c1 - s0 - s1) / r^3
-    const f2 pr = fma2(kr1, s1, fma2(kr0, s0, add2(c0, c1)));
-    const f2 qi = fma2(kr1, c1, fma2(kr0, c0, neg2(add2(s0, s1))));
-    const f2 hsr = mul2(pr, neg2(ri3)), hsi = mul2(qi, ri3);
-    const f2 psr = hi2(P1), psi = lo2(P2), phr = hi2(P2), phi = P3;
-    A.u1r = fma2(gpr, psr, fma2(neg2(gpi), psi, A.u1r));
-    A.u1i = fma2(gpr, psi, fma2(gpi, psr, A.u1i));
-    A.t1r = fma2(hsr, phr, fma2(neg2(hsi), phi, A.t1r));
-    A.t1i = fma2(hsr, phi, fma2(hsi, phr, A.t1i));
-    const f2 hxr = mul2(hsr, dnx), hxi = mul2(hsi, dnx);
-    A.u2r = fma2(hxr, psr, fma2(neg2(hxi), psi, A.u2r));
-    A.u2i = fma2(hxr, psi, fma2(hxi, psr, A.u2i));
-    A.ur = fma2(gkr, phr, fma2(neg2(gki), phi, A.ur));
-    A.ui = fma2(gkr, phi, fma2(gki, phr, A.ui));
+    // -(H0 + H1), H = e^{ikr} (i k r - 1) / r^3:
+    //   re = (c0 + c1 + kr0 s0 + kr1 s1) / r^3,  im = (s0 + s1 - kr0 c0 - kr1 c1) / r^3
+    const f2 hp = mul2(fma2(kr1, s1, fma2(kr0, s0, add2(c0, c1))), ri3);
+    const f2 hq = mul2(fma2(nkr1, c1, fma2(nkr0, c0, add2(s0, s1))), ri3);
+    A.t1r = fma2(hp, phr, fma2(hq, mphi, A.t1r));  // T1n = -sum Hs phi
+    A.t1i = fma2(hp, phi, fma2(hq, phr, A.t1i));
+    // T block: (H0 + H1)(x - y).n_x psi = (-(H0 + H1)) (y - x).n_x psi
+    const f2 hxp = mul2(hp, dnxn), hxq = mul2(hq, dnxn);
+    A.u2r = fma2(hxp, psr, fma2(hxq, mpsi, A.u2r));
+    A.u2i = fma2(hxp, psi, fma2(hxq, psr, A.u2i));
 }
 
 // One thread per pair of test points (2j, 2j+1) of test triangle 2j / 6,
@@ -233,16 +251,13 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 &P0, co
 template <bool REDUCE>
 __global__ void __launch_bounds__(FAR_THREADS)
 far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ tn,
-           const int4 *__restrict__ tv, const float4 *__restrict__ sP0,
-           const float4 *__restrict__ sP1, const float4 *__restrict__ sP2,
-           const float2 *__restrict__ sP3, const float4 *__restrict__ sC, int nt, int npts,
+           const int4 *__restrict__ tv, const float4 *__restrict__ sP,
+           const float2 *__restrict__ sP5, const float4 *__restrict__ sC, int nt, int npts,
            int tris_per_split, FarConst2 c, float *__restrict__ part) {
-    __shared__ float4 shP0[FAR_TS * 6];
-    __shared__ float4 shP1[FAR_TS * 6];
-    __shared__ float4 shP2[FAR_TS * 6];
-    __shared__ float2 shP3[FAR_TS * 6];
+    __shared__ float4 shP[FAR_TS * 6 * 5];
+    __shared__ float2 shP5[FAR_TS * 6];
     __shared__ float4 shN[FAR_TS];
-    __shared__ float4 shC[FAR_TS * 3];
+    __shared__ float4 shC[FAR_TS * 5];
     __shared__ int4 shV[FAR_TS];
 
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -256,7 +271,7 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ tn,
     const f2 X = make_float2(xa.x, xb.x), Y = make_float2(xa.y, xb.y), Z = make_float2(xa.z, xb.z);
     const float4 n4 = tn[tau];
     const int4 vt = tv[tau];
-    const f2 nx2 = dup2(n4.x), ny2 = dup2(n4.y), nz2 = dup2(n4.z);
+    const f2 mnx = dup2(-n4.x), mny = dup2(-n4.y), mnz = dup2(-n4.z);
     const f2 W1 = dup2((float)kQw1), W2 = dup2((float)kQw2);
 
     f2 run[10];
@@ -266,15 +281,12 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ tn,
     for (int t0 = s_begin; t0 < s_end; t0 += FAR_TS) {
         const int cnt = min(FAR_TS, s_end - t0);
         __syncthreads();
-        for (int i = threadIdx.x; i < cnt * 6; i += blockDim.x) {
-            shP0[i] = sP0[6 * t0 + i];
-            shP1[i] = sP1[6 * t0 + i];
-            shP2[i] = sP2[6 * t0 + i];
-            shP3[i] = sP3[6 * t0 + i];
-        }
-        for (int i = threadIdx.x; i < cnt * 3; i += blockDim.x) shC[i] = sC[3 * t0 + i];
+        for (int i = threadIdx.x; i < cnt * 30; i += blockDim.x) shP[i] = sP[30 * (size_t)t0 + i];
+        for (int i = threadIdx.x; i < cnt * 6; i += blockDim.x) shP5[i] = sP5[6 * (size_t)t0 + i];
+        for (int i = threadIdx.x; i < cnt * 5; i += blockDim.x) shC[i] = sC[5 * (size_t)t0 + i];
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-            shN[i] = tn[t0 + i];
+            const float4 ns = tn[t0 + i];
+            shN[i] = make_float4(-ns.x, -ns.y, -ns.z, ns.w);
             shV[i] = tv[t0 + i];
         }
         __syncthreads();
@@ -288,27 +300,29 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ tn,
                                (vs.y == vt.x) | (vs.y == vt.y) | (vs.y == vt.z) |
                                (vs.z == vt.x) | (vs.z == vt.y) | (vs.z == vt.z);
             if (touch) continue;
-            const float4 ns = shN[s];
-            // (x - y).n_y = x.n_y - n_y.P0 is constant over the source triangle
-            const f2 xny = fma2(Z, dup2(ns.z), fma2(Y, dup2(ns.y), fma2(X, dup2(ns.x), dup2(-ns.w))));
-            const float nxny = n4.x * ns.x + n4.y * ns.y + n4.z * ns.z;
+            const float4 mns = shN[s];  // (-n_y, n_y.P0)
+            // -(x - y).n_y = h_y - x.n_y, constant over the source triangle
+            const f2 xnyn = fma2(Z, dup2(mns.z), fma2(Y, dup2(mns.y), fma2(X, dup2(mns.x), dup2(mns.w))));
+            const float nxnyn = n4.x * mns.x + n4.y * mns.y + n4.z * mns.z;  // -n_x.n_y
             A.t1r = A.t1i = A.ur = A.ui = A.t3r = A.t3i = make_float2(0.f, 0.f);
 #pragma unroll
             for (int q = 0; q < 6; ++q)
-                far_pair2<REDUCE>(X, Y, Z, shP0[6 * s + q], shP1[6 * s + q], shP2[6 * s + q],
-                                  shP3[6 * s + q], nx2, ny2, nz2, q < 3 ? W1 : W2, c, A);
-            const f2 nn = dup2(-nxny);
-            A.u1r = fma2(xny, A.t1r, A.u1r);
-            A.u1i = fma2(xny, A.t1i, A.u1i);
+                far_pair2<REDUCE>(X, Y, Z, &shP[30 * s + 5 * q], shP5[6 * s + q], mnx, mny, mnz,
+                                  q < 3 ? W1 : W2, c, A);
+            // u1 += (x - y).n_y T1 = (-(x - y).n_y)(-T1);  u2 += (-n_x.n_y) U
+            A.u1r = fma2(xnyn, A.t1r, A.u1r);
+            A.u1i = fma2(xnyn, A.t1i, A.u1i);
+            const f2 nn = dup2(nxnyn);
             A.u2r = fma2(nn, A.ur, A.u2r);
             A.u2i = fma2(nn, A.ui, A.u2i);
-            const float4 Cx = shC[3 * s], Cy = shC[3 * s + 1], Cz = shC[3 * s + 2];
-            A.axr = fma2(A.t3r, lo2(Cx), fma2(neg2(A.t3i), hi2(Cx), A.axr));
-            A.axi = fma2(A.t3r, hi2(Cx), fma2(A.t3i, lo2(Cx), A.axi));
-            A.ayr = fma2(A.t3r, lo2(Cy), fma2(neg2(A.t3i), hi2(Cy), A.ayr));
-            A.ayi = fma2(A.t3r, hi2(Cy), fma2(A.t3i, lo2(Cy), A.ayi));
-            A.azr = fma2(A.t3r, lo2(Cz), fma2(neg2(A.t3i), hi2(Cz), A.azr));
-            A.azi = fma2(A.t3r, hi2(Cz), fma2(A.t3i, lo2(Cz), A.azi));
+            const float4 C0 = shC[5 * s], C1 = shC[5 * s + 1], C2 = shC[5 * s + 2];
+            const float4 C3 = shC[5 * s + 3], C4 = shC[5 * s + 4];
+            A.axr = fma2(A.t3r, lo2(C0), fma2(A.t3i, lo2(C1), A.axr));
+            A.axi = fma2(A.t3r, hi2(C0), fma2(A.t3i, lo2(C0), A.axi));
+            A.ayr = fma2(A.t3r, hi2(C1), fma2(A.t3i, hi2(C2), A.ayr));
+            A.ayi = fma2(A.t3r, lo2(C2), fma2(A.t3i, hi2(C1), A.ayi));
+            A.azr = fma2(A.t3r, lo2(C3), fma2(A.t3i, lo2(C4), A.azr));
+            A.azi = fma2(A.t3r, hi2(C3), fma2(A.t3i, lo2(C3), A.azi));
         }
         run[0] = add2(run[0], A.u1r); run[1] = add2(run[1], A.u1i);
         run[2] = add2(run[2], A.u2r); run[3] = add2(run[3], A.u2i);
@@ -387,11 +401,9 @@ int far_setup_geometry(osrc_problem *pb, cudaStream_t st) {
     OSRC_TRY(pb->d_tn.alloc(m->ctx, nt));
     OSRC_TRY(pb->d_tv.alloc(m->ctx, nt));
     OSRC_TRY(pb->d_tgeo.alloc(m->ctx, 16 * (size_t)nt));
-    OSRC_TRY(pb->d_sP0.alloc(m->ctx, 6 * (size_t)nt));
-    OSRC_TRY(pb->d_sP1.alloc(m->ctx, 6 * (size_t)nt));
-    OSRC_TRY(pb->d_sP2.alloc(m->ctx, 6 * (size_t)nt));
-    OSRC_TRY(pb->d_sP3.alloc(m->ctx, 6 * (size_t)nt));
-    OSRC_TRY(pb->d_sC.alloc(m->ctx, 3 * (size_t)nt));
+    OSRC_TRY(pb->d_sP.alloc(m->ctx, 30 * (size_t)nt));
+    OSRC_TRY(pb->d_sP5.alloc(m->ctx, 6 * (size_t)nt));
+    OSRC_TRY(pb->d_sC.alloc(m->ctx, 5 * (size_t)nt));
     far_geom_kernel<<<(nt + 127) / 128, 128, 0, st>>>(m->d_verts.p, m->d_tris.p, nt, pb->d_pt.p,
                                                       pb->d_tn.p, pb->d_tv.p, pb->d_tgeo.p);
     pb->launches++;
@@ -445,8 +457,8 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
     const int use_near = (part & OSRC_PART_NEAR) ? 1 : 0;
     if (use_far) {
         far_prep_kernel<<<(nt + 127) / 128, 128, 0, st>>>(x, nv, nt, m->d_tris.p, pb->d_pt.p,
-                                                          pb->d_tgeo.p, pb->d_sP0.p, pb->d_sP1.p,
-                                                          pb->d_sP2.p, pb->d_sP3.p, pb->d_sC.p);
+                                                          pb->d_tgeo.p, pb->d_sP.p, pb->d_sP5.p,
+                                                          pb->d_sC.p);
         pb->launches++;
         const double k0 = pb->p.k_ext, k1 = pb->p.k_int, rho = pb->p.rho_ratio;
         const double inv2pi = 0.15915494309189533577;
@@ -454,6 +466,8 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
         FarConst2 c;
         c.k0 = d2(k0);
         c.k1 = d2(k1);
+        c.nk0 = d2(-k0);
+        c.nk1 = d2(-k1);
         c.k0r = d2(k0 * inv2pi);
         c.k1r = d2(k1 * inv2pi);
         c.rho = d2(rho);
@@ -469,14 +483,12 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
         }
         if (pb->far_reduce)
             far_kernel<true><<<grid, FAR_THREADS, 0, st>>>(pb->d_pt.p, pb->d_tn.p, pb->d_tv.p,
-                                                           pb->d_sP0.p, pb->d_sP1.p, pb->d_sP2.p,
-                                                           pb->d_sP3.p, pb->d_sC.p, nt, npts, tps, c,
-                                                           pb->d_part.p);
+                                                           pb->d_sP.p, pb->d_sP5.p, pb->d_sC.p, nt,
+                                                           npts, tps, c, pb->d_part.p);
         else
             far_kernel<false><<<grid, FAR_THREADS, 0, st>>>(pb->d_pt.p, pb->d_tn.p, pb->d_tv.p,
-                                                            pb->d_sP0.p, pb->d_sP1.p, pb->d_sP2.p,
-                                                            pb->d_sP3.p, pb->d_sC.p, nt, npts, tps, c,
-                                                            pb->d_part.p);
+                                                            pb->d_sP.p, pb->d_sP5.p, pb->d_sC.p, nt,
+                                                            npts, tps, c, pb->d_part.p);
         pb->launches++;
         if (pb->prof_on) {
             OSRC_CK(cudaEventRecord(pb->prof_ev[1], st));

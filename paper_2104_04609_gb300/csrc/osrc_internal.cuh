@@ -110,9 +110,9 @@ struct osrc_problem {
     DBuf<float4> d_tn;   // [nt]   outward normal, plane offset n.P0
     DBuf<int4> d_tv;     // [nt]   vertex indices
     // ---- far field: per-apply workspace ----------------------------------
-    DBuf<float4> d_sP0, d_sP1, d_sP2;  // [6nt] source points, duplicated pairs (-y, psi, phi)
-    DBuf<float2> d_sP3;                // [6nt] (phi.im, phi.im)
-    DBuf<float4> d_sC;                 // [3nt] c_sigma components (re, re, im, im)
+    DBuf<float4> d_sP;   // [6nt][5] source points: -y, psi, phi with both signs, duplicated pairs
+    DBuf<float2> d_sP5;  // [6nt] (-phi.im, -phi.im)
+    DBuf<float4> d_sC;   // [nt][5] c_sigma components with both signs, duplicated pairs
     DBuf<float> d_part;       // [nsplit][6nt][10] per test point partial sums
     int nsplit = 1;
     bool far_reduce = false;  // explicit phase reduction for large k r
