@@ -44,7 +44,8 @@ constexpr int FAR_THREADS = 128;
 constexpr int FAR_TS = 64;  // source triangles per shared-memory tile
 
 __global__ void far_geom_kernel(const double *__restrict__ verts, const int *__restrict__ tris,
-                                int nt, float4 *__restrict__ pt, float4 *__restrict__ tn,
+                                int nt, float4 *__restrict__ pt, float4 *__restrict__ poff,
+                                float4 *__restrict__ cen, float4 *__restrict__ tn,
                                 int4 *__restrict__ tv, double *__restrict__ tgeo) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
@@ -65,13 +66,25 @@ __global__ void far_geom_kernel(const double *__restrict__ verts, const int *__r
     const double len = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
     const double area = 0.5 * len;
     double n[3] = {c[0] / len, c[1] / len, c[2] / len};
+    double cc[3];
+    for (int j = 0; j < 3; ++j) cc[j] = (P[0][j] + P[1][j] + P[2][j]) / 3.0;
     for (int q = 0; q < 6; ++q) {
         double b[3], w;
         rule_point(q, b, w);
         double x[3];
         for (int j = 0; j < 3; ++j) x[j] = b[0] * P[0][j] + b[1] * P[1][j] + b[2] * P[2][j];
         pt[6 * t + q] = make_float4((float)x[0], (float)x[1], (float)x[2], (float)(w * area));
+        poff[6 * t + q] = make_float4((float)(x[0] - cc[0]), (float)(x[1] - cc[1]),
+                                      (float)(x[2] - cc[2]), (float)(w * area));
     }
+    // centroid as an unevaluated float pair (hi + lo), about 48 significant bits
+    float hi[3], lo[3];
+    for (int j = 0; j < 3; ++j) {
+        hi[j] = (float)cc[j];
+        lo[j] = (float)(cc[j] - (double)hi[j]);
+    }
+    cen[2 * t] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    cen[2 * t + 1] = make_float4(lo[0], lo[1], lo[2], 0.f);
     const double h = n[0] * P[0][0] + n[1] * P[0][1] + n[2] * P[0][2];
     tn[t] = make_float4((float)n[0], (float)n[1], (float)n[2], (float)h);
     tv[t] = make_int4(v[0], v[1], v[2], 0);
@@ -173,28 +186,97 @@ struct PairAcc {
     f2 t1r, t1i, ur, ui, t3r, t3i;
 };
 
-// e^{i k r} for one point: for |k r| below 64 pi the MUFU sine / cosine take
-// the argument directly (their own reduction has the same FP32 rounding as an
-// explicit one); REDUCE folds k r / (2 pi) to [-1/2, 1/2] revolutions first.
-template <bool REDUCE>
-__device__ __forceinline__ void phasor1(float kr, float r, float krev, float &s, float &c) {
-    if (REDUCE) {
-        const float t = r * krev;
-        __sincosf(6.28318530717958647692f * (t - rintf(t)), &s, &c);
-    } else {
-        __sincosf(kr, &s, &c);
+// Per (test triangle, source triangle) data of the centred (large k r)
+// variant: D = c_x - c_y (centroid difference, FP32 rounding of a
+// float-float value), r_c = |D| and the phase k r_c as a fraction of a
+// revolution in [-1/2, 1/2], from float-float arithmetic (about 48 bits).
+struct CenterPair {
+    f2 Dx, Dy, Dz, rc, b0, b1;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float v = s - a;
+    e = (a - (s - v)) + (b - v);
+}
+
+// a - b for float-float a = (ah, al), b = (bh, bl); result (h, l)
+__device__ __forceinline__ void ff_sub(float ah, float al, float bh, float bl, float &h, float &l) {
+    float s, e;
+    two_sum(ah, -bh, s, e);
+    e += al - bl;
+    h = s + e;
+    l = e - (h - s);
+}
+
+// frac(r (kh + kl)) in revolutions for float-float r = (rh, rl)
+__device__ __forceinline__ float ff_phase_rev(float rh, float rl, float kh, float kl) {
+    const float p = rh * kh;
+    const float pe = fmaf(rh, kh, -p) + fmaf(rh, kl, rl * kh);
+    const float n = rintf(p);
+    return (p - n) + pe;
+}
+
+__device__ __forceinline__ CenterPair center_pair(const float4 &cth, const float4 &ctl,
+                                                  const float4 &csh, const float4 &csl,
+                                                  float k0h, float k0l, float k1h, float k1l) {
+    float dh[3], dl[3];
+    ff_sub(cth.x, ctl.x, csh.x, csl.x, dh[0], dl[0]);
+    ff_sub(cth.y, ctl.y, csh.y, csl.y, dh[1], dl[1]);
+    ff_sub(cth.z, ctl.z, csh.z, csl.z, dh[2], dl[2]);
+    // |D|^2 as float-float: exact squares of the high parts plus cross terms
+    float sh = 0.f, sl = 0.f;
+    for (int i = 0; i < 3; ++i) {
+        const float p = dh[i] * dh[i];
+        const float e = fmaf(dh[i], dh[i], -p) + 2.f * dh[i] * dl[i];
+        float s, t;
+        two_sum(sh, p, s, t);
+        sh = s;
+        sl += t + e;
     }
+    // square root with one Newton correction
+    const float rs = sqrtf(sh);
+    const float corr = (fmaf(-rs, rs, sh) + sl) * (0.5f / rs);
+    const float rh = rs + corr;
+    const float rl = corr - (rh - rs);
+    CenterPair c;
+    c.Dx = dup2(dh[0]);
+    c.Dy = dup2(dh[1]);
+    c.Dz = dup2(dh[2]);
+    c.rc = dup2(rh);
+    c.b0 = dup2(ff_phase_rev(rh, rl, k0h, k0l));
+    c.b1 = dup2(ff_phase_rev(rh, rl, k1h, k1l));
+    return c;
 }
 
 // One source point against the two test points of the thread, both
 // wavenumbers, packed FP32 arithmetic.  P[0..4], P5 hold the signed
 // duplicated source data; (mnx, mny, mnz) is the negated test-triangle
-// normal; wq2 the rule weight.
-template <bool REDUCE>
+// normal; wq2 the rule weight.  Plain variant: (X, Y, Z) are the test points
+// and the source coordinates absolute; the MUFU sine / cosine take k r
+// directly (their own argument scaling has the same FP32 rounding as an
+// explicit reduction).  CENTRED variant (large k r): coordinates are offsets
+// from the triangle centroids, x - y = D + delta, and the phase is
+// k r = k r_c + k (2 D.delta + delta.delta) / (r + r_c) with k r_c reduced in
+// float-float arithmetic once per triangle pair.
+template <bool CENTRED>
 __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, const f2 &P5, f2 mnx,
-                                          f2 mny, f2 mnz, f2 wq2, const FarConst2 &c, PairAcc &A) {
+                                          f2 mny, f2 mnz, f2 wq2, const FarConst2 &c,
+                                          const CenterPair &cp, PairAcc &A) {
     const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3], P4 = P[4];
-    const f2 dx = add2(X, lo2(P0)), dy = add2(Y, hi2(P0)), dz = add2(Z, lo2(P1));  // x - y
+    f2 dx, dy, dz, ddx, ddy, ddz;
+    if (CENTRED) {
+        ddx = add2(X, lo2(P0));  // delta = a - b
+        ddy = add2(Y, hi2(P0));
+        ddz = add2(Z, lo2(P1));
+        dx = add2(ddx, cp.Dx);
+        dy = add2(ddy, cp.Dy);
+        dz = add2(ddz, cp.Dz);
+    } else {
+        dx = add2(X, lo2(P0));  // x - y
+        dy = add2(Y, hi2(P0));
+        dz = add2(Z, lo2(P1));
+    }
     f2 r2 = mul2(dx, dx);
     r2 = fma2(dy, dy, r2);
     r2 = fma2(dz, dz, r2);
@@ -208,12 +290,32 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
     const f2 kr0 = mul2(r, c.k0), kr1 = mul2(r, c.k1);
     const f2 nkr0 = mul2(r, c.nk0), nkr1 = mul2(r, c.nk1);
     f2 s0, c0, s1, c1;
-    phasor1<REDUCE>(kr0.x, r.x, c.k0r.x, s0.x, c0.x);
-    phasor1<REDUCE>(kr0.y, r.y, c.k0r.y, s0.y, c0.y);
-    phasor1<REDUCE>(kr1.x, r.x, c.k1r.x, s1.x, c1.x);
-    phasor1<REDUCE>(kr1.y, r.y, c.k1r.y, s1.y, c1.y);
+    if (CENTRED) {
+        f2 num = mul2(ddx, ddx);
+        num = fma2(ddy, ddy, num);
+        num = fma2(ddz, ddz, num);
+        f2 dd = mul2(ddx, cp.Dx);
+        dd = fma2(ddy, cp.Dy, dd);
+        dd = fma2(ddz, cp.Dz, dd);
+        num = fma2(dd, dup2(2.f), num);  // r^2 - r_c^2
+        const f2 den = add2(r, cp.rc);
+        const f2 dlt = mul2(num, make_float2(__frcp_rn(den.x), __frcp_rn(den.y)));  // r - r_c
+        const f2 ph0 = mul2(fma2(c.k0r, dlt, cp.b0), dup2(6.28318530717958647692f));
+        const f2 ph1 = mul2(fma2(c.k1r, dlt, cp.b1), dup2(6.28318530717958647692f));
+        __sincosf(ph0.x, &s0.x, &c0.x);
+        __sincosf(ph0.y, &s0.y, &c0.y);
+        __sincosf(ph1.x, &s1.x, &c1.x);
+        __sincosf(ph1.y, &s1.y, &c1.y);
+    } else {
+        __sincosf(kr0.x, &s0.x, &c0.x);
+        __sincosf(kr0.y, &s0.y, &c0.y);
+        __sincosf(kr1.x, &s1.x, &c1.x);
+        __sincosf(kr1.y, &s1.y, &c1.y);
+    }
     const f2 psr = hi2(P1), psi = lo2(P2), mpsr = hi2(P2), mpsi = lo2(P3);
     const f2 phr = hi2(P3), phi = lo2(P4), mphr = hi2(P4), mphi = P5;
+    (void)mpsr;
+    (void)mphr;
     // V block (G0 + rho G1) psi, without 1/(4 pi)
     const f2 gpr = mul2(fma2(c.rho, c1, c0), ri), gpi = mul2(fma2(c.rho, s1, s0), ri);
     A.u1r = fma2(gpr, psr, fma2(gpi, mpsi, A.u1r));
@@ -248,17 +350,21 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
 //   A  = sum_s (sum_q w_q (G0 + G1/rho)) c_s
 // with G, H here without the factor 1/(4 pi) (applied in the gather).  Sums
 // run per 64-triangle tile, then tile sums are added to running sums.
-template <bool REDUCE>
+// CENTRED: pt holds offsets from the test-triangle centroid and cen the
+// float-float centroids (see far_pair2).
+template <bool CENTRED>
 __global__ void __launch_bounds__(FAR_THREADS)
-far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ tn,
-           const int4 *__restrict__ tv, const float4 *__restrict__ sP,
-           const float2 *__restrict__ sP5, const float4 *__restrict__ sC, int nt, int npts,
-           int tris_per_split, FarConst2 c, float *__restrict__ part) {
+far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
+           const float4 *__restrict__ tn, const int4 *__restrict__ tv,
+           const float4 *__restrict__ sP, const float2 *__restrict__ sP5,
+           const float4 *__restrict__ sC, int nt, int npts, int tris_per_split, FarConst2 c,
+           float4 kff, float *__restrict__ part) {
     __shared__ float4 shP[FAR_TS * 6 * 5];
     __shared__ float2 shP5[FAR_TS * 6];
     __shared__ float4 shN[FAR_TS];
     __shared__ float4 shC[FAR_TS * 5];
     __shared__ int4 shV[FAR_TS];
+    __shared__ float4 shCen[CENTRED ? 2 * FAR_TS : 1];
 
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int split = blockIdx.y;
@@ -273,6 +379,11 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ tn,
     const int4 vt = tv[tau];
     const f2 mnx = dup2(-n4.x), mny = dup2(-n4.y), mnz = dup2(-n4.z);
     const f2 W1 = dup2((float)kQw1), W2 = dup2((float)kQw2);
+    float4 cth = make_float4(0.f, 0.f, 0.f, 0.f), ctl = cth;
+    if (CENTRED) {
+        cth = cen[2 * tau];
+        ctl = cen[2 * tau + 1];
+    }
 
     f2 run[10];
 #pragma unroll
@@ -289,6 +400,8 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ tn,
             shN[i] = make_float4(-ns.x, -ns.y, -ns.z, ns.w);
             shV[i] = tv[t0 + i];
         }
+        if (CENTRED)
+            for (int i = threadIdx.x; i < 2 * cnt; i += blockDim.x) shCen[i] = cen[2 * (size_t)t0 + i];
         __syncthreads();
 
         PairAcc A;
@@ -301,14 +414,22 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ tn,
                                (vs.z == vt.x) | (vs.z == vt.y) | (vs.z == vt.z);
             if (touch) continue;
             const float4 mns = shN[s];  // (-n_y, n_y.P0)
-            // -(x - y).n_y = h_y - x.n_y, constant over the source triangle
-            const f2 xnyn = fma2(Z, dup2(mns.z), fma2(Y, dup2(mns.y), fma2(X, dup2(mns.x), dup2(mns.w))));
+            CenterPair cp;
+            f2 xnyn;  // -(x - y).n_y, constant over the source triangle
+            if (CENTRED) {
+                cp = center_pair(cth, ctl, shCen[2 * s], shCen[2 * s + 1], kff.x, kff.y, kff.z, kff.w);
+                // (x - y).n_y = (c_x - c_y + a).n_y since c_y lies in the source plane
+                const float dn = cp.Dx.x * mns.x + cp.Dy.x * mns.y + cp.Dz.x * mns.z;
+                xnyn = fma2(Z, dup2(mns.z), fma2(Y, dup2(mns.y), fma2(X, dup2(mns.x), dup2(dn))));
+            } else {
+                xnyn = fma2(Z, dup2(mns.z), fma2(Y, dup2(mns.y), fma2(X, dup2(mns.x), dup2(mns.w))));
+            }
             const float nxnyn = n4.x * mns.x + n4.y * mns.y + n4.z * mns.z;  // -n_x.n_y
             A.t1r = A.t1i = A.ur = A.ui = A.t3r = A.t3i = make_float2(0.f, 0.f);
 #pragma unroll
             for (int q = 0; q < 6; ++q)
-                far_pair2<REDUCE>(X, Y, Z, &shP[30 * s + 5 * q], shP5[6 * s + q], mnx, mny, mnz,
-                                  q < 3 ? W1 : W2, c, A);
+                far_pair2<CENTRED>(X, Y, Z, &shP[30 * s + 5 * q], shP5[6 * s + q], mnx, mny, mnz,
+                                   q < 3 ? W1 : W2, c, cp, A);
             // u1 += (x - y).n_y T1 = (-(x - y).n_y)(-T1);  u2 += (-n_x.n_y) U
             A.u1r = fma2(xnyn, A.t1r, A.u1r);
             A.u1i = fma2(xnyn, A.t1i, A.u1i);
@@ -398,6 +519,8 @@ int far_setup_geometry(osrc_problem *pb, cudaStream_t st) {
     osrc_mesh *m = pb->mesh;
     const int nt = pb->nt;
     OSRC_TRY(pb->d_pt.alloc(m->ctx, 6 * (size_t)nt));
+    OSRC_TRY(pb->d_poff.alloc(m->ctx, 6 * (size_t)nt));
+    OSRC_TRY(pb->d_cen.alloc(m->ctx, 2 * (size_t)nt));
     OSRC_TRY(pb->d_tn.alloc(m->ctx, nt));
     OSRC_TRY(pb->d_tv.alloc(m->ctx, nt));
     OSRC_TRY(pb->d_tgeo.alloc(m->ctx, 16 * (size_t)nt));
@@ -405,23 +528,12 @@ int far_setup_geometry(osrc_problem *pb, cudaStream_t st) {
     OSRC_TRY(pb->d_sP5.alloc(m->ctx, 6 * (size_t)nt));
     OSRC_TRY(pb->d_sC.alloc(m->ctx, 5 * (size_t)nt));
     far_geom_kernel<<<(nt + 127) / 128, 128, 0, st>>>(m->d_verts.p, m->d_tris.p, nt, pb->d_pt.p,
-                                                      pb->d_tn.p, pb->d_tv.p, pb->d_tgeo.p);
+                                                      pb->d_poff.p, pb->d_cen.p, pb->d_tn.p,
+                                                      pb->d_tv.p, pb->d_tgeo.p);
     pb->launches++;
     OSRC_CK(cudaGetLastError());
-    // split the source range so that the grid covers the GPU several times
-    int dev = m->ctx->device, sms = 0, per_sm = 0;
-    OSRC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    OSRC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far_kernel<false>, FAR_THREADS, 0));
-    if (per_sm < 1) per_sm = 1;
-    const int bx = (pb->npts / 2 + FAR_THREADS - 1) / FAR_THREADS;
-    const int slots = sms * per_sm;
-    int ns = (4 * slots + bx - 1) / bx;
-    const int max_ns = (nt + FAR_TS - 1) / FAR_TS;
-    if (ns > max_ns) ns = max_ns;
-    if (ns < 1) ns = 1;
-    pb->nsplit = ns;
     // largest phase k r over the mesh (bounding-box diagonal): beyond 64 pi
-    // radians the explicit reduction to [-1/2, 1/2] revolutions is used
+    // radians the centred variant with float-float phases is used
     {
         double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
         for (int i = 0; i < m->nv; ++i)
@@ -434,6 +546,21 @@ int far_setup_geometry(osrc_problem *pb, cudaStream_t st) {
         const double kmax = fmax(pb->p.k_ext, pb->p.k_int);
         pb->far_reduce = kmax * diag > 64.0 * 3.14159265358979323846;
     }
+    // split the source range so that the grid covers the GPU several times
+    int dev = m->ctx->device, sms = 0, per_sm = 0;
+    OSRC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (pb->far_reduce)
+        OSRC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far_kernel<true>, FAR_THREADS, 0));
+    else
+        OSRC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far_kernel<false>, FAR_THREADS, 0));
+    if (per_sm < 1) per_sm = 1;
+    const int bx = (pb->npts / 2 + FAR_THREADS - 1) / FAR_THREADS;
+    const int slots = sms * per_sm;
+    int ns = (4 * slots + bx - 1) / bx;
+    const int max_ns = (nt + FAR_TS - 1) / FAR_TS;
+    if (ns > max_ns) ns = max_ns;
+    if (ns < 1) ns = 1;
+    pb->nsplit = ns;
     OSRC_TRY(pb->d_part.alloc(m->ctx, (size_t)ns * 10 * pb->npts));
     return OSRC_OK;
 }
@@ -456,7 +583,8 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
     const int use_far = (part & OSRC_PART_FAR) ? 1 : 0;
     const int use_near = (part & OSRC_PART_NEAR) ? 1 : 0;
     if (use_far) {
-        far_prep_kernel<<<(nt + 127) / 128, 128, 0, st>>>(x, nv, nt, m->d_tris.p, pb->d_pt.p,
+        const float4 *src_pts = pb->far_reduce ? pb->d_poff.p : pb->d_pt.p;
+        far_prep_kernel<<<(nt + 127) / 128, 128, 0, st>>>(x, nv, nt, m->d_tris.p, src_pts,
                                                           pb->d_tgeo.p, pb->d_sP.p, pb->d_sP5.p,
                                                           pb->d_sC.p);
         pb->launches++;
@@ -474,6 +602,10 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
         c.irho = d2(1.0 / rho);
         c.dk0 = d2(k0 * k0);
         c.dk1 = d2(k1 * k1 / rho);
+        // k / (2 pi) as float pairs (hi, lo) for the float-float phases
+        const double q0 = k0 * inv2pi, q1 = k1 * inv2pi;
+        const float q0h = (float)q0, q1h = (float)q1;
+        const float4 kff = make_float4(q0h, (float)(q0 - (double)q0h), q1h, (float)(q1 - (double)q1h));
         const int ns = pb->nsplit;
         const int tps = (nt + ns - 1) / ns;
         dim3 grid((npts / 2 + FAR_THREADS - 1) / FAR_THREADS, ns);
@@ -482,13 +614,15 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
             OSRC_CK(cudaEventRecord(pb->prof_ev[0], st));
         }
         if (pb->far_reduce)
-            far_kernel<true><<<grid, FAR_THREADS, 0, st>>>(pb->d_pt.p, pb->d_tn.p, pb->d_tv.p,
-                                                           pb->d_sP.p, pb->d_sP5.p, pb->d_sC.p, nt,
-                                                           npts, tps, c, pb->d_part.p);
+            far_kernel<true><<<grid, FAR_THREADS, 0, st>>>(pb->d_poff.p, pb->d_cen.p, pb->d_tn.p,
+                                                           pb->d_tv.p, pb->d_sP.p, pb->d_sP5.p,
+                                                           pb->d_sC.p, nt, npts, tps, c, kff,
+                                                           pb->d_part.p);
         else
-            far_kernel<false><<<grid, FAR_THREADS, 0, st>>>(pb->d_pt.p, pb->d_tn.p, pb->d_tv.p,
-                                                            pb->d_sP.p, pb->d_sP5.p, pb->d_sC.p, nt,
-                                                            npts, tps, c, pb->d_part.p);
+            far_kernel<false><<<grid, FAR_THREADS, 0, st>>>(pb->d_pt.p, pb->d_cen.p, pb->d_tn.p,
+                                                            pb->d_tv.p, pb->d_sP.p, pb->d_sP5.p,
+                                                            pb->d_sC.p, nt, npts, tps, c, kff,
+                                                            pb->d_part.p);
         pb->launches++;
         if (pb->prof_on) {
             OSRC_CK(cudaEventRecord(pb->prof_ev[1], st));

@@ -107,6 +107,8 @@ struct osrc_problem {
 
     // ---- far field (FP32): static geometry -----------------------------
     DBuf<float4> d_pt;   // [6nt]  point x, y, z, quadrature weight * area
+    DBuf<float4> d_poff; // [6nt]  point minus triangle centroid, quadrature weight * area
+    DBuf<float4> d_cen;  // [2nt]  triangle centroid as float pairs (hi, lo)
     DBuf<float4> d_tn;   // [nt]   outward normal, plane offset n.P0
     DBuf<int4> d_tv;     // [nt]   vertex indices
     // ---- far field: per-apply workspace ----------------------------------
@@ -115,7 +117,7 @@ struct osrc_problem {
     DBuf<float4> d_sC;   // [nt][5] c_sigma components with both signs, duplicated pairs
     DBuf<float> d_part;       // [nsplit][6nt][10] per test point partial sums
     int nsplit = 1;
-    bool far_reduce = false;  // explicit phase reduction for large k r
+    bool far_reduce = false;  // centred far kernel with float-float phases (large k r)
     // ---- FP64 per-triangle geometry: area, normal, curls of the hat functions
     DBuf<double> d_tgeo;      // [nt][16]
     // ---- near field CSR (vertex pairs of touching triangles), FP64 --------
