@@ -186,6 +186,64 @@ enum { OSRC_HOST_BUFFERS = 1 };
 int osrc_gmres_solve(osrc_problem *pb, const void *b, void *x, int nrhs, double tol,
                      int maxit, int flags, osrc_solve_info *info, void *stream);
 
+/* ---- serving loop ------------------------------------------------------------------ */
+/* A continuous-batching server for solve requests of uneven mesh size and
+ * frequency (the serving pattern that the solver is deployed in).  A worker
+ * thread owns the GPU work; each request is split into one GMRES job per
+ * right-hand side; jobs are admitted into at most max_active slots as slots
+ * free up and as the context's device-memory budget (osrc_create) allows.
+ * Every slot has its own stream and workspace, so jobs overlap on the device;
+ * each result is bit-identical to solving the request alone because no kernel
+ * or launch configuration depends on the mix.  Resident problem state (mesh
+ * topology, near-field CSR, M, S, Pade constants) is cached by mesh and
+ * parameters and shared by every right-hand side and request that matches;
+ * unreferenced entries are evicted least-recently-used when memory is
+ * needed.  While a server exists its worker is the only user of the context:
+ * create no other handles on it.  Requests that cannot fit even alone finish
+ * with OSRC_OUT_OF_MEMORY. */
+typedef struct osrc_server osrc_server;
+
+typedef struct osrc_request {
+    const double *verts;   /* host, nv x 3; copied at submit */
+    int32_t nv;
+    const int32_t *tris;   /* host, nt x 3, counter-clockwise from outside; copied */
+    int32_t nt;
+    osrc_params params;    /* wavenumbers, density ratio, OSRC and quadrature options */
+    int rhs_kind;          /* 0: plane waves (src = unit directions), 1: point sources (src = positions) */
+    const double *src;     /* host, nrhs x 3; copied */
+    int nrhs;
+    double tol;            /* GMRES tolerance (preconditioned relative residual) */
+    int maxit;             /* GMRES iteration cap */
+} osrc_request;
+
+typedef struct osrc_server_stats {
+    long long submitted, completed, failed, jobs_started;
+    long long cache_hits, cache_misses, evictions;
+    long long active_peak;  /* most slots busy at once */
+    size_t mem_peak;        /* most device bytes allocated through the context */
+    size_t mem_used;        /* device bytes allocated now */
+} osrc_server_stats;
+
+/* Starts a server with max_active slots (1..64) on the context. */
+int osrc_server_create(osrc_ctx *ctx, int max_active, osrc_server **out);
+/* Queues a request (validates the mesh on the host); *id identifies it. */
+int osrc_server_submit(osrc_server *sv, const osrc_request *req, long long *id);
+/* Non-blocking: *done = 1 once every right-hand side has finished; then
+ * latency_ms (submit to completion, host clock) and info (worst residuals,
+ * summed iterations and phase times) are filled and the request's status is
+ * returned.  May be called until osrc_server_result releases the request. */
+int osrc_server_poll(osrc_server *sv, long long id, int *done, double *latency_ms,
+                     osrc_solve_info *info);
+/* Blocks until the request finishes (its status) or timeout_s passes (OSRC_TIMEOUT). */
+int osrc_server_wait(osrc_server *sv, long long id, double timeout_s);
+/* Copies the solution (host, nrhs x 2nv complex, [psi; phi] per right-hand
+ * side) and releases the request; OSRC_TIMEOUT if it has not finished. */
+int osrc_server_result(osrc_server *sv, long long id, void *x_host);
+int osrc_server_get_stats(osrc_server *sv, osrc_server_stats *out);
+/* Stops the worker (jobs in flight finish their current step; queued
+ * requests are dropped) and frees every resource of the server. */
+void osrc_server_destroy(osrc_server *sv);
+
 /* ---- allocation-free batched solve ------------------------------------------------- */
 /* The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory when they need a solve: code running

@@ -66,6 +66,29 @@ class osrc_solve_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class osrc_request(ctypes.Structure):
+    _fields_ = [
+        ("verts", ctypes.c_void_p), ("nv", ctypes.c_int32),
+        ("tris", ctypes.c_void_p), ("nt", ctypes.c_int32),
+        ("params", osrc_params), ("rhs_kind", ctypes.c_int),
+        ("src", ctypes.c_void_p), ("nrhs", ctypes.c_int),
+        ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
+    ]
+
+
+class osrc_server_stats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+        ("failed", ctypes.c_longlong), ("jobs_started", ctypes.c_longlong),
+        ("cache_hits", ctypes.c_longlong), ("cache_misses", ctypes.c_longlong),
+        ("evictions", ctypes.c_longlong), ("active_peak", ctypes.c_longlong),
+        ("mem_peak", ctypes.c_size_t), ("mem_used", ctypes.c_size_t),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _VP = ctypes.c_void_p
 _DP = ctypes.POINTER(ctypes.c_double)
 _IP = ctypes.POINTER(ctypes.c_int32)
@@ -99,6 +122,16 @@ SIGNATURES = {
                                                   _DP, _DP, _VP, _VP, ctypes.c_double,
                                                   ctypes.c_int, ctypes.c_int,
                                                   ctypes.POINTER(ctypes.c_int), _VP]),
+    "osrc_server_create": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(_VP)]),
+    "osrc_server_submit": (ctypes.c_int, [_VP, ctypes.POINTER(osrc_request),
+                                          ctypes.POINTER(ctypes.c_longlong)]),
+    "osrc_server_poll": (ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(osrc_solve_info)]),
+    "osrc_server_wait": (ctypes.c_int, [_VP, ctypes.c_longlong, ctypes.c_double]),
+    "osrc_server_result": (ctypes.c_int, [_VP, ctypes.c_longlong, _VP]),
+    "osrc_server_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(osrc_server_stats)]),
+    "osrc_server_destroy": (None, [_VP]),
     "osrc_launch_count": (ctypes.c_longlong, [_VP]),
     "osrc_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "osrc_far_kernel_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong),
@@ -304,6 +337,58 @@ def osrc_shifted_solve_noalloc(row_ptr, col_idx, M_vals, S_vals, alpha, beta, f,
         int(maxit), int(conj), it, _stream(stream))
     _check(s, "osrc_shifted_solve_noalloc")
     return list(it)
+
+
+def osrc_server_create(ctx, max_active=4):
+    h = _VP()
+    _check(lib().osrc_server_create(ctx, int(max_active), ctypes.byref(h)), "osrc_server_create")
+    return h
+
+
+def osrc_server_submit(sv, verts, tris, params, src, rhs_kind=0, tol=1e-5, maxit=500):
+    """Queues a request; returns its id.  verts (nv, 3), tris (nt, 3), src
+    (nrhs, 3) host arrays; params an osrc_params."""
+    v, _ = _host_f64(verts)
+    t, _ = _host_i32(tris)
+    s = np.ascontiguousarray(np.atleast_2d(src), dtype=np.float64)
+    rq = osrc_request(v.ctypes.data, v.shape[0], t.ctypes.data, t.shape[0], params,
+                      int(rhs_kind), s.ctypes.data, s.shape[0], float(tol), int(maxit))
+    rid = ctypes.c_longlong()
+    _check(lib().osrc_server_submit(sv, ctypes.byref(rq), ctypes.byref(rid)), "osrc_server_submit")
+    return rid.value
+
+
+def osrc_server_poll(sv, rid):
+    """Returns (done, status, latency_ms, info dict or None)."""
+    done = ctypes.c_int()
+    lat = ctypes.c_double()
+    info = osrc_solve_info()
+    s = lib().osrc_server_poll(sv, int(rid), ctypes.byref(done), ctypes.byref(lat), ctypes.byref(info))
+    if done.value:
+        return True, s, lat.value, info.as_dict()
+    if s != OSRC_OK:
+        raise OsrcError(s, "osrc_server_poll")
+    return False, s, None, None
+
+
+def osrc_server_wait(sv, rid, timeout_s=600.0):
+    return lib().osrc_server_wait(sv, int(rid), float(timeout_s))
+
+
+def osrc_server_result(sv, rid, nrhs, nv):
+    x = np.zeros((nrhs, 2 * nv), dtype=np.complex128)
+    s = lib().osrc_server_result(sv, int(rid), ctypes.c_void_p(x.ctypes.data))
+    return s, x
+
+
+def osrc_server_get_stats(sv):
+    st = osrc_server_stats()
+    _check(lib().osrc_server_get_stats(sv, ctypes.byref(st)), "osrc_server_get_stats")
+    return st.as_dict()
+
+
+def osrc_server_destroy(sv):
+    lib().osrc_server_destroy(sv)
 
 
 def osrc_launch_count(pb):

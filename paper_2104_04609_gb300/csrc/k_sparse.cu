@@ -353,14 +353,7 @@ int check_kry(osrc_problem *pb, int nsys, cudaStream_t st) {
     int stat[KRY_MAX_SYS];
     OSRC_CK(cudaMemcpyAsync(stat, pb->d_kry_stat.p, nsys * sizeof(int), cudaMemcpyDeviceToHost, st));
     OSRC_CK(cudaStreamSynchronize(st));
-    int worst = 0;
-    for (int i = 0; i < nsys; ++i) {
-        if (stat[i] <= -1000000) return OSRC_BREAKDOWN;
-        if (stat[i] < 0) return OSRC_NOT_CONVERGED;
-        if (stat[i] > worst) worst = stat[i];
-    }
-    if (worst > pb->inner_last_max) pb->inner_last_max = worst;
-    return OSRC_OK;
+    return kry_status_host(pb, stat, nsys);
 }
 
 }  // namespace
@@ -419,7 +412,25 @@ int mass_solve(osrc_problem *pb, const double2 *x, double2 *y, cudaStream_t st) 
 //   (1 + B X)^-1 u2 = (M - B S / k_eps^2)^-1 y2
 // so the mass solve of row 1 and all 2 N_Pade + 1 shifted systems run as one
 // batched launch (row 2 needs no mass solve at all).
+int osrc_precond_nsys(const osrc_problem *pb) { return 2 * pb->p.n_pade + 2; }
+
+int kry_status_host(osrc_problem *pb, const int *stat, int nsys) {
+    int worst = 0;
+    for (int i = 0; i < nsys; ++i) {
+        if (stat[i] <= -1000000) return OSRC_BREAKDOWN;
+        if (stat[i] < 0) return OSRC_NOT_CONVERGED;
+        if (stat[i] > worst) worst = stat[i];
+    }
+    if (worst > pb->inner_last_max) pb->inner_last_max = worst;
+    return OSRC_OK;
+}
+
 int osrc_precond_fused(osrc_problem *pb, const double2 *y, double2 *z, cudaStream_t st) {
+    OSRC_TRY(osrc_precond_fused_async(pb, y, z, st));
+    return check_kry(pb, osrc_precond_nsys(pb), st);
+}
+
+int osrc_precond_fused_async(osrc_problem *pb, const double2 *y, double2 *z, cudaStream_t st) {
     const int n = pb->nv, np = pb->p.n_pade;
     const double2 ke2 = cmul(pb->k_eps, pb->k_eps);
     const double2 inv_ke2 = cdiv(cd(1.0, 0.0), ke2);
@@ -475,7 +486,7 @@ int osrc_precond_fused(osrc_problem *pb, const double2 *y, double2 *z, cudaStrea
     osrc_combine_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, c, sol, z);
     pb->launches++;
     OSRC_CK(cudaGetLastError());
-    return check_kry(pb, b.nsys, st);
+    return OSRC_OK;
 }
 
 // P x for a strong-form vector x: P x = P M^-1 (M x).

@@ -553,20 +553,11 @@ extern "C" int osrc_precond_apply(osrc_problem *pb, const void *x, void *y, int 
 // ---------------------------------------------------------------------------
 // GMRES (Sec. 3.1): no restart, x0 = 0, preconditioned relative residual
 // ---------------------------------------------------------------------------
-namespace {
+// pinned host block of a workspace: doubles [0, 16), then status ints
+static const int kHostDoubles = 16;
+static const int kHostInts = 48;
 
-struct PhaseTimer {
-    cudaEvent_t ev[4];
-    bool ok = false;
-    PhaseTimer() {
-        ok = true;
-        for (auto &e : ev)
-            if (cudaEventCreate(&e) != cudaSuccess) ok = false;
-    }
-    ~PhaseTimer() {
-        for (auto &e : ev) cudaEventDestroy(e);
-    }
-};
+static int *host_stat(osrc_problem *pb) { return (int *)(pb->h_res + kHostDoubles); }
 
 int ensure_gmres_workspace(osrc_problem *pb, int maxit) {
     osrc_ctx *ctx = pb->mesh->ctx;
@@ -577,7 +568,7 @@ int ensure_gmres_workspace(osrc_problem *pb, int maxit) {
         pb->d_givens.release();
         OSRC_TRY(pb->d_basis.alloc(ctx, (size_t)(maxit + 1) * n));
         OSRC_TRY(pb->d_h.alloc(ctx, (size_t)(maxit + 1) * maxit));
-        OSRC_TRY(pb->d_givens.alloc(ctx, 4 * (size_t)(maxit + 1) + 2 * (size_t)(maxit + 1)));
+        OSRC_TRY(pb->d_givens.alloc(ctx, 6 * (size_t)(maxit + 1)));
         pb->basis_cap = maxit;
     }
     if (!pb->d_w.p) {
@@ -587,102 +578,265 @@ int ensure_gmres_workspace(osrc_problem *pb, int maxit) {
         OSRC_TRY(pb->d_b1.alloc(ctx, n));
         OSRC_TRY(pb->d_x1.alloc(ctx, n));
     }
-    if (!pb->h_res) OSRC_CK(cudaMallocHost((void **)&pb->h_res, 8 * sizeof(double)));
+    if (!pb->h_res)
+        OSRC_CK(cudaMallocHost((void **)&pb->h_res, kHostDoubles * sizeof(double) + kHostInts * sizeof(int)));
     return OSRC_OK;
 }
 
-// w = P M^-1 B v; timings accumulated into info
-int precond_matvec(osrc_problem *pb, const double2 *v, double2 *w, cudaStream_t st, PhaseTimer &tm,
-                   double &ms_mv, double &ms_pc) {
-    double2 *t1 = pb->d_tmp2.p;            // B v
-    if (tm.ok) cudaEventRecord(tm.ev[0], st);
-    if (pb->p.precision == OSRC_FP64_DENSE) {
-        OSRC_TRY(dense_apply(pb, v, t1, st));
-    } else {
-        OSRC_TRY(far_apply(pb, v, t1, OSRC_PART_ALL, st));
-    }
-    if (tm.ok) cudaEventRecord(tm.ev[1], st);
-    OSRC_TRY(osrc_precond_fused(pb, t1, w, st));
-    if (tm.ok) {
-        cudaEventRecord(tm.ev[2], st);
-        cudaEventSynchronize(tm.ev[2]);
-        float a = 0.f, b = 0.f;
-        cudaEventElapsedTime(&a, tm.ev[0], tm.ev[1]);
-        cudaEventElapsedTime(&b, tm.ev[1], tm.ev[2]);
-        ms_mv += a;
-        ms_pc += b;
-    }
+GmresRun::~GmresRun() {
+    if (ev) cudaEventDestroy(ev);
+    for (auto &e : tev)
+        if (e) cudaEventDestroy(e);
+}
+
+bool GmresRun::ready() const { return ev == nullptr || cudaEventQuery(ev) != cudaErrorNotReady; }
+
+// Copies the status words of the last inner solve next to the scalars and
+// marks the end of the enqueued step.
+static int end_step(GmresRun &g) {
+    osrc_problem *pb = g.pb;
+    const int nsys = osrc_precond_nsys(pb);
+    OSRC_CK(cudaMemcpyAsync(host_stat(pb), pb->d_kry_stat.p, nsys * sizeof(int), cudaMemcpyDeviceToHost, g.st));
+    OSRC_CK(cudaEventRecord(g.ev, g.st));
     return OSRC_OK;
 }
 
-int gmres_one(osrc_problem *pb, const double2 *b, double2 *x, double tol, int maxit, cudaStream_t st,
-              osrc_solve_info &info, PhaseTimer &tm) {
-    const int n = 2 * pb->nv;
-    const int ldh = maxit + 1;
-    double2 *V = pb->d_basis.p, *H = pb->d_h.p, *gv = pb->d_givens.p;
+// one Arnoldi step: w = P M^-1 B v_j, CGS2 against v_0..v_j, Givens, |g_{j+1}|/beta
+static int enqueue_iteration(GmresRun &g) {
+    osrc_problem *pb = g.pb;
+    cudaStream_t st = g.st;
+    const int n = 2 * pb->nv, j = g.j, ldh = g.maxit + 1;
+    double2 *V = pb->d_basis.p, *H = pb->d_h.p, *gv = pb->d_givens.p, *w = pb->d_w.p;
     double *sc = pb->d_scalars.p;
-    // c = P M^-1 b
-    OSRC_TRY(osrc_precond_fused(pb, b, pb->d_cvec.p, st));
+    OSRC_CK(cudaEventRecord(g.tev[0], st));
+    if (pb->p.precision == OSRC_FP64_DENSE) OSRC_TRY(dense_apply(pb, V + (size_t)j * n, pb->d_tmp2.p, st));
+    else OSRC_TRY(far_apply(pb, V + (size_t)j * n, pb->d_tmp2.p, OSRC_PART_ALL, st));
+    OSRC_CK(cudaEventRecord(g.tev[1], st));
+    OSRC_TRY(osrc_precond_fused_async(pb, pb->d_tmp2.p, w, st));
+    OSRC_CK(cudaEventRecord(g.tev[2], st));
+    double2 *hc = H + (size_t)ldh * j;
+    double2 *h2 = gv + 4 * ldh;  // second-pass projections
+    OSRC_TRY(vec_dots_conj(pb, V, j + 1, w, n, hc, st));
+    OSRC_TRY(vec_update(pb, V, j + 1, hc, w, n, st));
+    OSRC_TRY(vec_dots_conj(pb, V, j + 1, w, n, h2, st));
+    OSRC_TRY(vec_update(pb, V, j + 1, h2, w, n, st));
+    OSRC_TRY(vec_axpby(pb, cd(1, 0), hc, cd(1, 0), h2, hc, j + 1, st));
+    OSRC_TRY(vec_norm(pb, w, n, sc + 1, st));
+    OSRC_CK(cudaMemcpyAsync(hc + j + 1, sc + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    OSRC_CK(cudaMemsetAsync((double *)(hc + j + 1) + 1, 0, sizeof(double), st));
+    OSRC_TRY(vec_scale_copy(pb, w, sc + 1, V + (size_t)(j + 1) * n, n, st));
+    OSRC_TRY(gmres_givens(pb, j, ldh, H, gv, sc + 2, g.beta, st));
+    OSRC_CK(cudaMemcpyAsync(pb->h_res + 2, sc + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    OSRC_CK(cudaEventRecord(g.tev[3], st));
+    return end_step(g);
+}
+
+// x = V y, then the true weak residual |b - B x| / |b|
+static int enqueue_finish(GmresRun &g) {
+    osrc_problem *pb = g.pb;
+    cudaStream_t st = g.st;
+    const int n = 2 * pb->nv;
+    double *sc = pb->d_scalars.p;
+    if (g.j > 0) {
+        OSRC_TRY(gmres_finish(pb, g.j, g.maxit + 1, pb->d_h.p, pb->d_givens.p, pb->d_basis.p, g.x, n, st));
+    } else {
+        OSRC_CK(cudaMemsetAsync(g.x, 0, n * sizeof(double2), st));
+    }
+    double2 *t = pb->d_w.p;
+    if (pb->p.precision == OSRC_FP64_DENSE) OSRC_TRY(dense_apply(pb, g.x, t, st));
+    else OSRC_TRY(far_apply(pb, g.x, t, OSRC_PART_ALL, st));
+    OSRC_TRY(vec_axpby(pb, cd(1, 0), g.b, cd(-1, 0), t, t, n, st));
+    OSRC_TRY(vec_norm(pb, t, n, sc + 4, st));
+    OSRC_TRY(vec_norm(pb, g.b, n, sc + 5, st));
+    OSRC_CK(cudaMemcpyAsync(pb->h_res + 4, sc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    OSRC_CK(cudaEventRecord(g.ev, st));
+    return OSRC_OK;
+}
+
+int GmresRun::start(osrc_problem *p, cudaStream_t s, const double2 *b_, double2 *x_, double tol_,
+                    int maxit_) {
+    pb = p;
+    st = s;
+    b = b_;
+    x = x_;
+    tol = tol_;
+    maxit = maxit_;
+    j = 0;
+    beta = 0.0;
+    res = 1.0;
+    status = OSRC_OK;
+    converged = false;
+    info = osrc_solve_info{};
+    OSRC_TRY(ensure_gmres_workspace(pb, maxit));
+    if (!ev) OSRC_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    for (auto &e : tev)
+        if (!e) OSRC_CK(cudaEventCreate(&e));
+    const int n = 2 * pb->nv;
+    double *sc = pb->d_scalars.p;
+    // c = P M^-1 b, beta = |c|
+    OSRC_TRY(osrc_precond_fused_async(pb, b, pb->d_cvec.p, st));
     OSRC_TRY(vec_norm(pb, pb->d_cvec.p, n, sc, st));
     OSRC_CK(cudaMemcpyAsync(pb->h_res, sc, sizeof(double), cudaMemcpyDeviceToHost, st));
-    OSRC_CK(cudaStreamSynchronize(st));
-    const double beta = pb->h_res[0];
-    if (!(beta > 0.0) || !std::isfinite(beta)) {
-        OSRC_CK(cudaMemsetAsync(x, 0, n * sizeof(double2), st));
-        info.iterations = 0;
-        info.precond_residual = 0.0;
-        return std::isfinite(beta) ? OSRC_OK : OSRC_INVALID_ARG;
-    }
-    OSRC_TRY(vec_scale_copy(pb, pb->d_cvec.p, sc, V, n, st));
-    OSRC_CK(cudaMemsetAsync(H, 0, (size_t)ldh * maxit * sizeof(double2), st));
-    OSRC_CK(cudaMemsetAsync(gv, 0, 4 * (size_t)ldh * sizeof(double2), st));
-    const double2 g0 = cd(beta, 0.0);
-    OSRC_CK(cudaMemcpyAsync(gv + 2 * ldh, &g0, sizeof(double2), cudaMemcpyHostToDevice, st));
-    double res = 1.0;
-    int j = 0;
-    bool conv = false;
-    double2 *h2 = gv + 4 * ldh;  // second-pass projections
-    for (j = 0; j < maxit; ++j) {
-        double2 *w = pb->d_w.p;
-        OSRC_TRY(precond_matvec(pb, V + (size_t)j * n, w, st, tm, info.ms_matvec, info.ms_precond));
-        if (tm.ok) cudaEventRecord(tm.ev[0], st);
-        double2 *hc = H + (size_t)ldh * j;
-        // classical Gram-Schmidt, twice
-        OSRC_TRY(vec_dots_conj(pb, V, j + 1, w, n, hc, st));
-        OSRC_TRY(vec_update(pb, V, j + 1, hc, w, n, st));
-        OSRC_TRY(vec_dots_conj(pb, V, j + 1, w, n, h2, st));
-        OSRC_TRY(vec_update(pb, V, j + 1, h2, w, n, st));
-        OSRC_TRY(vec_axpby(pb, cd(1, 0), hc, cd(1, 0), h2, hc, j + 1, st));
-        OSRC_TRY(vec_norm(pb, w, n, sc + 1, st));
-        OSRC_CK(cudaMemcpyAsync(hc + j + 1, sc + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
-        OSRC_CK(cudaMemsetAsync((double *)(hc + j + 1) + 1, 0, sizeof(double), st));
-        OSRC_TRY(vec_scale_copy(pb, w, sc + 1, V + (size_t)(j + 1) * n, n, st));
-        OSRC_TRY(gmres_givens(pb, j, ldh, H, gv, sc + 2, beta, st));
-        OSRC_CK(cudaMemcpyAsync(pb->h_res, sc + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
-        if (tm.ok) cudaEventRecord(tm.ev[1], st);
-        OSRC_CK(cudaStreamSynchronize(st));
-        if (tm.ok) {
-            float a = 0.f;
-            cudaEventElapsedTime(&a, tm.ev[0], tm.ev[1]);
-            info.ms_arnoldi += a;
-        }
-        res = pb->h_res[0];
-        if (!std::isfinite(res)) return OSRC_BREAKDOWN;
-        if (res <= tol) {
-            conv = true;
-            ++j;
-            break;
-        }
-    }
-    OSRC_TRY(gmres_finish(pb, j, ldh, H, gv, V, x, n, st));
-    info.iterations = j;
-    info.precond_residual = res;
-    info.total_iterations += j;
-    if (!conv) info.converged = 0;
+    OSRC_TRY(end_step(*this));
+    phase = 1;
     return OSRC_OK;
 }
 
-}  // namespace
+int GmresRun::advance() {
+    const int n = 2 * pb->nv;
+    const int ldh = maxit + 1;
+    if (phase == 3) {  // final residual arrived
+        info.true_residual = pb->h_res[5] > 0 ? pb->h_res[4] / pb->h_res[5] : 0.0;
+        info.iterations = j;
+        info.precond_residual = (j > 0) ? res : 0.0;
+        info.converged = converged ? 1 : 0;
+        info.total_iterations = j;
+        phase = 4;
+        return status;
+    }
+    int s = kry_status_host(pb, host_stat(pb), osrc_precond_nsys(pb));
+    if (s != OSRC_OK) {
+        status = s;
+        phase = 4;
+        return s;
+    }
+    if (phase == 1) {
+        beta = pb->h_res[0];
+        if (!std::isfinite(beta)) {
+            status = OSRC_INVALID_ARG;
+            phase = 4;
+            return status;
+        }
+        if (!(beta > 0.0)) {  // zero right-hand side: x = 0
+            converged = true;
+            res = 0.0;
+            OSRC_TRY(enqueue_finish(*this));
+            phase = 3;
+            return OSRC_OK;
+        }
+        double2 *V = pb->d_basis.p, *H = pb->d_h.p, *gv = pb->d_givens.p;
+        OSRC_TRY(vec_scale_copy(pb, pb->d_cvec.p, pb->d_scalars.p, V, n, st));
+        OSRC_CK(cudaMemsetAsync(H, 0, (size_t)ldh * maxit * sizeof(double2), st));
+        OSRC_CK(cudaMemsetAsync(gv, 0, 4 * (size_t)ldh * sizeof(double2), st));
+        pb->h_res[6] = beta;  // g_0 = (beta, 0), copied from pinned memory
+        pb->h_res[7] = 0.0;
+        OSRC_CK(cudaMemcpyAsync(gv + 2 * ldh, pb->h_res + 6, sizeof(double2), cudaMemcpyHostToDevice, st));
+        OSRC_TRY(enqueue_iteration(*this));
+        phase = 2;
+        return OSRC_OK;
+    }
+    // phase 2: iteration j finished
+    {
+        float a = 0.f, bb = 0.f, c = 0.f;
+        cudaEventElapsedTime(&a, tev[0], tev[1]);
+        cudaEventElapsedTime(&bb, tev[1], tev[2]);
+        cudaEventElapsedTime(&c, tev[2], tev[3]);
+        info.ms_matvec += a;
+        info.ms_precond += bb;
+        info.ms_arnoldi += c;
+    }
+    res = pb->h_res[2];
+    ++j;
+    if (!std::isfinite(res)) {
+        status = OSRC_BREAKDOWN;
+        phase = 4;
+        return status;
+    }
+    if (res <= tol) converged = true;
+    if (converged || j >= maxit) {
+        OSRC_TRY(enqueue_finish(*this));
+        phase = 3;
+        return OSRC_OK;
+    }
+    OSRC_TRY(enqueue_iteration(*this));
+    return OSRC_OK;
+}
+
+int GmresRun::run_to_completion() {
+    while (!done()) {
+        OSRC_CK(cudaEventSynchronize(ev));
+        const int s = advance();
+        if (s != OSRC_OK) return s;
+    }
+    return status;
+}
+
+// ---------------------------------------------------------------------------
+// problem clones: shared resident state, own workspace (serving slots)
+// ---------------------------------------------------------------------------
+int problem_clone(osrc_problem *m, osrc_problem **out) {
+    *out = nullptr;
+    osrc_ctx *ctx = m->mesh->ctx;
+    osrc_problem *c = new osrc_problem;
+    c->mesh = m->mesh;
+    c->p = m->p;
+    c->nv = m->nv;
+    c->nt = m->nt;
+    c->npts = m->npts;
+    c->nsplit = m->nsplit;
+    c->far_reduce = m->far_reduce;
+    c->near_pairs = m->near_pairs;
+    c->near_nnz = m->near_nnz;
+    c->ms_nnz = m->ms_nnz;
+    c->k_osrc = m->k_osrc;
+    c->k_eps = m->k_eps;
+    c->C0 = m->C0;
+    c->g0 = m->g0;
+    c->A = m->A;
+    c->B = m->B;
+    c->g = m->g;
+    c->d_pt.borrow(m->d_pt);
+    c->d_poff.borrow(m->d_poff);
+    c->d_cen.borrow(m->d_cen);
+    c->d_tn.borrow(m->d_tn);
+    c->d_tv.borrow(m->d_tv);
+    c->d_tgeo.borrow(m->d_tgeo);
+    c->d_nr_ptr.borrow(m->d_nr_ptr);
+    c->d_nr_col.borrow(m->d_nr_col);
+    c->d_nr_val.borrow(m->d_nr_val);
+    c->d_ms_ptr.borrow(m->d_ms_ptr);
+    c->d_ms_col.borrow(m->d_ms_col);
+    c->d_M.borrow(m->d_M);
+    c->d_S.borrow(m->d_S);
+    c->d_dense.borrow(m->d_dense);
+    const int nt = m->nt, nv = m->nv;
+    const int nsys = 2 * m->p.n_pade + 2;
+    int s = OSRC_OK;
+    if ((s = c->d_sP.alloc(ctx, 30 * (size_t)nt)) || (s = c->d_sP5.alloc(ctx, 6 * (size_t)nt)) ||
+        (s = c->d_sC.alloc(ctx, 5 * (size_t)nt)) ||
+        (s = c->d_part.alloc(ctx, (size_t)c->nsplit * 10 * c->npts)) ||
+        (s = c->d_kry.alloc(ctx, 5 * (size_t)nsys * nv)) ||
+        (s = c->d_kry_rhs.alloc(ctx, (size_t)(2 + nsys) * nv)) || (s = c->d_kry_stat.alloc(ctx, 40)) ||
+        (s = c->d_kry_res.alloc(ctx, 40)) || (s = c->d_tmp2.alloc(ctx, 4 * (size_t)nv)) ||
+        (s = c->d_scalars.alloc(ctx, 64))) {
+        delete c;
+        return s;
+    }
+    *out = c;
+    return OSRC_OK;
+}
+
+size_t estimate_problem_bytes(int nv, int nt, const osrc_params &p) {
+    size_t b = 0;
+    b += (size_t)nt * (6 * 16 * 2 + 2 * 16 + 16 + 16 + 16 * 8);   // far geometry + FP64 triangle data
+    b += (size_t)nv * 20 * (4 + 64) + (size_t)nv * 4;               // near CSR
+    b += (size_t)nv * 8 * (4 + 16) + (size_t)nv * 4;                // M, S
+    b += (size_t)nt * 14 * (576 + 16 + 9 * 8);                      // transient Sauter-Schwab build
+    if (p.precision == OSRC_FP64_DENSE) b += (size_t)4 * nv * nv * 16;
+    return b;
+}
+
+size_t estimate_work_bytes(int nv, int nt, const osrc_params &p, int maxit) {
+    const size_t nsys = 2 * (size_t)p.n_pade + 2;
+    size_t b = 0;
+    b += (size_t)nt * (30 * 16 + 6 * 8 + 5 * 16);      // far source data
+    const size_t ns = std::min<size_t>(64, (size_t)(nt + 63) / 64);
+    b += ns * 10 * 6 * (size_t)nt * 4;                  // far partial sums
+    b += nsys * nv * (5 + 1) * 16 + 2 * (size_t)nv * 16 + 4 * (size_t)nv * 16;  // inner solves
+    b += (size_t)(maxit + 1) * 2 * nv * 16 + (size_t)(maxit + 1) * maxit * 16;   // Krylov basis
+    b += (size_t)5 * 2 * nv * 16 + 6 * (size_t)(maxit + 1) * 16;
+    return b;
+}
 
 extern "C" int osrc_gmres_solve(osrc_problem *pb, const void *b, void *x, int nrhs, double tol, int maxit,
                                 int flags, osrc_solve_info *info_out, void *stream) {
@@ -694,9 +848,9 @@ extern "C" int osrc_gmres_solve(osrc_problem *pb, const void *b, void *x, int nr
     const int n = 2 * pb->nv;
     osrc_solve_info info{};
     info.converged = 1;
-    PhaseTimer tm;
     pb->inner_last_max = 0;
     const bool host = (flags & OSRC_HOST_BUFFERS) != 0;
+    GmresRun run;
     for (int r = 0; r < nrhs; ++r) {
         const double2 *br;
         double2 *xr;
@@ -709,22 +863,21 @@ extern "C" int osrc_gmres_solve(osrc_problem *pb, const void *b, void *x, int nr
             br = (const double2 *)b + (size_t)n * r;
             xr = (double2 *)x + (size_t)n * r;
         }
-        OSRC_TRY(gmres_one(pb, br, xr, tol, maxit, st, info, tm));
-        // true weak residual |b - B x| / |b|
-        double *sc = pb->d_scalars.p;
-        double2 *t = pb->d_w.p;
-        if (pb->p.precision == OSRC_FP64_DENSE) OSRC_TRY(dense_apply(pb, xr, t, st));
-        else OSRC_TRY(far_apply(pb, xr, t, OSRC_PART_ALL, st));
-        OSRC_TRY(vec_axpby(pb, cd(1, 0), br, cd(-1, 0), t, t, n, st));
-        OSRC_TRY(vec_norm(pb, t, n, sc + 4, st));
-        OSRC_TRY(vec_norm(pb, br, n, sc + 5, st));
-        OSRC_CK(cudaMemcpyAsync(pb->h_res + 4, sc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        OSRC_TRY(run.start(pb, st, br, xr, tol, maxit));
+        OSRC_TRY(run.run_to_completion());
         if (host)
             OSRC_CK(cudaMemcpyAsync((double2 *)x + (size_t)n * r, xr, n * sizeof(double2),
                                     cudaMemcpyDeviceToHost, st));
-        OSRC_CK(cudaStreamSynchronize(st));
-        info.true_residual = pb->h_res[5] > 0 ? pb->h_res[4] / pb->h_res[5] : 0.0;
+        info.iterations = run.info.iterations;
+        info.precond_residual = run.info.precond_residual;
+        info.true_residual = run.info.true_residual;
+        info.ms_matvec += run.info.ms_matvec;
+        info.ms_precond += run.info.ms_precond;
+        info.ms_arnoldi += run.info.ms_arnoldi;
+        info.total_iterations += run.info.iterations;
+        if (!run.converged) info.converged = 0;
     }
+    OSRC_CK(cudaStreamSynchronize(st));
     info.inner_iterations_max = pb->inner_last_max;
     info.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (info_out) *info_out = info;

@@ -61,22 +61,34 @@ int ctx_alloc(osrc_ctx *ctx, void **p, size_t bytes);
 void ctx_free(osrc_ctx *ctx, void *p, size_t bytes);
 
 // A device buffer whose size is accounted to a context.
+// A borrowed buffer (borrow()) points at another buffer's memory and never
+// frees it; its owner must outlive it.
 template <class T>
 struct DBuf {
     T *p = nullptr;
     size_t n = 0;
     osrc_ctx *ctx = nullptr;
+    bool owned = true;
     int alloc(osrc_ctx *c, size_t count) {
         release();
         ctx = c;
         n = count;
+        owned = true;
         if (count == 0) return OSRC_OK;
         return ctx_alloc(ctx, (void **)&p, count * sizeof(T));
     }
+    void borrow(const DBuf &o) {
+        release();
+        p = o.p;
+        n = o.n;
+        ctx = o.ctx;
+        owned = false;
+    }
     void release() {
-        if (p) ctx_free(ctx, p, n * sizeof(T));
+        if (p && owned) ctx_free(ctx, p, n * sizeof(T));
         p = nullptr;
         n = 0;
+        owned = true;
     }
     ~DBuf() { release(); }
 };
@@ -150,8 +162,7 @@ struct osrc_problem {
     DBuf<double2> d_givens;   // cs (as .x), sn, g vectors
     DBuf<double> d_scalars;   // reduction scratch
     DBuf<double2> d_w, d_y, d_x1, d_b1, d_cvec;  // 2nv vectors
-    DBuf<double> h_pinned_dummy;
-    double *h_res = nullptr;  // pinned host word for the residual estimate
+    double *h_res = nullptr;  // pinned host block: doubles [0, 16), then ints (inner status)
     // ---- far-kernel event timing -------------------------------------------------
     bool prof_on = false, prof_pending = false;
     cudaEvent_t prof_ev[2] = {nullptr, nullptr};
@@ -183,6 +194,11 @@ int ms_build(osrc_problem *pb, const std::vector<int> &contrib_ptr,
 int mass_solve(osrc_problem *pb, const double2 *x, double2 *y, cudaStream_t st);
 int osrc_precond(osrc_problem *pb, const double2 *x, double2 *y, cudaStream_t st);
 int osrc_precond_fused(osrc_problem *pb, const double2 *y, double2 *z, cudaStream_t st);
+// the same without waiting: the inner status is left in d_kry_stat
+int osrc_precond_fused_async(osrc_problem *pb, const double2 *y, double2 *z, cudaStream_t st);
+int osrc_precond_nsys(const osrc_problem *pb);
+// turns a host copy of the inner status words into a status code
+int kry_status_host(osrc_problem *pb, const int *stat, int nsys);
 
 // GMRES helpers (k_gmres.cu)
 int vec_dots_conj(osrc_problem *pb, const double2 *V, int nvec, const double2 *w, int n,
@@ -201,3 +217,42 @@ int vec_axpby(osrc_problem *pb, double2 a, const double2 *x, double2 b, const do
 
 // right-hand sides (k_rhs.cu)
 int rhs_build(osrc_problem *pb, int kind, const double *src3, double2 *b, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// resumable GMRES (osrc_api.cu): one right-hand side, advanced one iteration
+// at a time without blocking the host, so that several runs overlap on the
+// GPU (the serving loop) or are driven to completion synchronously
+// (osrc_gmres_solve).
+// ---------------------------------------------------------------------------
+struct GmresRun {
+    osrc_problem *pb = nullptr;
+    cudaStream_t st = nullptr;
+    const double2 *b = nullptr;
+    double2 *x = nullptr;
+    double tol = 1e-5;
+    int maxit = 100;
+    int j = 0;          // completed iterations
+    double beta = 0.0;  // |P M^-1 b|
+    double res = 1.0;   // relative preconditioned residual estimate
+    int phase = 0;      // 0 idle, 1 initial norm, 2 iteration, 3 final residual, 4 done
+    int status = OSRC_OK;
+    bool converged = false;
+    cudaEvent_t ev = nullptr;
+    cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
+    osrc_solve_info info{};
+    int start(osrc_problem *p, cudaStream_t s, const double2 *b_, double2 *x_, double tol_, int maxit_);
+    bool ready() const;   // the work enqueued last has finished
+    int advance();        // consumes the finished step and enqueues the next
+    bool done() const { return phase == 4; }
+    int run_to_completion();
+    ~GmresRun();
+};
+
+int ensure_gmres_workspace(osrc_problem *pb, int maxit);
+// a problem that borrows the resident state of `master` and owns a fresh
+// workspace (per-apply, inner-solver and GMRES buffers)
+int problem_clone(osrc_problem *master, osrc_problem **out);
+// device bytes of the resident state and of one workspace (estimates used
+// for admission by device memory)
+size_t estimate_problem_bytes(int nv, int nt, const osrc_params &p);
+size_t estimate_work_bytes(int nv, int nt, const osrc_params &p, int maxit);
