@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle sample")
+    ap.add_argument("--serve-requests", type=int, default=12,
+                    help="requests of the seeded Poisson stream in the serving leg (0: skip)")
     return ap.parse_args()
 
 
@@ -302,7 +304,86 @@ def run_ours(args, D):
     if peaks is not None:
         out["measured_peaks_file"] = True
     S.close()
+    if args.serve_requests > 0 and D.rank == 0:
+        out["serving"] = run_serving(args.serve_requests, D.local)
     return out, (infos[-1]["iterations"] if infos else REF_ITERATIONS)
+
+
+# --------------------------------------------------------------------------
+# serving leg: continuous batching on a seeded Poisson stream
+# --------------------------------------------------------------------------
+SERVE_MAX_NV = 8000
+SERVE_MAX_RHS = 4
+SERVE_MAX_KA = 20.0
+
+
+def serving_workload(n_req):
+    """The first n_req requests of the seeded stream (rate 50/s, seed 2) with
+    the mesh size capped at SERVE_MAX_NV vertices, ka at SERVE_MAX_KA and the
+    right-hand sides at SERVE_MAX_RHS so that the leg stays bounded; spheres
+    and ellipsoids (Fibonacci hulls), k_int = k_ext / c_ratio."""
+    import numpy as np
+
+    from paper_2104_04609_gb300.inputs import fibonacci_hull, plane_wave_dirs, serving_requests
+
+    out = []
+    for r in serving_requests(1000, 50.0, seed=2)[:n_req]:
+        nv = min(r["n_v"], SERVE_MAX_NV)
+        v, t = fibonacci_hull(nv)
+        v = v * np.asarray(r["axes"])[None, :]
+        a = max(r["axes"])
+        k_ext = min(r["ka"], SERVE_MAX_KA) / a
+        out.append(dict(t=r["t"], verts=v, tris=t, k_ext=k_ext, k_int=k_ext / r["c_ratio"],
+                        rho=r["rho_ratio"], dirs=plane_wave_dirs(min(r["nrhs"], SERVE_MAX_RHS),
+                                                                 seed=r["seed"] % (2 ** 31))))
+    return out
+
+
+def run_serving(n_req, device):
+    import numpy as np
+
+    from paper_2104_04609_gb300 import binding as B
+
+    work = serving_workload(n_req)
+    ctx = B.osrc_create(device, 0)
+    sv = B.osrc_server_create(ctx, 4)
+    try:
+        t0 = time.perf_counter()
+        ids = []
+        for w in work:
+            delay = t0 + w["t"] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            p = B.osrc_params_default(k_ext=w["k_ext"], k_int=w["k_int"], rho_ratio=w["rho"])
+            ids.append(B.osrc_server_submit(sv, w["verts"], w["tris"], p, w["dirs"], tol=TOL,
+                                            maxit=1000))
+        lat, its, ok = [], 0, 0
+        for rid in ids:
+            B.osrc_server_wait(sv, rid, 1800.0)
+            done, st, l, info = B.osrc_server_poll(sv, rid)
+            if done:
+                lat.append(l)
+                its += info["total_iterations"]
+                ok += 1 if st == B.OSRC_OK else 0
+        t1 = time.perf_counter()
+        stats = B.osrc_server_get_stats(sv)
+    finally:
+        B.osrc_server_destroy(sv)
+        B.osrc_destroy(ctx)
+    nrhs = sum(len(w["dirs"]) for w in work)
+    lat = np.sort(np.asarray(lat))
+    return {
+        "requests": len(work), "right_hand_sides": nrhs, "converged_requests": ok,
+        "solves_per_s": nrhs / (t1 - t0), "wall_s": t1 - t0,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(lat[-1])},
+        "gmres_iterations": its, "max_active": 4, "active_peak": stats["active_peak"],
+        "cache_hits": stats["cache_hits"], "cache_misses": stats["cache_misses"],
+        "mem_peak_bytes": stats["mem_peak"],
+        "sample": f"first {len(work)} requests of the seeded Poisson stream (50/s, seed 2), "
+                  f"vertices capped at {SERVE_MAX_NV}, ka at {SERVE_MAX_KA:g}, right-hand sides "
+                  f"at {SERVE_MAX_RHS}; latency = submit to completion of all right-hand sides",
+    }
 
 
 # --------------------------------------------------------------------------
