@@ -186,6 +186,18 @@ enum { OSRC_HOST_BUFFERS = 1 };
 int osrc_gmres_solve(osrc_problem *pb, const void *b, void *x, int nrhs, double tol,
                      int maxit, int flags, osrc_solve_info *info, void *stream);
 
+/* ---- tensor-core GEMM (dense assembled path) ----------------------------------------- */
+/* C = A B^T on the 5th-generation tensor cores (tcgen05 MMA, FP32 accumulator
+ * in tensor memory, TMA-staged operands): the dense complex products of the
+ * assembled path (Sec. 2.3 system applied to blocks of right-hand sides) run
+ * through it in their real embedding.  A: device BF16, M x K row-major;
+ * B: device BF16, N x K row-major (both K-major); C: device FP32, M x ldc.
+ * M % 128 == 0, K % 64 == 0, 16 <= N <= 256 with N % 16 == 0, rows 16-byte
+ * aligned; otherwise OSRC_INVALID_ARG.  err_flag_dev: device int that the
+ * kernel sets to 1 if a bounded wait gave up (then C is unspecified). */
+int osrc_gemm_bf16(const void *A, int M, int K, const void *B, int N, float *C, int ldc,
+                   int *err_flag_dev, void *stream);
+
 /* ---- serving loop ------------------------------------------------------------------ */
 /* A continuous-batching server for solve requests of uneven mesh size and
  * frequency (the serving pattern that the solver is deployed in).  A worker

@@ -132,6 +132,8 @@ SIGNATURES = {
     "osrc_server_result": (ctypes.c_int, [_VP, ctypes.c_longlong, _VP]),
     "osrc_server_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(osrc_server_stats)]),
     "osrc_server_destroy": (None, [_VP]),
+    "osrc_gemm_bf16": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP,
+                                      ctypes.c_int, _VP, _VP]),
     "osrc_launch_count": (ctypes.c_longlong, [_VP]),
     "osrc_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "osrc_far_kernel_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong),
@@ -389,6 +391,22 @@ def osrc_server_get_stats(sv):
 
 def osrc_server_destroy(sv):
     lib().osrc_server_destroy(sv)
+
+
+def osrc_gemm_bf16(A, B, C, err, stream=None):
+    """C = A B^T on the tensor cores; A (M, K), B (N, K) bfloat16 CUDA tensors,
+    C (M, ldc) float32, err a one-element int32 CUDA tensor (set to 1 if the
+    kernel's bounded waits gave up)."""
+    import torch
+
+    assert A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16 and C.dtype == torch.float32
+    assert A.is_cuda and B.is_cuda and C.is_cuda and err.is_cuda and err.dtype == torch.int32
+    assert A.is_contiguous() and B.is_contiguous() and C.is_contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    _check(lib().osrc_gemm_bf16(ctypes.c_void_p(A.data_ptr()), M, K, ctypes.c_void_p(B.data_ptr()), N,
+                                ctypes.c_void_p(C.data_ptr()), C.shape[1],
+                                ctypes.c_void_p(err.data_ptr()), _stream(stream)), "osrc_gemm_bf16")
 
 
 def osrc_launch_count(pb):
