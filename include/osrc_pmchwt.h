@@ -198,6 +198,37 @@ int osrc_gmres_solve(osrc_problem *pb, const void *b, void *x, int nrhs, double 
 int osrc_gemm_bf16(const void *A, int M, int K, const void *B, int N, float *C, int ldc,
                    int *err_flag_dev, void *stream);
 
+/* ---- batched mixed-precision solve (dense assembled path) ---------------------------- */
+typedef struct osrc_batched_info {
+    int refinements;       /* outer FP64 refinement steps taken */
+    int inner_iterations;  /* inner GMRES iterations summed over the steps */
+    double residual;       /* largest |b_r - A x_r| / |b_r| over the right-hand sides (FP64) */
+    double ms_total;
+} osrc_batched_info;
+
+/* Solves A x_r = b_r for up to 128 right-hand sides at once on a problem
+ * created with OSRC_FP64_DENSE (A = the assembled permuted PMCHWT system of
+ * Sec. 2.7): FP64 outer iterative refinement x += d, r = b - A x (FP64
+ * residual on the FP64 matrix), each correction solved approximately for all
+ * right-hand sides together by GMRES on P M^-1 A d = P M^-1 r (OSRC and mass
+ * preconditioning of Sec. 2.4-2.7, inner Krylov solves in FP32) whose
+ * operator applies the far-field part of A in BF16 on the tensor cores (FP32
+ * accumulation) and the touching-pair blocks exactly.  Stops when every
+ * |b_r - A x_r| / |b_r| <= tol or after max_refine steps
+ * (OSRC_NOT_CONVERGED).  inner_tol: relative tolerance of each inner solve
+ * (e.g. 1e-3); inner_maxit <= 1000.  b, x: device, nrhs x 2nv complex FP64. */
+int osrc_dense_batched_solve(osrc_problem *pb, const void *b, void *x, int nrhs, double tol,
+                             int max_refine, double inner_tol, int inner_maxit,
+                             osrc_batched_info *info, void *stream);
+
+/* The inner pieces of osrc_dense_batched_solve on nrhs (<= 128) vectors,
+ * computed in FP32 / BF16 and returned in FP64: what 0 the inner operator
+ * (far field BF16 on the tensor cores + exact touching-pair blocks), 1 the
+ * FP32 preconditioner P M^-1 (Sec. 2.4, 2.6), 2 their product.  x, y:
+ * device, nrhs x 2nv complex FP64.  Problem created with OSRC_FP64_DENSE. */
+int osrc_dense_batched_apply(osrc_problem *pb, const void *x, void *y, int nrhs, int what,
+                             void *stream);
+
 /* ---- serving loop ------------------------------------------------------------------ */
 /* A continuous-batching server for solve requests of uneven mesh size and
  * frequency (the serving pattern that the solver is deployed in).  A worker

@@ -66,6 +66,14 @@ class osrc_solve_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class osrc_batched_info(ctypes.Structure):
+    _fields_ = [("refinements", ctypes.c_int), ("inner_iterations", ctypes.c_int),
+                ("residual", ctypes.c_double), ("ms_total", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class osrc_request(ctypes.Structure):
     _fields_ = [
         ("verts", ctypes.c_void_p), ("nv", ctypes.c_int32),
@@ -134,6 +142,10 @@ SIGNATURES = {
     "osrc_server_destroy": (None, [_VP]),
     "osrc_gemm_bf16": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP,
                                       ctypes.c_int, _VP, _VP]),
+    "osrc_dense_batched_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
+                                                ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                                ctypes.POINTER(osrc_batched_info), _VP]),
+    "osrc_dense_batched_apply": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     "osrc_launch_count": (ctypes.c_longlong, [_VP]),
     "osrc_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "osrc_far_kernel_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong),
@@ -407,6 +419,24 @@ def osrc_gemm_bf16(A, B, C, err, stream=None):
     _check(lib().osrc_gemm_bf16(ctypes.c_void_p(A.data_ptr()), M, K, ctypes.c_void_p(B.data_ptr()), N,
                                 ctypes.c_void_p(C.data_ptr()), C.shape[1],
                                 ctypes.c_void_p(err.data_ptr()), _stream(stream)), "osrc_gemm_bf16")
+
+
+def osrc_dense_batched_solve(pb, b, x, tol=1e-6, max_refine=8, inner_tol=1e-3, inner_maxit=200,
+                             stream=None, raise_on_nonconvergence=True):
+    """Batched mixed-precision solve; b, x (nrhs, 2nv) complex128 CUDA tensors.
+    Returns the osrc_batched_info record as a dict."""
+    info = osrc_batched_info()
+    s = lib().osrc_dense_batched_solve(pb, _dev(b), _dev(x), int(b.shape[0]), float(tol),
+                                       int(max_refine), float(inner_tol), int(inner_maxit),
+                                       ctypes.byref(info), _stream(stream))
+    if s != OSRC_OK and (s != OSRC_NOT_CONVERGED or raise_on_nonconvergence):
+        raise OsrcError(s, "osrc_dense_batched_solve")
+    return info.as_dict()
+
+
+def osrc_dense_batched_apply(pb, x, y, what, stream=None):
+    _check(lib().osrc_dense_batched_apply(pb, _dev(x), _dev(y), int(x.shape[0]), int(what),
+                                          _stream(stream)), "osrc_dense_batched_apply")
 
 
 def osrc_launch_count(pb):

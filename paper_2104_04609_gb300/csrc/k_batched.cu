@@ -1,0 +1,884 @@
+// k_batched.cu -- kernels of the batched mixed-precision solve of the
+// assembled system (the dense path for blocks of right-hand sides):
+//   - packing of the FP64 dense system into the BF16 real embedding used by
+//     the tensor-core GEMM (far-field entries only: the touching-pair blocks
+//     stay exact in the near-field CSR);
+//   - packing / unpacking of blocks of right-hand sides around the GEMM,
+//     fused with the near-field CSR product;
+//   - an FP32 multi-right-hand-side CG / COCG for the fused OSRC
+//     preconditioner (Sec. 2.6, 2.7), one CTA per (system, group of 8
+//     right-hand sides);
+//   - FP32 batched Arnoldi helpers (projections, updates, norms, Givens);
+//   - the FP64 residual product R = B - A X of the outer refinement.
+// Block vectors of the inner solver are stored [row][rhs] (right-hand sides
+// fastest, complex FP32), so every row access is coalesced across the block.
+#include <cuda_bf16.h>
+
+#include <chrono>
+#include <cmath>
+
+#include "osrc_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ float2 f2c(float r, float i) { return make_float2(r, i); }
+__device__ __forceinline__ float2 fadd(float2 a, float2 b) { return f2c(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 fsub(float2 a, float2 b) { return f2c(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 fmulc(float2 a, float2 b) {
+    return f2c(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 fscale(float2 a, float s) { return f2c(a.x * s, a.y * s); }
+__device__ __forceinline__ float fabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ float2 fdivc(float2 a, float2 b) {
+    const float d = b.x * b.x + b.y * b.y;
+    return f2c((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// A_cat[m][k] = Re A[m][k] (k < n2), Im A[m][k - n2] (n2 <= k < 2 n2), 0 else.
+__global__ void pack_a_kernel(int n2, int Mp, int Kp, const double2 *__restrict__ A,
+                              __nv_bfloat16 *__restrict__ Acat) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)Mp * Kp) return;
+    const int m = (int)(idx / Kp), k = (int)(idx % Kp);
+    float v = 0.f;
+    if (m < n2) {
+        if (k < n2) v = (float)A[(size_t)m * n2 + k].x;
+        else if (k < 2 * n2) v = (float)A[(size_t)m * n2 + (k - n2)].y;
+    }
+    Acat[idx] = __float2bfloat16_rn(v);
+}
+
+// At the vertex pairs of the near-field CSR the BF16 matrix keeps only the
+// far-field part: A - (touching-pair blocks), which are applied exactly in
+// FP32 from the CSR (a vertex pair can receive both touching and
+// non-touching triangle-pair contributions).
+__global__ void far_part_near_kernel(int nv, int Kp, const int *__restrict__ ptr, const int *__restrict__ col,
+                                     const double2 *__restrict__ val, const double2 *__restrict__ A,
+                                     __nv_bfloat16 *__restrict__ Acat) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    const int n2 = 2 * nv;
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+        const int j = col[e];
+        const int rows[2] = {i, nv + i}, cols[2] = {j, nv + j};
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                const double2 f = csub(A[(size_t)rows[a] * n2 + cols[b]], val[4 * (size_t)e + 2 * a + b]);
+                Acat[(size_t)rows[a] * Kp + cols[b]] = __float2bfloat16_rn((float)f.x);
+                Acat[(size_t)rows[a] * Kp + n2 + cols[b]] = __float2bfloat16_rn((float)f.y);
+            }
+    }
+}
+
+// B_cat rows r < R: [Re X_r | -Im X_r]; rows R + r: [Im X_r | Re X_r];
+// X given [row][rhs] complex FP32 (R right-hand sides, n2 rows).
+__global__ void pack_b_kernel(int n2, int R, int Kp, const float2 *__restrict__ X,
+                              __nv_bfloat16 *__restrict__ Bcat) {
+    __shared__ float2 tile[32][33];
+    const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int j = ty; j < 32; j += 8) {
+        const int k = k0 + j, r = r0 + tx;
+        tile[j][tx] = (k < n2 && r < R) ? X[(size_t)k * R + r] : f2c(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+        const int r = r0 + j, k = k0 + tx;
+        if (r >= R || k >= n2) continue;
+        const float2 v = tile[tx][j];
+        Bcat[(size_t)r * Kp + k] = __float2bfloat16_rn(v.x);
+        Bcat[(size_t)r * Kp + n2 + k] = __float2bfloat16_rn(-v.y);
+        Bcat[(size_t)(R + r) * Kp + k] = __float2bfloat16_rn(v.y);
+        Bcat[(size_t)(R + r) * Kp + n2 + k] = __float2bfloat16_rn(v.x);
+    }
+}
+
+// zero the padding columns of B_cat once
+__global__ void zero_pad_b_kernel(int n2, int NN, int Kp, __nv_bfloat16 *__restrict__ Bcat) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int pad = Kp - 2 * n2;
+    if (pad <= 0 || idx >= (size_t)NN * pad) return;
+    const int r = (int)(idx / pad), k = 2 * n2 + (int)(idx % pad);
+    Bcat[(size_t)r * Kp + k] = __float2bfloat16_rn(0.f);
+}
+
+// y[m][r] = (C[m][r], C[m][R + r]) + (near CSR product)[m][r]
+__global__ void unpack_near_kernel(int nv, int R, int ldc, const float *__restrict__ C,
+                                   const int *__restrict__ ptr, const int *__restrict__ col,
+                                   const double2 *__restrict__ val, const float2 *__restrict__ X,
+                                   float2 *__restrict__ Y) {
+    const int i = blockIdx.x;  // vertex
+    const int r = threadIdx.x;
+    if (i >= nv || r >= R) return;
+    float2 y1 = f2c(C[(size_t)i * ldc + r], C[(size_t)i * ldc + R + r]);
+    float2 y2 = f2c(C[(size_t)(nv + i) * ldc + r], C[(size_t)(nv + i) * ldc + R + r]);
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+        const int j = col[e];
+        const double2 *b = val + 4 * (size_t)e;
+        const float2 xa = X[(size_t)j * R + r], xb = X[(size_t)(nv + j) * R + r];
+        const float2 b0 = f2c((float)b[0].x, (float)b[0].y), b1 = f2c((float)b[1].x, (float)b[1].y);
+        const float2 b2 = f2c((float)b[2].x, (float)b[2].y), b3 = f2c((float)b[3].x, (float)b[3].y);
+        y1 = fadd(y1, fadd(fmulc(b0, xa), fmulc(b1, xb)));
+        y2 = fadd(y2, fadd(fmulc(b2, xa), fmulc(b3, xb)));
+    }
+    Y[(size_t)i * R + r] = y1;
+    Y[(size_t)(nv + i) * R + r] = y2;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 multi-right-hand-side CG / COCG: one CTA per (system, group of 8
+// right-hand sides).  System s: (M + beta_s S) w = f, rows n = nv, input f
+// is block row `half` of the block vector F ([2nv][R]), solution into W_s
+// ([nv][R]).  Jacobi preconditioning, stop per right-hand side at
+// |r| <= tol |f| (converged columns freeze), bounded by maxit.
+// ---------------------------------------------------------------------------
+constexpr int K32_THREADS = 512;
+constexpr int K32_G = 8;
+
+struct Kry32Sys {
+    float2 beta;
+    int half;   // 0: rows [0, nv), 1: rows [nv, 2nv) of F
+    int conj;   // 1: Hermitian CG, 0: COCG
+};
+
+struct Kry32Batch {
+    int nsys;
+    Kry32Sys s[34];
+};
+
+__device__ float2 dotf(float2 a, float2 b, int conj) {
+    return conj ? f2c(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x) : fmulc(a, b);
+}
+
+__global__ void __launch_bounds__(K32_THREADS)
+kry32_kernel(Kry32Batch batch, int nv, int R, const int *__restrict__ ptr, const int *__restrict__ col,
+             const float *__restrict__ Mv, const float *__restrict__ Sv, const float2 *__restrict__ F,
+             float2 *__restrict__ W, float2 *__restrict__ work, float tol, int maxit,
+             int *__restrict__ its_out) {
+    __shared__ float red[K32_THREADS / 32][K32_G][3];
+    __shared__ float2 sc_rho[K32_G], sc_al[K32_G], sc_be[K32_G];
+    __shared__ float sc_bb[K32_G], sc_rr[K32_G];
+    __shared__ int active[K32_G];
+    const int sid = blockIdx.x;
+    const int g0 = blockIdx.y * K32_G;
+    const Kry32Sys sy = batch.s[sid];
+    const int gl = threadIdx.x % K32_G;       // right-hand side within the group
+    const int rl = threadIdx.x / K32_G;       // row lane
+    const int nrl = K32_THREADS / K32_G;
+    const int r = g0 + gl;
+    const bool rv = r < R;
+    const size_t plane = (size_t)nv * R;
+    float2 *rr = work + ((size_t)sid * 5 + 0) * plane;
+    float2 *zz = work + ((size_t)sid * 5 + 1) * plane;
+    float2 *pp = work + ((size_t)sid * 5 + 2) * plane;
+    float2 *qq = work + ((size_t)sid * 5 + 3) * plane;
+    float2 *dinv = work + ((size_t)sid * 5 + 4) * plane;
+    float2 *x = W + (size_t)sid * plane;
+    const float2 *f = F + (size_t)sy.half * plane;
+    const int cj = sy.conj;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // reduce three floats per right-hand side over the CTA into sums[g][0..2]
+    auto reduce3 = [&](float a, float b, float c, float (*out)[3]) {
+        // lanes with the same gl are 8 apart inside a warp
+        for (int o = 16; o >= K32_G; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        if (lane < K32_G) {
+            red[warp][lane][0] = a;
+            red[warp][lane][1] = b;
+            red[warp][lane][2] = c;
+        }
+        __syncthreads();
+        if (threadIdx.x < K32_G) {
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+            for (int w = 0; w < K32_THREADS / 32; ++w) {
+                s0 += red[w][threadIdx.x][0];
+                s1 += red[w][threadIdx.x][1];
+                s2 += red[w][threadIdx.x][2];
+            }
+            out[threadIdx.x][0] = s0;
+            out[threadIdx.x][1] = s1;
+            out[threadIdx.x][2] = s2;
+        }
+        __syncthreads();
+    };
+    __shared__ float sums[K32_G][3];
+
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    for (int i = rl; i < nv; i += nrl) {
+        if (!rv) continue;
+        float md = 0.f, sd = 0.f;
+        for (int e = ptr[i]; e < ptr[i + 1]; ++e)
+            if (col[e] == i) { md = Mv[e]; sd = Sv[e]; }
+        const float2 d = f2c(md + sy.beta.x * sd, sy.beta.y * sd);
+        const float2 di = fdivc(f2c(1.f, 0.f), d);
+        const size_t k = (size_t)i * R + r;
+        const float2 b = f[k];
+        dinv[k] = di;
+        x[k] = f2c(0.f, 0.f);
+        rr[k] = b;
+        const float2 zi = fmulc(di, b);
+        zz[k] = zi;
+        pp[k] = zi;
+        const float2 t = dotf(b, zi, cj);
+        a0 += t.x;
+        a1 += t.y;
+        a2 += fabs2(b);
+    }
+    reduce3(a0, a1, a2, sums);
+    if (threadIdx.x < K32_G) {
+        sc_rho[threadIdx.x] = f2c(sums[threadIdx.x][0], sums[threadIdx.x][1]);
+        sc_bb[threadIdx.x] = sums[threadIdx.x][2];
+        active[threadIdx.x] = (g0 + (int)threadIdx.x < R && sums[threadIdx.x][2] > 0.f) ? 1 : 0;
+        if (its_out && g0 + (int)threadIdx.x < R) its_out[sid * R + g0 + threadIdx.x] = 0;
+    }
+    __syncthreads();
+    for (int it = 1; it <= maxit; ++it) {
+        int any = 0;
+        for (int g = 0; g < K32_G; ++g) any |= active[g];
+        if (!any) break;
+        const bool act = rv && active[gl];
+        float w0 = 0.f, w1 = 0.f;
+        for (int i = rl; i < nv; i += nrl) {
+            if (!act) continue;
+            float2 mp = f2c(0.f, 0.f), sp = f2c(0.f, 0.f);
+            for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+                const float2 pj = pp[(size_t)col[e] * R + r];
+                mp = fadd(mp, fscale(pj, Mv[e]));
+                sp = fadd(sp, fscale(pj, Sv[e]));
+            }
+            const float2 acc = fadd(mp, fmulc(sy.beta, sp));
+            const size_t k = (size_t)i * R + r;
+            qq[k] = acc;
+            const float2 t = dotf(pp[k], acc, cj);
+            w0 += t.x;
+            w1 += t.y;
+        }
+        reduce3(w0, w1, 0.f, sums);
+        if (threadIdx.x < K32_G) {
+            const float2 pq = f2c(sums[threadIdx.x][0], sums[threadIdx.x][1]);
+            if (active[threadIdx.x] && !(fabs2(pq) > 0.f)) active[threadIdx.x] = 0;  // breakdown: freeze
+            sc_al[threadIdx.x] = active[threadIdx.x] ? fdivc(sc_rho[threadIdx.x], pq) : f2c(0.f, 0.f);
+        }
+        __syncthreads();
+        const bool act2 = rv && active[gl];
+        const float2 al = sc_al[gl];
+        float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+        for (int i = rl; i < nv; i += nrl) {
+            if (!act2) continue;
+            const size_t k = (size_t)i * R + r;
+            x[k] = fadd(x[k], fmulc(al, pp[k]));
+            const float2 ri = fsub(rr[k], fmulc(al, qq[k]));
+            rr[k] = ri;
+            const float2 zi = fmulc(dinv[k], ri);
+            zz[k] = zi;
+            const float2 t = dotf(ri, zi, cj);
+            u0 += t.x;
+            u1 += t.y;
+            u2 += fabs2(ri);
+        }
+        reduce3(u0, u1, u2, sums);
+        if (threadIdx.x < K32_G) {
+            const int g = threadIdx.x;
+            if (active[g]) {
+                const float2 rn = f2c(sums[g][0], sums[g][1]);
+                if (its_out) its_out[sid * R + g0 + g] = it;
+                if (sums[g][2] <= tol * tol * sc_bb[g] || !(fabs2(sc_rho[g]) > 0.f)) {
+                    active[g] = 0;
+                    sc_be[g] = f2c(0.f, 0.f);
+                } else {
+                    sc_be[g] = fdivc(rn, sc_rho[g]);
+                    sc_rho[g] = rn;
+                }
+            }
+        }
+        __syncthreads();
+        const bool act3 = rv && active[gl];
+        const float2 be = sc_be[gl];
+        for (int i = rl; i < nv; i += nrl) {
+            if (!act3) continue;
+            const size_t k = (size_t)i * R + r;
+            pp[k] = fadd(zz[k], fmulc(be, pp[k]));
+        }
+        __syncthreads();
+    }
+}
+
+struct OsrcComb32 {
+    int np;
+    float2 ik, iik, cu, g0;
+    float2 a[16], g[16];
+};
+
+// z1 = i k [cu u1 - sum_j a_j v_j],  z2 = [g0 v'_0 + sum_j g_j v'_j] / (i k)
+__global__ void osrc_combine32_kernel(int nv, int R, OsrcComb32 c, const float2 *__restrict__ W,
+                                      float2 *__restrict__ Z) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t plane = (size_t)nv * R;
+    if (k >= plane) return;
+    float2 a = fmulc(c.cu, W[k]);
+    for (int j = 0; j < c.np; ++j) a = fsub(a, fmulc(c.a[j], W[(size_t)(1 + j) * plane + k]));
+    float2 b = fmulc(c.g0, W[(size_t)(c.np + 1) * plane + k]);
+    for (int j = 0; j < c.np; ++j) b = fadd(b, fmulc(c.g[j], W[(size_t)(c.np + 2 + j) * plane + k]));
+    Z[k] = fmulc(c.ik, a);
+    Z[plane + k] = fmulc(c.iik, b);
+}
+
+// M and S values in FP32
+__global__ void d2f_kernel(int n, const double *__restrict__ a, float *__restrict__ b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+// ---------------------------------------------------------------------------
+// FP32 batched Arnoldi: block vectors [n2][R]
+// ---------------------------------------------------------------------------
+// out[i][r] = sum_m conj(V_i[m][r]) w[m][r] for i < nvec; block per i.
+__global__ void bdots_kernel(const float2 *__restrict__ V, size_t ldv, int nvec, const float2 *__restrict__ w,
+                             int n2, int R, float2 *__restrict__ out) {
+    const int i = blockIdx.x;
+    if (i >= nvec) return;
+    __shared__ float2 acc[256];
+    const int r = threadIdx.x % R;
+    const int rl = threadIdx.x / R, nrl = blockDim.x / R;
+    const float2 *v = V + ldv * i;
+    float2 s = f2c(0.f, 0.f);
+    if (threadIdx.x < nrl * R)
+        for (int m = rl; m < n2; m += nrl) {
+            const float2 a = v[(size_t)m * R + r], b = w[(size_t)m * R + r];
+            s.x += a.x * b.x + a.y * b.y;
+            s.y += a.x * b.y - a.y * b.x;
+        }
+    acc[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < R) {
+        float2 t = f2c(0.f, 0.f);
+        for (int l = 0; l < nrl; ++l) t = fadd(t, acc[l * R + threadIdx.x]);
+        out[(size_t)i * R + threadIdx.x] = t;
+    }
+}
+
+// w[m][r] -= sum_i h[i][r] V_i[m][r]
+__global__ void bupdate_kernel(const float2 *__restrict__ V, size_t ldv, int nvec, const float2 *__restrict__ h,
+                               float2 *__restrict__ w, int n2, int R) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (size_t)n2 * R) return;
+    const int r = (int)(k % R);
+    float2 s = w[k];
+    for (int i = 0; i < nvec; ++i) s = fsub(s, fmulc(h[(size_t)i * R + r], V[ldv * i + k]));
+    w[k] = s;
+}
+
+// nrm[r] = |w[:, r]|
+__global__ void bnorm_kernel(const float2 *__restrict__ w, int n2, int R, float *__restrict__ nrm) {
+    __shared__ float acc[256];
+    const int r = threadIdx.x % R;
+    const int rl = threadIdx.x / R, nrl = blockDim.x / R;
+    float s = 0.f;
+    if (threadIdx.x < nrl * R)
+        for (int m = rl; m < n2; m += nrl) s += fabs2(w[(size_t)m * R + r]);
+    acc[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < R) {
+        float t = 0.f;
+        for (int l = 0; l < nrl; ++l) t += acc[l * R + threadIdx.x];
+        nrm[threadIdx.x] = sqrtf(t);
+    }
+}
+
+// v[m][r] = w[m][r] / nrm[r] (0 where the column is frozen or nrm is 0)
+__global__ void bscale_kernel(const float2 *__restrict__ w, const float *__restrict__ nrm,
+                              const int *__restrict__ done, float2 *__restrict__ v, int n2, int R) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (size_t)n2 * R) return;
+    const int r = (int)(k % R);
+    const float s = nrm[r];
+    v[k] = (done[r] || !(s > 0.f)) ? f2c(0.f, 0.f) : fscale(w[k], 1.f / s);
+}
+
+// Per right-hand side r (one thread each): new Hessenberg column
+// H[.][j][r] (h from the projections, h_{j+1} = nrm[r]), earlier Givens
+// rotations, the new rotation, g update, residual estimate; columns that
+// have converged keep their state (done[r] = 1, iteration count fixed).
+__global__ void bgivens_kernel(int j, int ldh, int R, const float2 *__restrict__ hcol,
+                               const float *__restrict__ nrm, float2 *__restrict__ H,
+                               float *__restrict__ cs, float2 *__restrict__ sn, float2 *__restrict__ g,
+                               const float *__restrict__ beta, float tol, int *__restrict__ done,
+                               int *__restrict__ its, float *__restrict__ res) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R || done[r]) return;
+    float2 *h = H + ((size_t)j * ldh) * R;  // h[i] at h[i * R + r]
+    for (int i = 0; i <= j; ++i) h[(size_t)i * R + r] = hcol[(size_t)i * R + r];
+    h[(size_t)(j + 1) * R + r] = f2c(nrm[r], 0.f);
+    for (int i = 0; i < j; ++i) {
+        const float c = cs[(size_t)i * R + r];
+        const float2 s = sn[(size_t)i * R + r];
+        const float2 hi = h[(size_t)i * R + r], hi1 = h[(size_t)(i + 1) * R + r];
+        const float2 t = fadd(fscale(hi, c), fmulc(s, hi1));
+        h[(size_t)(i + 1) * R + r] = fadd(fscale(fmulc(f2c(s.x, -s.y), hi), -1.f), fscale(hi1, c));
+        h[(size_t)i * R + r] = t;
+    }
+    const float2 a = h[(size_t)j * R + r], b = h[(size_t)(j + 1) * R + r];
+    const float aa = sqrtf(fabs2(a)), bb = sqrtf(fabs2(b));
+    const float nu = hypotf(aa, bb);
+    float c;
+    float2 s;
+    if (aa == 0.f) {
+        c = 0.f;
+        s = f2c(1.f, 0.f);
+    } else {
+        c = aa / nu;
+        s = fscale(fmulc(fscale(a, 1.f / aa), f2c(b.x, -b.y)), 1.f / nu);
+    }
+    cs[(size_t)j * R + r] = c;
+    sn[(size_t)j * R + r] = s;
+    h[(size_t)j * R + r] = fadd(fscale(a, c), fmulc(s, b));
+    h[(size_t)(j + 1) * R + r] = f2c(0.f, 0.f);
+    const float2 gj = g[(size_t)j * R + r];
+    g[(size_t)(j + 1) * R + r] = fscale(fmulc(f2c(s.x, -s.y), gj), -1.f);
+    g[(size_t)j * R + r] = fscale(gj, c);
+    const float rel = sqrtf(fabs2(g[(size_t)(j + 1) * R + r])) / beta[r];
+    res[r] = rel;
+    its[r] = j + 1;
+    if (rel <= tol || !(nu > 0.f)) done[r] = 1;
+}
+
+// y_r = H_r^-1 g_r (its[r] x its[r] upper triangular), one thread per r
+__global__ void bbacksub_kernel(int ldh, int R, const float2 *__restrict__ H, const float2 *__restrict__ g,
+                                const int *__restrict__ its, float2 *__restrict__ y) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const int m = its[r];
+    for (int i = m - 1; i >= 0; --i) {
+        float2 s = g[(size_t)i * R + r];
+        for (int k = i + 1; k < m; ++k)
+            s = fsub(s, fmulc(H[((size_t)k * ldh + i) * R + r], y[(size_t)k * R + r]));
+        y[(size_t)i * R + r] = fdivc(s, H[((size_t)i * ldh + i) * R + r]);
+    }
+}
+
+// x[m][r] = sum_{i < its[r]} y[i][r] V_i[m][r]
+__global__ void bcombine_kernel(const float2 *__restrict__ V, size_t ldv, int maxm, const float2 *__restrict__ y,
+                                const int *__restrict__ its, float2 *__restrict__ x, int n2, int R) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (size_t)n2 * R) return;
+    const int r = (int)(k % R);
+    const int m = min(its[r], maxm);
+    float2 s = f2c(0.f, 0.f);
+    for (int i = 0; i < m; ++i) s = fadd(s, fmulc(y[(size_t)i * R + r], V[ldv * i + k]));
+    x[k] = s;
+}
+
+// a[k] += b[k]
+__global__ void addcols_kernel(float2 *__restrict__ a, const float2 *__restrict__ b, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) a[k] = fadd(a[k], b[k]);
+}
+
+// beta[r] = |c[:, r]| and V_0 = c / beta, g_0 = beta
+__global__ void binit_kernel(int R, const float *__restrict__ nrm, float *__restrict__ beta,
+                             float2 *__restrict__ g, int *__restrict__ done, int *__restrict__ its) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    beta[r] = nrm[r];
+    g[r] = f2c(nrm[r], 0.f);
+    done[r] = nrm[r] > 0.f ? 0 : 1;
+    its[r] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 residual of the outer refinement: R[r][m] = B[r][m] - sum_k A[m][k] X[r][k]
+// (A [n2][n2] row-major complex FP64; B, X, R [nrhs][n2]).  Tile 32 rows x
+// 16 right-hand sides per block, K staged through shared memory.
+// ---------------------------------------------------------------------------
+constexpr int RS_TM = 32, RS_TR = 16, RS_TK = 32;
+
+__global__ void __launch_bounds__(RS_TM * RS_TR / 2)
+resid64_kernel(int n2, int nrhs, const double2 *__restrict__ A, const double2 *__restrict__ X,
+               const double2 *__restrict__ B, double2 *__restrict__ Rr) {
+    __shared__ double2 sa[RS_TM][RS_TK + 1];
+    __shared__ double2 sx[RS_TR][RS_TK + 1];
+    const int m0 = blockIdx.x * RS_TM, r0 = blockIdx.y * RS_TR;
+    const int tid = threadIdx.x;           // 256 threads: each 2 outputs
+    const int tm = tid % RS_TM, tr = (tid / RS_TM) * 2;
+    double2 acc0 = cd(0, 0), acc1 = cd(0, 0);
+    for (int k0 = 0; k0 < n2; k0 += RS_TK) {
+        for (int e = tid; e < RS_TM * RS_TK; e += blockDim.x) {
+            const int mm = e / RS_TK, kk = e % RS_TK;
+            sa[mm][kk] = (m0 + mm < n2 && k0 + kk < n2) ? A[(size_t)(m0 + mm) * n2 + k0 + kk] : cd(0, 0);
+        }
+        for (int e = tid; e < RS_TR * RS_TK; e += blockDim.x) {
+            const int rr = e / RS_TK, kk = e % RS_TK;
+            sx[rr][kk] = (r0 + rr < nrhs && k0 + kk < n2) ? X[(size_t)(r0 + rr) * n2 + k0 + kk] : cd(0, 0);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < RS_TK; ++kk) {
+            const double2 a = sa[tm][kk];
+            acc0 = cadd(acc0, cmul(a, sx[tr][kk]));
+            acc1 = cadd(acc1, cmul(a, sx[tr + 1][kk]));
+        }
+        __syncthreads();
+    }
+    const int m = m0 + tm;
+    if (m < n2) {
+        if (r0 + tr < nrhs)
+            Rr[(size_t)(r0 + tr) * n2 + m] = csub(B[(size_t)(r0 + tr) * n2 + m], acc0);
+        if (r0 + tr + 1 < nrhs)
+            Rr[(size_t)(r0 + tr + 1) * n2 + m] = csub(B[(size_t)(r0 + tr + 1) * n2 + m], acc1);
+    }
+}
+
+// per right-hand side: nrm[r] = |v[r][:]| (FP64, [nrhs][n2])
+__global__ void norm_rows64_kernel(int n2, const double2 *__restrict__ v, double *__restrict__ nrm) {
+    __shared__ double acc[256];
+    const int r = blockIdx.x;
+    double s = 0.0;
+    for (int m = threadIdx.x; m < n2; m += blockDim.x) s += cabs2(v[(size_t)r * n2 + m]);
+    acc[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) acc[threadIdx.x] += acc[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) nrm[r] = sqrt(acc[0]);
+}
+
+// [nrhs][n2] FP64 -> [n2][R] FP32, scaled per right-hand side by 1/scale[r]
+__global__ void to_block32_kernel(int n2, int nrhs, int R, const double2 *__restrict__ src,
+                                  const double *__restrict__ scale, float2 *__restrict__ dst) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (size_t)n2 * R) return;
+    const int m = (int)(k / R), r = (int)(k % R);
+    if (r >= nrhs || !(scale[r] > 0.0)) {
+        dst[k] = f2c(0.f, 0.f);
+        return;
+    }
+    const double2 v = src[(size_t)r * n2 + m];
+    const double s = 1.0 / scale[r];
+    dst[k] = f2c((float)(v.x * s), (float)(v.y * s));
+}
+
+// x[r][m] = d[m][r] (FP32 block -> FP64 rows)
+__global__ void from_block32_kernel(int n2, int nrhs, int R, const float2 *__restrict__ d,
+                                    double2 *__restrict__ x) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (size_t)n2 * nrhs) return;
+    const int r = (int)(k / n2), m = (int)(k % n2);
+    const float2 v = d[(size_t)m * R + r];
+    x[k] = cd(v.x, v.y);
+}
+
+__global__ void fill1_kernel(double *__restrict__ a, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = 1.0;
+}
+
+// x[r][m] += scale[r] * d[m][r]
+__global__ void add_block32_kernel(int n2, int nrhs, int R, const float2 *__restrict__ d,
+                                   const double *__restrict__ scale, double2 *__restrict__ x) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (size_t)n2 * nrhs) return;
+    const int r = (int)(k / n2), m = (int)(k % n2);
+    const float2 v = d[(size_t)m * R + r];
+    const double s = scale[r];
+    x[k] = cadd(x[k], cd(s * v.x, s * v.y));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+int umma_gemm_bf16(const void *A, int M, int K, const void *Bm, int N, float *C, int ldc, int *err,
+                   cudaStream_t st);
+
+struct BatchedState {
+    int n2 = 0, Mp = 0, Kp = 0, R = 0;
+    DBuf<__nv_bfloat16> Acat, Bcat;
+    DBuf<float> C;
+    DBuf<float> M32, S32;
+    DBuf<int> err;
+    DBuf<float2> kwork, kW;     // multi-RHS Krylov work and solutions
+    DBuf<float2> V, w, t1, t2;  // inner GMRES basis and temporaries
+    DBuf<float2> H, hcol, h2, g, sn, yv;
+    DBuf<float> cs, nrm, beta, res;
+    DBuf<int> done, its, kits;
+    DBuf<double2> X64, R64;
+    DBuf<double> bn, rn, scl;
+    int basis_cap = 0;
+};
+
+void batched_free(BatchedState *s) { delete s; }
+
+int batched_prepare(osrc_problem *pb, int R, int maxit_inner, cudaStream_t st) {
+    if (!pb->d_dense.p) return OSRC_UNSUPPORTED;
+    osrc_ctx *ctx = pb->mesh->ctx;
+    BatchedState *&bs = pb->batched;
+    const int nv = pb->nv, n2 = 2 * nv;
+    if (!bs) {
+        bs = new BatchedState;
+        bs->n2 = n2;
+        bs->Mp = (n2 + 127) / 128 * 128;
+        bs->Kp = (2 * n2 + 63) / 64 * 64;
+        OSRC_TRY(bs->Acat.alloc(ctx, (size_t)bs->Mp * bs->Kp));
+        const size_t tot = (size_t)bs->Mp * bs->Kp;
+        pack_a_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n2, bs->Mp, bs->Kp, pb->d_dense.p, bs->Acat.p);
+        far_part_near_kernel<<<(nv + 127) / 128, 128, 0, st>>>(nv, bs->Kp, pb->d_nr_ptr.p, pb->d_nr_col.p,
+                                                               pb->d_nr_val.p, pb->d_dense.p, bs->Acat.p);
+        OSRC_TRY(bs->M32.alloc(ctx, pb->ms_nnz));
+        OSRC_TRY(bs->S32.alloc(ctx, pb->ms_nnz));
+        d2f_kernel<<<(pb->ms_nnz + 255) / 256, 256, 0, st>>>(pb->ms_nnz, pb->d_M.p, bs->M32.p);
+        d2f_kernel<<<(pb->ms_nnz + 255) / 256, 256, 0, st>>>(pb->ms_nnz, pb->d_S.p, bs->S32.p);
+        OSRC_TRY(bs->err.alloc(ctx, 1));
+        OSRC_CK(cudaMemsetAsync(bs->err.p, 0, sizeof(int), st));
+        pb->launches += 4;
+        OSRC_CK(cudaGetLastError());
+    }
+    if (bs->R != R || bs->basis_cap < maxit_inner) {
+        const size_t plane = (size_t)n2 * R, vplane = (size_t)nv * R;
+        const int nsys = 2 * pb->p.n_pade + 2;
+        bs->R = R;
+        bs->basis_cap = maxit_inner;
+        OSRC_TRY(bs->Bcat.alloc(ctx, (size_t)2 * R * bs->Kp));
+        OSRC_CK(cudaMemsetAsync(bs->Bcat.p, 0, (size_t)2 * R * bs->Kp * sizeof(__nv_bfloat16), st));
+        OSRC_TRY(bs->C.alloc(ctx, (size_t)bs->Mp * 2 * R));
+        OSRC_TRY(bs->kwork.alloc(ctx, (size_t)nsys * 5 * vplane));
+        OSRC_TRY(bs->kW.alloc(ctx, (size_t)nsys * vplane));
+        OSRC_TRY(bs->V.alloc(ctx, (size_t)(maxit_inner + 1) * plane));
+        OSRC_TRY(bs->w.alloc(ctx, plane));
+        OSRC_TRY(bs->t1.alloc(ctx, plane));
+        OSRC_TRY(bs->t2.alloc(ctx, plane));
+        OSRC_TRY(bs->H.alloc(ctx, (size_t)(maxit_inner + 1) * (maxit_inner + 1) * R));
+        OSRC_TRY(bs->hcol.alloc(ctx, (size_t)(maxit_inner + 1) * R));
+        OSRC_TRY(bs->h2.alloc(ctx, (size_t)(maxit_inner + 1) * R));
+        OSRC_TRY(bs->g.alloc(ctx, (size_t)(maxit_inner + 1) * R));
+        OSRC_TRY(bs->sn.alloc(ctx, (size_t)(maxit_inner + 1) * R));
+        OSRC_TRY(bs->yv.alloc(ctx, (size_t)(maxit_inner + 1) * R));
+        OSRC_TRY(bs->cs.alloc(ctx, (size_t)(maxit_inner + 1) * R));
+        OSRC_TRY(bs->nrm.alloc(ctx, R));
+        OSRC_TRY(bs->beta.alloc(ctx, R));
+        OSRC_TRY(bs->res.alloc(ctx, R));
+        OSRC_TRY(bs->done.alloc(ctx, R));
+        OSRC_TRY(bs->its.alloc(ctx, R));
+        OSRC_TRY(bs->kits.alloc(ctx, (size_t)nsys * R));
+        OSRC_TRY(bs->bn.alloc(ctx, R));
+        OSRC_TRY(bs->rn.alloc(ctx, R));
+        OSRC_TRY(bs->scl.alloc(ctx, R));
+    }
+    return OSRC_OK;
+}
+
+// y = A_inner x for a block x ([n2][R] FP32): BF16 tensor-core GEMM of the
+// far-field part + exact near-field CSR product
+static int batched_matvec(osrc_problem *pb, const float2 *x, float2 *y, cudaStream_t st) {
+    BatchedState *bs = pb->batched;
+    const int n2 = bs->n2, R = bs->R, nv = pb->nv;
+    dim3 gb((n2 + 31) / 32, (R + 31) / 32);
+    pack_b_kernel<<<gb, dim3(32, 8), 0, st>>>(n2, R, bs->Kp, x, bs->Bcat.p);
+    OSRC_TRY(umma_gemm_bf16(bs->Acat.p, bs->Mp, bs->Kp, bs->Bcat.p, 2 * R, bs->C.p, 2 * R, bs->err.p, st));
+    unpack_near_kernel<<<nv, R, 0, st>>>(nv, R, 2 * R, bs->C.p, pb->d_nr_ptr.p, pb->d_nr_col.p, pb->d_nr_val.p,
+                                         x, y);
+    pb->launches += 3;
+    OSRC_CK(cudaGetLastError());
+    return OSRC_OK;
+}
+
+// z = P M^-1 y for a block y ([n2][R] FP32), inner tolerance tol
+static int batched_precond(osrc_problem *pb, const float2 *y, float2 *z, float tol, int maxit, cudaStream_t st) {
+    BatchedState *bs = pb->batched;
+    const int nv = pb->nv, R = bs->R, np = pb->p.n_pade;
+    const double2 ke2 = cmul(pb->k_eps, pb->k_eps);
+    const double2 inv = cdiv(cd(1.0, 0.0), ke2);
+    Kry32Batch b{};
+    b.nsys = 2 * np + 2;
+    b.s[0] = Kry32Sys{make_float2(0.f, 0.f), 0, 1};
+    for (int j = 0; j < np; ++j) {
+        const double2 be = cscale(cmul(pb->B[j], inv), -1.0);
+        b.s[1 + j] = Kry32Sys{make_float2((float)be.x, (float)be.y), 0, 0};
+        b.s[np + 2 + j] = Kry32Sys{make_float2((float)be.x, (float)be.y), 1, 0};
+    }
+    const double2 be0 = cscale(inv, -1.0);
+    b.s[np + 1] = Kry32Sys{make_float2((float)be0.x, (float)be0.y), 1, 0};
+    dim3 grid(b.nsys, (R + K32_G - 1) / K32_G);
+    kry32_kernel<<<grid, K32_THREADS, 0, st>>>(b, nv, R, pb->d_ms_ptr.p, pb->d_ms_col.p, bs->M32.p, bs->S32.p, y,
+                                               bs->kW.p, bs->kwork.p, tol, maxit, bs->kits.p);
+    OsrcComb32 c{};
+    c.np = np;
+    c.ik = make_float2(0.f, (float)pb->k_osrc);
+    c.iik = make_float2(0.f, (float)(-1.0 / pb->k_osrc));
+    double2 cu = pb->C0;
+    for (int j = 0; j < np; ++j) {
+        const double2 a = cdiv(pb->A[j], pb->B[j]);
+        cu = cadd(cu, a);
+        c.a[j] = make_float2((float)a.x, (float)a.y);
+        c.g[j] = make_float2((float)pb->g[j].x, (float)pb->g[j].y);
+    }
+    c.cu = make_float2((float)cu.x, (float)cu.y);
+    c.g0 = make_float2((float)pb->g0.x, (float)pb->g0.y);
+    const size_t plane = (size_t)nv * R;
+    osrc_combine32_kernel<<<(unsigned)((plane + 255) / 256), 256, 0, st>>>(nv, R, c, bs->kW.p, z);
+    pb->launches += 2;
+    OSRC_CK(cudaGetLastError());
+    return OSRC_OK;
+}
+
+// Inner solve: GMRES (FP32, classical Gram-Schmidt twice) on P M^-1 A_inner d = P M^-1 c
+// for a block c ([n2][R]); d returned in bs->t1.  Returns the largest
+// iteration count.
+static int batched_inner_gmres(osrc_problem *pb, const float2 *c, float tol, int maxit, float ptol,
+                               int pmaxit, int *iters_out, cudaStream_t st) {
+    BatchedState *bs = pb->batched;
+    const int n2 = bs->n2, R = bs->R;
+    const size_t plane = (size_t)n2 * R;
+    const int ldh = maxit + 1;
+    const unsigned gp = (unsigned)((plane + 255) / 256);
+    const int thr = (256 / R) * R;
+    // rhs of the preconditioned system
+    OSRC_TRY(batched_precond(pb, c, bs->w.p, ptol, pmaxit, st));
+    bnorm_kernel<<<1, thr, 0, st>>>(bs->w.p, n2, R, bs->nrm.p);
+    binit_kernel<<<(R + 127) / 128, 128, 0, st>>>(R, bs->nrm.p, bs->beta.p, bs->g.p, bs->done.p, bs->its.p);
+    OSRC_CK(cudaMemsetAsync(bs->g.p + R, 0, (size_t)maxit * R * sizeof(float2), st));
+    bscale_kernel<<<gp, 256, 0, st>>>(bs->w.p, bs->nrm.p, bs->done.p, bs->V.p, n2, R);
+    std::vector<int> hdone(R);
+    int j = 0;
+    for (j = 0; j < maxit; ++j) {
+        float2 *vj = bs->V.p + (size_t)j * plane;
+        OSRC_TRY(batched_matvec(pb, vj, bs->t2.p, st));
+        OSRC_TRY(batched_precond(pb, bs->t2.p, bs->w.p, ptol, pmaxit, st));
+        bdots_kernel<<<j + 1, thr, 0, st>>>(bs->V.p, plane, j + 1, bs->w.p, n2, R, bs->hcol.p);
+        bupdate_kernel<<<gp, 256, 0, st>>>(bs->V.p, plane, j + 1, bs->hcol.p, bs->w.p, n2, R);
+        bdots_kernel<<<j + 1, thr, 0, st>>>(bs->V.p, plane, j + 1, bs->w.p, n2, R, bs->h2.p);
+        bupdate_kernel<<<gp, 256, 0, st>>>(bs->V.p, plane, j + 1, bs->h2.p, bs->w.p, n2, R);
+        bnorm_kernel<<<1, thr, 0, st>>>(bs->w.p, n2, R, bs->nrm.p);
+        addcols_kernel<<<((j + 1) * R + 255) / 256, 256, 0, st>>>(bs->hcol.p, bs->h2.p, (j + 1) * R);
+        bgivens_kernel<<<(R + 127) / 128, 128, 0, st>>>(j, ldh, R, bs->hcol.p, bs->nrm.p, bs->H.p, bs->cs.p,
+                                                        bs->sn.p, bs->g.p, bs->beta.p, tol, bs->done.p,
+                                                        bs->its.p, bs->res.p);
+        bscale_kernel<<<gp, 256, 0, st>>>(bs->w.p, bs->nrm.p, bs->done.p, bs->V.p + (size_t)(j + 1) * plane, n2, R);
+        pb->launches += 8;
+        OSRC_CK(cudaMemcpyAsync(hdone.data(), bs->done.p, R * sizeof(int), cudaMemcpyDeviceToHost, st));
+        OSRC_CK(cudaStreamSynchronize(st));
+        bool all = true;
+        for (int r = 0; r < R; ++r) all = all && hdone[r];
+        if (all) {
+            ++j;
+            break;
+        }
+    }
+    bbacksub_kernel<<<(R + 127) / 128, 128, 0, st>>>(ldh, R, bs->H.p, bs->g.p, bs->its.p, bs->yv.p);
+    bcombine_kernel<<<gp, 256, 0, st>>>(bs->V.p, plane, maxit, bs->yv.p, bs->its.p, bs->t1.p, n2, R);
+    pb->launches += 2;
+    OSRC_CK(cudaGetLastError());
+    *iters_out = j;
+    return OSRC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// outer FP64 iterative refinement
+// ---------------------------------------------------------------------------
+extern "C" int osrc_dense_batched_solve(osrc_problem *pb, const void *b, void *x, int nrhs, double tol,
+                                        int max_refine, double inner_tol, int inner_maxit,
+                                        osrc_batched_info *info_out, void *stream) {
+    if (!pb || !b || !x || nrhs < 1 || nrhs > 128 || !(tol > 0.0) || max_refine < 1 || !(inner_tol > 0.0) ||
+        inner_tol >= 1.0 || inner_maxit < 1 || inner_maxit > 1000)
+        return OSRC_INVALID_ARG;
+    if (pb->p.precision != OSRC_FP64_DENSE) {
+        osrc_set_error("osrc_dense_batched_solve needs a problem created with OSRC_FP64_DENSE");
+        return OSRC_UNSUPPORTED;
+    }
+    OSRC_CK(cudaSetDevice(pb->mesh->ctx->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = (cudaStream_t)stream;
+    const int R = (nrhs + 7) / 8 * 8;
+    OSRC_TRY(batched_prepare(pb, R, inner_maxit, st));
+    BatchedState *bs = pb->batched;
+    osrc_ctx *ctx = pb->mesh->ctx;
+    const int n2 = bs->n2;
+    if (bs->R64.n < (size_t)nrhs * n2) OSRC_TRY(bs->R64.alloc(ctx, (size_t)nrhs * n2));
+    const double2 *B = (const double2 *)b;
+    double2 *X = (double2 *)x;
+    osrc_batched_info info{};
+    OSRC_CK(cudaMemsetAsync(X, 0, (size_t)nrhs * n2 * sizeof(double2), st));
+    OSRC_CK(cudaMemcpyAsync(bs->R64.p, B, (size_t)nrhs * n2 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    OSRC_CK(cudaMemsetAsync(bs->rn.p, 0, R * sizeof(double), st));
+    norm_rows64_kernel<<<nrhs, 256, 0, st>>>(n2, B, bs->bn.p);
+    std::vector<double> hb(nrhs), hr(nrhs);
+    OSRC_CK(cudaMemcpyAsync(hb.data(), bs->bn.p, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    OSRC_CK(cudaStreamSynchronize(st));
+    const size_t plane = (size_t)n2 * R;
+    const unsigned gp = (unsigned)((plane + 255) / 256);
+    const unsigned gx = (unsigned)(((size_t)nrhs * n2 + 255) / 256);
+    double worst = 1.0;
+    int refine = 0;
+    for (refine = 0; refine <= max_refine; ++refine) {
+        norm_rows64_kernel<<<nrhs, 256, 0, st>>>(n2, bs->R64.p, bs->rn.p);
+        OSRC_CK(cudaMemcpyAsync(hr.data(), bs->rn.p, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+        OSRC_CK(cudaStreamSynchronize(st));
+        worst = 0.0;
+        for (int r = 0; r < nrhs; ++r) worst = fmax(worst, hb[r] > 0 ? hr[r] / hb[r] : 0.0);
+        if (!std::isfinite(worst)) return OSRC_BREAKDOWN;
+        if (worst <= tol || refine == max_refine) break;
+        // scaled residual block: c = R64 / |R64_r|
+        OSRC_CK(cudaMemcpyAsync(bs->scl.p, bs->rn.p, nrhs * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        to_block32_kernel<<<gp, 256, 0, st>>>(n2, nrhs, R, bs->R64.p, bs->scl.p, bs->t2.p);
+        OSRC_CK(cudaMemcpyAsync(bs->w.p, bs->t2.p, plane * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+        int its = 0;
+        OSRC_TRY(batched_inner_gmres(pb, bs->w.p, (float)inner_tol, inner_maxit, 1e-5f, 500, &its, st));
+        info.inner_iterations += its;
+        add_block32_kernel<<<gx, 256, 0, st>>>(n2, nrhs, R, bs->t1.p, bs->scl.p, X);
+        dim3 grid((n2 + RS_TM - 1) / RS_TM, (nrhs + RS_TR - 1) / RS_TR);
+        resid64_kernel<<<grid, RS_TM * RS_TR / 2, 0, st>>>(n2, nrhs, pb->d_dense.p, X, B, bs->R64.p);
+        pb->launches += 3;
+        OSRC_CK(cudaGetLastError());
+    }
+    int err = 0;
+    OSRC_CK(cudaMemcpyAsync(&err, bs->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    OSRC_CK(cudaStreamSynchronize(st));
+    info.refinements = refine;
+    info.residual = worst;
+    info.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (info_out) *info_out = info;
+    if (err) {
+        osrc_set_error("tensor-core GEMM: a bounded wait gave up");
+        return OSRC_TIMEOUT;
+    }
+    return worst <= tol ? OSRC_OK : OSRC_NOT_CONVERGED;
+}
+
+// y = op(x) with the inner (mixed-precision) pieces, for tests: what 0 the
+// BF16 far + exact near operator, 1 the FP32 preconditioner P M^-1, 2 both.
+extern "C" int osrc_dense_batched_apply(osrc_problem *pb, const void *x, void *y, int nrhs, int what,
+                                        void *stream) {
+    if (!pb || !x || !y || nrhs < 1 || nrhs > 128 || what < 0 || what > 2) return OSRC_INVALID_ARG;
+    if (pb->p.precision != OSRC_FP64_DENSE) return OSRC_UNSUPPORTED;
+    OSRC_CK(cudaSetDevice(pb->mesh->ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int R = (nrhs + 7) / 8 * 8;
+    OSRC_TRY(batched_prepare(pb, R, 8, st));
+    BatchedState *bs = pb->batched;
+    const int n2 = bs->n2;
+    const size_t plane = (size_t)n2 * R;
+    fill1_kernel<<<(R + 127) / 128, 128, 0, st>>>(bs->scl.p, R);
+    to_block32_kernel<<<(unsigned)((plane + 255) / 256), 256, 0, st>>>(n2, nrhs, R, (const double2 *)x,
+                                                                      bs->scl.p, bs->t2.p);
+    float2 *out = bs->t2.p;
+    if (what == 0 || what == 2) {
+        OSRC_TRY(batched_matvec(pb, bs->t2.p, bs->w.p, st));
+        out = bs->w.p;
+    }
+    if (what == 1 || what == 2) {
+        OSRC_TRY(batched_precond(pb, out, bs->t1.p, 1e-6f, 1000, st));
+        out = bs->t1.p;
+    }
+    from_block32_kernel<<<(unsigned)(((size_t)n2 * nrhs + 255) / 256), 256, 0, st>>>(n2, nrhs, R, out,
+                                                                                     (double2 *)y);
+    OSRC_CK(cudaGetLastError());
+    int err = 0;
+    OSRC_CK(cudaMemcpyAsync(&err, bs->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    OSRC_CK(cudaStreamSynchronize(st));
+    return err ? OSRC_TIMEOUT : OSRC_OK;
+}

@@ -447,6 +447,7 @@ extern "C" void osrc_problem_destroy(osrc_problem *pb) {
     if (pb->h_res) cudaFreeHost(pb->h_res);
     for (auto &e : pb->prof_ev)
         if (e) cudaEventDestroy(e);
+    if (pb->batched) batched_free(pb->batched);
     delete pb;
 }
 

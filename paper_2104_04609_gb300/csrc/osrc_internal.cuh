@@ -111,8 +111,12 @@ struct NearPair {
     int perm;      // pt[0..2] | ps[0..2] << 6, 2 bits each
 };
 
+struct BatchedState;
+void batched_free(BatchedState *s);
+
 struct osrc_problem {
     osrc_mesh *mesh = nullptr;
+    BatchedState *batched = nullptr;  // dense batched-solve state (k_batched.cu)
     osrc_params p{};
     int nv = 0, nt = 0, npts = 0;
     long long launches = 0;
