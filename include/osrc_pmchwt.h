@@ -216,9 +216,12 @@ typedef struct osrc_batched_info {
  * accumulation) and the touching-pair blocks exactly.  Stops when every
  * |b_r - A x_r| / |b_r| <= tol or after max_refine steps
  * (OSRC_NOT_CONVERGED).  inner_tol: relative tolerance of each inner solve
- * (e.g. 1e-3); inner_maxit <= 1000.  b, x: device, nrhs x 2nv complex FP64. */
+ * (e.g. 1e-3); inner_maxit <= 1000.  precond_tol: relative tolerance of the
+ * FP32 shifted solves inside P M^-1 (at most 500 iterations each); <= 0
+ * selects 0.1 inner_tol clamped to [1e-6, 1e-3].  b, x: device, nrhs x 2nv
+ * complex FP64. */
 int osrc_dense_batched_solve(osrc_problem *pb, const void *b, void *x, int nrhs, double tol,
-                             int max_refine, double inner_tol, int inner_maxit,
+                             int max_refine, double inner_tol, int inner_maxit, double precond_tol,
                              osrc_batched_info *info, void *stream);
 
 /* The inner pieces of osrc_dense_batched_solve on nrhs (<= 128) vectors,
@@ -228,6 +231,14 @@ int osrc_dense_batched_solve(osrc_problem *pb, const void *b, void *x, int nrhs,
  * device, nrhs x 2nv complex FP64.  Problem created with OSRC_FP64_DENSE. */
 int osrc_dense_batched_apply(osrc_problem *pb, const void *x, void *y, int nrhs, int what,
                              void *stream);
+
+/* As osrc_dense_batched_apply (which uses ptol 1e-6, pmaxit 1000), with the
+ * relative tolerance ptol and iteration cap pmaxit of the FP32 shifted
+ * solves inside P M^-1 (Sec. 2.6) given explicitly.  pits_max (host, may be
+ * NULL): the largest iteration count any of those solves took; passing it
+ * synchronises the stream. */
+int osrc_dense_batched_apply_ex(osrc_problem *pb, const void *x, void *y, int nrhs, int what,
+                                double ptol, int pmaxit, int *pits_max, void *stream);
 
 /* ---- serving loop ------------------------------------------------------------------ */
 /* A continuous-batching server for solve requests of uneven mesh size and

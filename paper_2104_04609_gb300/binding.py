@@ -144,8 +144,12 @@ SIGNATURES = {
                                       ctypes.c_int, _VP, _VP]),
     "osrc_dense_batched_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
                                                 ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                                                ctypes.POINTER(osrc_batched_info), _VP]),
+                                                ctypes.c_double, ctypes.POINTER(osrc_batched_info),
+                                                _VP]),
     "osrc_dense_batched_apply": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
+    "osrc_dense_batched_apply_ex": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_double, ctypes.c_int,
+                                                   ctypes.POINTER(ctypes.c_int), _VP]),
     "osrc_launch_count": (ctypes.c_longlong, [_VP]),
     "osrc_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "osrc_far_kernel_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong),
@@ -422,13 +426,13 @@ def osrc_gemm_bf16(A, B, C, err, stream=None):
 
 
 def osrc_dense_batched_solve(pb, b, x, tol=1e-6, max_refine=8, inner_tol=1e-3, inner_maxit=200,
-                             stream=None, raise_on_nonconvergence=True):
+                             precond_tol=0.0, stream=None, raise_on_nonconvergence=True):
     """Batched mixed-precision solve; b, x (nrhs, 2nv) complex128 CUDA tensors.
     Returns the osrc_batched_info record as a dict."""
     info = osrc_batched_info()
     s = lib().osrc_dense_batched_solve(pb, _dev(b), _dev(x), int(b.shape[0]), float(tol),
                                        int(max_refine), float(inner_tol), int(inner_maxit),
-                                       ctypes.byref(info), _stream(stream))
+                                       float(precond_tol), ctypes.byref(info), _stream(stream))
     if s != OSRC_OK and (s != OSRC_NOT_CONVERGED or raise_on_nonconvergence):
         raise OsrcError(s, "osrc_dense_batched_solve")
     return info.as_dict()
@@ -437,6 +441,16 @@ def osrc_dense_batched_solve(pb, b, x, tol=1e-6, max_refine=8, inner_tol=1e-3, i
 def osrc_dense_batched_apply(pb, x, y, what, stream=None):
     _check(lib().osrc_dense_batched_apply(pb, _dev(x), _dev(y), int(x.shape[0]), int(what),
                                           _stream(stream)), "osrc_dense_batched_apply")
+
+
+def osrc_dense_batched_apply_ex(pb, x, y, what, ptol, pmaxit, stream=None):
+    """As osrc_dense_batched_apply with the preconditioner's inner tolerance and
+    cap given; returns the largest inner iteration count."""
+    k = ctypes.c_int(0)
+    _check(lib().osrc_dense_batched_apply_ex(pb, _dev(x), _dev(y), int(x.shape[0]), int(what),
+                                             float(ptol), int(pmaxit), ctypes.byref(k),
+                                             _stream(stream)), "osrc_dense_batched_apply_ex")
+    return k.value
 
 
 def osrc_launch_count(pb):

@@ -12,12 +12,16 @@
 //   - the FP64 residual product R = B - A X of the outer refinement.
 // Block vectors of the inner solver are stored [row][rhs] (right-hand sides
 // fastest, complex FP32), so every row access is coalesced across the block.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 
 #include "osrc_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -150,37 +154,63 @@ __device__ float2 dotf(float2 a, float2 b, int conj) {
     return conj ? f2c(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x) : fmulc(a, b);
 }
 
+// Jacobi inverse diagonal of every system: dinv[s][i] = 1 / (M_ii + beta_s S_ii)
+__global__ void kry32_diag_kernel(Kry32Batch batch, int nv, const int *__restrict__ ptr,
+                                  const int *__restrict__ col, const float *__restrict__ Mv,
+                                  const float *__restrict__ Sv, float2 *__restrict__ dinv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sid = blockIdx.y;
+    if (i >= nv) return;
+    float md = 0.f, sd = 0.f;
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e)
+        if (col[e] == i) {
+            md = Mv[e];
+            sd = Sv[e];
+        }
+    const float2 be = batch.s[sid].beta;
+    dinv[(size_t)sid * nv + i] = fdivc(f2c(1.f, 0.f), f2c(md + be.x * sd, be.y * sd));
+}
+
+// One cluster of CS CTAs per (system, group of 8 right-hand sides); each CTA
+// owns a contiguous block of rows.  Search directions of other CTAs are read
+// with L2-only loads after the cluster barrier; per-right-hand-side dot
+// products are reduced over the cluster through distributed shared memory
+// and summed in rank order, so every CTA takes the same decisions.
 __global__ void __launch_bounds__(K32_THREADS)
-kry32_kernel(Kry32Batch batch, int nv, int R, const int *__restrict__ ptr, const int *__restrict__ col,
-             const float *__restrict__ Mv, const float *__restrict__ Sv, const float2 *__restrict__ F,
-             float2 *__restrict__ W, float2 *__restrict__ work, float tol, int maxit,
-             int *__restrict__ its_out) {
+kry32_kernel(Kry32Batch batch, int nv, int R, int ngroups, const int *__restrict__ ptr,
+             const int *__restrict__ col, const float *__restrict__ Mv, const float *__restrict__ Sv,
+             const float2 *__restrict__ F, const float2 *__restrict__ dinv, float2 *__restrict__ W,
+             float2 *__restrict__ work, float tol, int maxit, int *__restrict__ its_out) {
     __shared__ float red[K32_THREADS / 32][K32_G][3];
+    __shared__ float slotA[K32_G][3], slotB[K32_G][3], slotC[K32_G][3];
+    __shared__ float gath[16][K32_G][3];
+    __shared__ float sums[K32_G][3];
     __shared__ float2 sc_rho[K32_G], sc_al[K32_G], sc_be[K32_G];
-    __shared__ float sc_bb[K32_G], sc_rr[K32_G];
-    __shared__ int active[K32_G];
-    const int sid = blockIdx.x;
-    const int g0 = blockIdx.y * K32_G;
+    __shared__ float sc_bb[K32_G];
+    __shared__ int active[K32_G], stepped[K32_G];
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned cs = cl.num_blocks(), rank = cl.block_rank();
+    const int cid = blockIdx.x / cs;
+    const int sid = cid / ngroups, grp = cid % ngroups;
+    const int g0 = grp * K32_G;
     const Kry32Sys sy = batch.s[sid];
-    const int gl = threadIdx.x % K32_G;       // right-hand side within the group
-    const int rl = threadIdx.x / K32_G;       // row lane
+    const int gl = threadIdx.x % K32_G, rl = threadIdx.x / K32_G;
     const int nrl = K32_THREADS / K32_G;
+    const int rows = (nv + (int)cs - 1) / (int)cs;
+    const int r0 = min(nv, (int)rank * rows), r1 = min(nv, r0 + rows);
     const int r = g0 + gl;
     const bool rv = r < R;
     const size_t plane = (size_t)nv * R;
-    float2 *rr = work + ((size_t)sid * 5 + 0) * plane;
-    float2 *zz = work + ((size_t)sid * 5 + 1) * plane;
-    float2 *pp = work + ((size_t)sid * 5 + 2) * plane;
-    float2 *qq = work + ((size_t)sid * 5 + 3) * plane;
-    float2 *dinv = work + ((size_t)sid * 5 + 4) * plane;
+    float2 *rr = work + ((size_t)sid * 3 + 0) * plane;
+    float2 *pp = work + ((size_t)sid * 3 + 1) * plane;
+    float2 *qq = work + ((size_t)sid * 3 + 2) * plane;
     float2 *x = W + (size_t)sid * plane;
     const float2 *f = F + (size_t)sy.half * plane;
     const int cj = sy.conj;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // reduce three floats per right-hand side over the CTA into sums[g][0..2]
-    auto reduce3 = [&](float a, float b, float c, float (*out)[3]) {
-        // lanes with the same gl are 8 apart inside a warp
+    // sums[g][0..2] = cluster-wide sums of (a, b, c) for right-hand side g
+    auto reduce3 = [&](float a, float b, float c, float (*slot)[3]) {
         for (int o = 16; o >= K32_G; o >>= 1) {
             a += __shfl_xor_sync(0xffffffffu, a, o);
             b += __shfl_xor_sync(0xffffffffu, b, o);
@@ -199,93 +229,108 @@ kry32_kernel(Kry32Batch batch, int nv, int R, const int *__restrict__ ptr, const
                 s1 += red[w][threadIdx.x][1];
                 s2 += red[w][threadIdx.x][2];
             }
-            out[threadIdx.x][0] = s0;
-            out[threadIdx.x][1] = s1;
-            out[threadIdx.x][2] = s2;
+            slot[threadIdx.x][0] = s0;
+            slot[threadIdx.x][1] = s1;
+            slot[threadIdx.x][2] = s2;
+        }
+        cl.sync();
+        if (threadIdx.x < cs * K32_G) {
+            const int rk = threadIdx.x / K32_G, g = threadIdx.x % K32_G;
+            const float *rem = cl.map_shared_rank(&slot[0][0], rk);
+            gath[rk][g][0] = rem[3 * g];
+            gath[rk][g][1] = rem[3 * g + 1];
+            gath[rk][g][2] = rem[3 * g + 2];
+        }
+        __syncthreads();
+        if (threadIdx.x < K32_G) {
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+            for (unsigned rk = 0; rk < cs; ++rk) {
+                s0 += gath[rk][threadIdx.x][0];
+                s1 += gath[rk][threadIdx.x][1];
+                s2 += gath[rk][threadIdx.x][2];
+            }
+            sums[threadIdx.x][0] = s0;
+            sums[threadIdx.x][1] = s1;
+            sums[threadIdx.x][2] = s2;
         }
         __syncthreads();
     };
-    __shared__ float sums[K32_G][3];
 
     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-    for (int i = rl; i < nv; i += nrl) {
-        if (!rv) continue;
-        float md = 0.f, sd = 0.f;
-        for (int e = ptr[i]; e < ptr[i + 1]; ++e)
-            if (col[e] == i) { md = Mv[e]; sd = Sv[e]; }
-        const float2 d = f2c(md + sy.beta.x * sd, sy.beta.y * sd);
-        const float2 di = fdivc(f2c(1.f, 0.f), d);
-        const size_t k = (size_t)i * R + r;
-        const float2 b = f[k];
-        dinv[k] = di;
-        x[k] = f2c(0.f, 0.f);
-        rr[k] = b;
-        const float2 zi = fmulc(di, b);
-        zz[k] = zi;
-        pp[k] = zi;
-        const float2 t = dotf(b, zi, cj);
-        a0 += t.x;
-        a1 += t.y;
-        a2 += fabs2(b);
-    }
-    reduce3(a0, a1, a2, sums);
+    if (rv)
+        for (int i = r0 + rl; i < r1; i += nrl) {
+            const float2 di = dinv[(size_t)sid * nv + i];
+            const size_t k = (size_t)i * R + r;
+            const float2 b = f[k];
+            x[k] = f2c(0.f, 0.f);
+            rr[k] = b;
+            const float2 zi = fmulc(di, b);
+            pp[k] = zi;
+            const float2 t = dotf(b, zi, cj);
+            a0 += t.x;
+            a1 += t.y;
+            a2 += fabs2(b);
+        }
+    reduce3(a0, a1, a2, slotA);
     if (threadIdx.x < K32_G) {
         sc_rho[threadIdx.x] = f2c(sums[threadIdx.x][0], sums[threadIdx.x][1]);
         sc_bb[threadIdx.x] = sums[threadIdx.x][2];
         active[threadIdx.x] = (g0 + (int)threadIdx.x < R && sums[threadIdx.x][2] > 0.f) ? 1 : 0;
-        if (its_out && g0 + (int)threadIdx.x < R) its_out[sid * R + g0 + threadIdx.x] = 0;
+        if (rank == 0 && its_out && g0 + (int)threadIdx.x < R) its_out[sid * R + g0 + threadIdx.x] = 0;
     }
-    __syncthreads();
+    cl.sync();  // p complete everywhere
     for (int it = 1; it <= maxit; ++it) {
         int any = 0;
         for (int g = 0; g < K32_G; ++g) any |= active[g];
         if (!any) break;
+        // q = A p on own rows, (p, q)
         const bool act = rv && active[gl];
         float w0 = 0.f, w1 = 0.f;
-        for (int i = rl; i < nv; i += nrl) {
-            if (!act) continue;
-            float2 mp = f2c(0.f, 0.f), sp = f2c(0.f, 0.f);
-            for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
-                const float2 pj = pp[(size_t)col[e] * R + r];
-                mp = fadd(mp, fscale(pj, Mv[e]));
-                sp = fadd(sp, fscale(pj, Sv[e]));
+        if (act)
+            for (int i = r0 + rl; i < r1; i += nrl) {
+                float2 mp = f2c(0.f, 0.f), sp = f2c(0.f, 0.f), pi = f2c(0.f, 0.f);
+                for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+                    const int j = col[e];
+                    const float2 pj = __ldcg(&pp[(size_t)j * R + r]);
+                    if (j == i) pi = pj;
+                    mp = fadd(mp, fscale(pj, Mv[e]));
+                    sp = fadd(sp, fscale(pj, Sv[e]));
+                }
+                const float2 acc = fadd(mp, fmulc(sy.beta, sp));
+                qq[(size_t)i * R + r] = acc;
+                const float2 t = dotf(pi, acc, cj);
+                w0 += t.x;
+                w1 += t.y;
             }
-            const float2 acc = fadd(mp, fmulc(sy.beta, sp));
-            const size_t k = (size_t)i * R + r;
-            qq[k] = acc;
-            const float2 t = dotf(pp[k], acc, cj);
-            w0 += t.x;
-            w1 += t.y;
-        }
-        reduce3(w0, w1, 0.f, sums);
+        reduce3(w0, w1, 0.f, slotB);
         if (threadIdx.x < K32_G) {
             const float2 pq = f2c(sums[threadIdx.x][0], sums[threadIdx.x][1]);
             if (active[threadIdx.x] && !(fabs2(pq) > 0.f)) active[threadIdx.x] = 0;  // breakdown: freeze
+            stepped[threadIdx.x] = active[threadIdx.x];
             sc_al[threadIdx.x] = active[threadIdx.x] ? fdivc(sc_rho[threadIdx.x], pq) : f2c(0.f, 0.f);
         }
         __syncthreads();
-        const bool act2 = rv && active[gl];
+        // r -= alpha q, z = D^-1 r, (r, z), |r|^2
+        const bool act2 = rv && stepped[gl];
         const float2 al = sc_al[gl];
         float u0 = 0.f, u1 = 0.f, u2 = 0.f;
-        for (int i = rl; i < nv; i += nrl) {
-            if (!act2) continue;
-            const size_t k = (size_t)i * R + r;
-            x[k] = fadd(x[k], fmulc(al, pp[k]));
-            const float2 ri = fsub(rr[k], fmulc(al, qq[k]));
-            rr[k] = ri;
-            const float2 zi = fmulc(dinv[k], ri);
-            zz[k] = zi;
-            const float2 t = dotf(ri, zi, cj);
-            u0 += t.x;
-            u1 += t.y;
-            u2 += fabs2(ri);
-        }
-        reduce3(u0, u1, u2, sums);
+        if (act2)
+            for (int i = r0 + rl; i < r1; i += nrl) {
+                const size_t k = (size_t)i * R + r;
+                const float2 ri = fsub(rr[k], fmulc(al, qq[k]));
+                rr[k] = ri;
+                const float2 zi = fmulc(dinv[(size_t)sid * nv + i], ri);
+                const float2 t = dotf(ri, zi, cj);
+                u0 += t.x;
+                u1 += t.y;
+                u2 += fabs2(ri);
+            }
+        reduce3(u0, u1, u2, slotC);
         if (threadIdx.x < K32_G) {
             const int g = threadIdx.x;
             if (active[g]) {
                 const float2 rn = f2c(sums[g][0], sums[g][1]);
-                if (its_out) its_out[sid * R + g0 + g] = it;
+                if (rank == 0 && its_out) its_out[sid * R + g0 + g] = it;
                 if (sums[g][2] <= tol * tol * sc_bb[g] || !(fabs2(sc_rho[g]) > 0.f)) {
                     active[g] = 0;
                     sc_be[g] = f2c(0.f, 0.f);
@@ -296,15 +341,19 @@ kry32_kernel(Kry32Batch batch, int nv, int R, const int *__restrict__ ptr, const
             }
         }
         __syncthreads();
+        // x += alpha p_old (every column that stepped); p = z + beta p_old (columns still active)
         const bool act3 = rv && active[gl];
         const float2 be = sc_be[gl];
-        for (int i = rl; i < nv; i += nrl) {
-            if (!act3) continue;
-            const size_t k = (size_t)i * R + r;
-            pp[k] = fadd(zz[k], fmulc(be, pp[k]));
-        }
-        __syncthreads();
+        if (act2)
+            for (int i = r0 + rl; i < r1; i += nrl) {
+                const size_t k = (size_t)i * R + r;
+                const float2 po = pp[k];
+                x[k] = fadd(x[k], fmulc(al, po));
+                if (act3) pp[k] = fadd(fmulc(dinv[(size_t)sid * nv + i], rr[k]), fmulc(be, po));
+            }
+        cl.sync();
     }
+    cl.sync();  // shared memory of every CTA stays alive until all have read it
 }
 
 struct OsrcComb32 {
@@ -337,28 +386,62 @@ __global__ void d2f_kernel(int n, const double *__restrict__ a, float *__restric
 // FP32 batched Arnoldi: block vectors [n2][R]
 // ---------------------------------------------------------------------------
 // out[i][r] = sum_m conj(V_i[m][r]) w[m][r] for i < nvec; block per i.
-__global__ void bdots_kernel(const float2 *__restrict__ V, size_t ldv, int nvec, const float2 *__restrict__ w,
-                             int n2, int R, float2 *__restrict__ out) {
-    const int i = blockIdx.x;
-    if (i >= nvec) return;
-    __shared__ float2 acc[256];
+// Column dot products in two deterministic stages.  Stage 1: block (c, i)
+// sums conj(V_i[m][r]) w[m][r] over row chunk c into part[i][c][r];
+// stage 2 adds the chunks in order.  nchunk * nvec blocks keep every SM
+// streaming even for the first basis vectors.
+constexpr int BD_THREADS = 256;
+constexpr int BD_MAX_CHUNK = 64;
+
+__global__ void __launch_bounds__(BD_THREADS)
+bdots_part_kernel(const float2 *__restrict__ V, size_t ldv, const float2 *__restrict__ w, int n2, int R,
+                  int nchunk, float2 *__restrict__ part) {
+    __shared__ float2 acc[BD_THREADS];
+    const int c = blockIdx.x, i = blockIdx.y;
     const int r = threadIdx.x % R;
-    const int rl = threadIdx.x / R, nrl = blockDim.x / R;
+    const int rl = threadIdx.x / R, nrl = BD_THREADS / R;
+    const int rows = (n2 + nchunk - 1) / nchunk;
+    const int m0 = c * rows, m1 = min(n2, m0 + rows);
     const float2 *v = V + ldv * i;
-    float2 s = f2c(0.f, 0.f);
-    if (threadIdx.x < nrl * R)
-        for (int m = rl; m < n2; m += nrl) {
-            const float2 a = v[(size_t)m * R + r], b = w[(size_t)m * R + r];
-            s.x += a.x * b.x + a.y * b.y;
-            s.y += a.x * b.y - a.y * b.x;
+    float2 s0 = f2c(0.f, 0.f), s1 = f2c(0.f, 0.f);
+    if (rl < nrl) {
+        int m = m0 + rl;
+        for (; m + nrl < m1; m += 2 * nrl) {
+            const float2 a0 = v[(size_t)m * R + r], b0 = w[(size_t)m * R + r];
+            const float2 a1 = v[(size_t)(m + nrl) * R + r], b1 = w[(size_t)(m + nrl) * R + r];
+            s0.x += a0.x * b0.x + a0.y * b0.y;
+            s0.y += a0.x * b0.y - a0.y * b0.x;
+            s1.x += a1.x * b1.x + a1.y * b1.y;
+            s1.y += a1.x * b1.y - a1.y * b1.x;
         }
-    acc[threadIdx.x] = s;
+        if (m < m1) {
+            const float2 a0 = v[(size_t)m * R + r], b0 = w[(size_t)m * R + r];
+            s0.x += a0.x * b0.x + a0.y * b0.y;
+            s0.y += a0.x * b0.y - a0.y * b0.x;
+        }
+    }
+    acc[threadIdx.x] = fadd(s0, s1);
     __syncthreads();
     if (threadIdx.x < R) {
         float2 t = f2c(0.f, 0.f);
         for (int l = 0; l < nrl; ++l) t = fadd(t, acc[l * R + threadIdx.x]);
-        out[(size_t)i * R + threadIdx.x] = t;
+        part[((size_t)i * nchunk + c) * R + threadIdx.x] = t;
     }
+}
+
+// out[i][r] = sum_c part[i][c][r]; with nrm != NULL (one vector, V = w)
+// nrm[r] = sqrt(Re out[0][r]) instead
+__global__ void bdots_fin_kernel(const float2 *__restrict__ part, int nvec, int nchunk, int R,
+                                 float2 *__restrict__ out, float *__restrict__ nrm) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nvec * R) return;
+    const int i = k / R, r = k % R;
+    float2 t = f2c(0.f, 0.f);
+    for (int c = 0; c < nchunk; ++c) t = fadd(t, part[((size_t)i * nchunk + c) * R + r]);
+    if (nrm)
+        nrm[r] = sqrtf(fmaxf(t.x, 0.f));
+    else
+        out[k] = t;
 }
 
 // w[m][r] -= sum_i h[i][r] V_i[m][r]
@@ -370,23 +453,6 @@ __global__ void bupdate_kernel(const float2 *__restrict__ V, size_t ldv, int nve
     float2 s = w[k];
     for (int i = 0; i < nvec; ++i) s = fsub(s, fmulc(h[(size_t)i * R + r], V[ldv * i + k]));
     w[k] = s;
-}
-
-// nrm[r] = |w[:, r]|
-__global__ void bnorm_kernel(const float2 *__restrict__ w, int n2, int R, float *__restrict__ nrm) {
-    __shared__ float acc[256];
-    const int r = threadIdx.x % R;
-    const int rl = threadIdx.x / R, nrl = blockDim.x / R;
-    float s = 0.f;
-    if (threadIdx.x < nrl * R)
-        for (int m = rl; m < n2; m += nrl) s += fabs2(w[(size_t)m * R + r]);
-    acc[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x < R) {
-        float t = 0.f;
-        for (int l = 0; l < nrl; ++l) t += acc[l * R + threadIdx.x];
-        nrm[threadIdx.x] = sqrtf(t);
-    }
 }
 
 // v[m][r] = w[m][r] / nrm[r] (0 where the column is frozen or nrm is 0)
@@ -603,8 +669,10 @@ struct BatchedState {
     DBuf<float> M32, S32;
     DBuf<int> err;
     DBuf<float2> kwork, kW;     // multi-RHS Krylov work and solutions
+    DBuf<float2> kdinv;         // Jacobi inverse diagonals [system][row]
     DBuf<float2> V, w, t1, t2;  // inner GMRES basis and temporaries
     DBuf<float2> H, hcol, h2, g, sn, yv;
+    DBuf<float2> part;          // per-chunk partial column dot products
     DBuf<float> cs, nrm, beta, res;
     DBuf<int> done, its, kits;
     DBuf<double2> X64, R64;
@@ -646,7 +714,8 @@ int batched_prepare(osrc_problem *pb, int R, int maxit_inner, cudaStream_t st) {
         OSRC_TRY(bs->Bcat.alloc(ctx, (size_t)2 * R * bs->Kp));
         OSRC_CK(cudaMemsetAsync(bs->Bcat.p, 0, (size_t)2 * R * bs->Kp * sizeof(__nv_bfloat16), st));
         OSRC_TRY(bs->C.alloc(ctx, (size_t)bs->Mp * 2 * R));
-        OSRC_TRY(bs->kwork.alloc(ctx, (size_t)nsys * 5 * vplane));
+        OSRC_TRY(bs->kwork.alloc(ctx, (size_t)nsys * 3 * vplane));
+        OSRC_TRY(bs->kdinv.alloc(ctx, (size_t)nsys * nv));
         OSRC_TRY(bs->kW.alloc(ctx, (size_t)nsys * vplane));
         OSRC_TRY(bs->V.alloc(ctx, (size_t)(maxit_inner + 1) * plane));
         OSRC_TRY(bs->w.alloc(ctx, plane));
@@ -655,6 +724,7 @@ int batched_prepare(osrc_problem *pb, int R, int maxit_inner, cudaStream_t st) {
         OSRC_TRY(bs->H.alloc(ctx, (size_t)(maxit_inner + 1) * (maxit_inner + 1) * R));
         OSRC_TRY(bs->hcol.alloc(ctx, (size_t)(maxit_inner + 1) * R));
         OSRC_TRY(bs->h2.alloc(ctx, (size_t)(maxit_inner + 1) * R));
+        OSRC_TRY(bs->part.alloc(ctx, (size_t)(maxit_inner + 1) * BD_MAX_CHUNK * R));
         OSRC_TRY(bs->g.alloc(ctx, (size_t)(maxit_inner + 1) * R));
         OSRC_TRY(bs->sn.alloc(ctx, (size_t)(maxit_inner + 1) * R));
         OSRC_TRY(bs->yv.alloc(ctx, (size_t)(maxit_inner + 1) * R));
@@ -703,9 +773,27 @@ static int batched_precond(osrc_problem *pb, const float2 *y, float2 *z, float t
     }
     const double2 be0 = cscale(inv, -1.0);
     b.s[np + 1] = Kry32Sys{make_float2((float)be0.x, (float)be0.y), 1, 0};
-    dim3 grid(b.nsys, (R + K32_G - 1) / K32_G);
-    kry32_kernel<<<grid, K32_THREADS, 0, st>>>(b, nv, R, pb->d_ms_ptr.p, pb->d_ms_col.p, bs->M32.p, bs->S32.p, y,
-                                               bs->kW.p, bs->kwork.p, tol, maxit, bs->kits.p);
+    kry32_diag_kernel<<<dim3((nv + 255) / 256, b.nsys), 256, 0, st>>>(b, nv, pb->d_ms_ptr.p, pb->d_ms_col.p,
+                                                                        bs->M32.p, bs->S32.p, bs->kdinv.p);
+    const int ngroups = (R + K32_G - 1) / K32_G;
+    int cs = (nv + 999) / 1000;
+    if (cs < 1) cs = 1;
+    if (cs > 8) cs = 8;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b.nsys * ngroups * cs, 1, 1);
+    cfg.blockDim = dim3(K32_THREADS, 1, 1);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    OSRC_CK(cudaLaunchKernelEx(&cfg, kry32_kernel, b, nv, R, ngroups, (const int *)pb->d_ms_ptr.p,
+                               (const int *)pb->d_ms_col.p, (const float *)bs->M32.p, (const float *)bs->S32.p,
+                               y, (const float2 *)bs->kdinv.p, bs->kW.p, bs->kwork.p, tol, maxit,
+                               bs->kits.p));
     OsrcComb32 c{};
     c.np = np;
     c.ik = make_float2(0.f, (float)pb->k_osrc);
@@ -721,7 +809,7 @@ static int batched_precond(osrc_problem *pb, const float2 *y, float2 *z, float t
     c.g0 = make_float2((float)pb->g0.x, (float)pb->g0.y);
     const size_t plane = (size_t)nv * R;
     osrc_combine32_kernel<<<(unsigned)((plane + 255) / 256), 256, 0, st>>>(nv, R, c, bs->kW.p, z);
-    pb->launches += 2;
+    pb->launches += 3;
     OSRC_CK(cudaGetLastError());
     return OSRC_OK;
 }
@@ -736,10 +824,19 @@ static int batched_inner_gmres(osrc_problem *pb, const float2 *c, float tol, int
     const size_t plane = (size_t)n2 * R;
     const int ldh = maxit + 1;
     const unsigned gp = (unsigned)((plane + 255) / 256);
-    const int thr = (256 / R) * R;
+    const int nchunk = std::max(1, std::min(BD_MAX_CHUNK, n2 / 64));
+    auto dots = [&](int nvec, const float2 *w, float2 *out) {
+        bdots_part_kernel<<<dim3(nchunk, nvec), BD_THREADS, 0, st>>>(bs->V.p, plane, w, n2, R, nchunk,
+                                                                     bs->part.p);
+        bdots_fin_kernel<<<(nvec * R + 255) / 256, 256, 0, st>>>(bs->part.p, nvec, nchunk, R, out, nullptr);
+    };
+    auto norm = [&](const float2 *w) {
+        bdots_part_kernel<<<dim3(nchunk, 1), BD_THREADS, 0, st>>>(w, plane, w, n2, R, nchunk, bs->part.p);
+        bdots_fin_kernel<<<(R + 255) / 256, 256, 0, st>>>(bs->part.p, 1, nchunk, R, nullptr, bs->nrm.p);
+    };
     // rhs of the preconditioned system
     OSRC_TRY(batched_precond(pb, c, bs->w.p, ptol, pmaxit, st));
-    bnorm_kernel<<<1, thr, 0, st>>>(bs->w.p, n2, R, bs->nrm.p);
+    norm(bs->w.p);
     binit_kernel<<<(R + 127) / 128, 128, 0, st>>>(R, bs->nrm.p, bs->beta.p, bs->g.p, bs->done.p, bs->its.p);
     OSRC_CK(cudaMemsetAsync(bs->g.p + R, 0, (size_t)maxit * R * sizeof(float2), st));
     bscale_kernel<<<gp, 256, 0, st>>>(bs->w.p, bs->nrm.p, bs->done.p, bs->V.p, n2, R);
@@ -749,17 +846,17 @@ static int batched_inner_gmres(osrc_problem *pb, const float2 *c, float tol, int
         float2 *vj = bs->V.p + (size_t)j * plane;
         OSRC_TRY(batched_matvec(pb, vj, bs->t2.p, st));
         OSRC_TRY(batched_precond(pb, bs->t2.p, bs->w.p, ptol, pmaxit, st));
-        bdots_kernel<<<j + 1, thr, 0, st>>>(bs->V.p, plane, j + 1, bs->w.p, n2, R, bs->hcol.p);
+        dots(j + 1, bs->w.p, bs->hcol.p);
         bupdate_kernel<<<gp, 256, 0, st>>>(bs->V.p, plane, j + 1, bs->hcol.p, bs->w.p, n2, R);
-        bdots_kernel<<<j + 1, thr, 0, st>>>(bs->V.p, plane, j + 1, bs->w.p, n2, R, bs->h2.p);
+        dots(j + 1, bs->w.p, bs->h2.p);
         bupdate_kernel<<<gp, 256, 0, st>>>(bs->V.p, plane, j + 1, bs->h2.p, bs->w.p, n2, R);
-        bnorm_kernel<<<1, thr, 0, st>>>(bs->w.p, n2, R, bs->nrm.p);
+        norm(bs->w.p);
         addcols_kernel<<<((j + 1) * R + 255) / 256, 256, 0, st>>>(bs->hcol.p, bs->h2.p, (j + 1) * R);
         bgivens_kernel<<<(R + 127) / 128, 128, 0, st>>>(j, ldh, R, bs->hcol.p, bs->nrm.p, bs->H.p, bs->cs.p,
                                                         bs->sn.p, bs->g.p, bs->beta.p, tol, bs->done.p,
                                                         bs->its.p, bs->res.p);
         bscale_kernel<<<gp, 256, 0, st>>>(bs->w.p, bs->nrm.p, bs->done.p, bs->V.p + (size_t)(j + 1) * plane, n2, R);
-        pb->launches += 8;
+        pb->launches += 11;
         OSRC_CK(cudaMemcpyAsync(hdone.data(), bs->done.p, R * sizeof(int), cudaMemcpyDeviceToHost, st));
         OSRC_CK(cudaStreamSynchronize(st));
         bool all = true;
@@ -781,10 +878,10 @@ static int batched_inner_gmres(osrc_problem *pb, const float2 *c, float tol, int
 // outer FP64 iterative refinement
 // ---------------------------------------------------------------------------
 extern "C" int osrc_dense_batched_solve(osrc_problem *pb, const void *b, void *x, int nrhs, double tol,
-                                        int max_refine, double inner_tol, int inner_maxit,
+                                        int max_refine, double inner_tol, int inner_maxit, double precond_tol,
                                         osrc_batched_info *info_out, void *stream) {
     if (!pb || !b || !x || nrhs < 1 || nrhs > 128 || !(tol > 0.0) || max_refine < 1 || !(inner_tol > 0.0) ||
-        inner_tol >= 1.0 || inner_maxit < 1 || inner_maxit > 1000)
+        inner_tol >= 1.0 || inner_maxit < 1 || inner_maxit > 1000 || !(precond_tol < 1.0))
         return OSRC_INVALID_ARG;
     if (pb->p.precision != OSRC_FP64_DENSE) {
         osrc_set_error("osrc_dense_batched_solve needs a problem created with OSRC_FP64_DENSE");
@@ -827,7 +924,8 @@ extern "C" int osrc_dense_batched_solve(osrc_problem *pb, const void *b, void *x
         to_block32_kernel<<<gp, 256, 0, st>>>(n2, nrhs, R, bs->R64.p, bs->scl.p, bs->t2.p);
         OSRC_CK(cudaMemcpyAsync(bs->w.p, bs->t2.p, plane * sizeof(float2), cudaMemcpyDeviceToDevice, st));
         int its = 0;
-        OSRC_TRY(batched_inner_gmres(pb, bs->w.p, (float)inner_tol, inner_maxit, 1e-5f, 500, &its, st));
+        const double ptol = precond_tol > 0.0 ? precond_tol : std::min(1e-3, std::max(1e-6, 0.1 * inner_tol));
+        OSRC_TRY(batched_inner_gmres(pb, bs->w.p, (float)inner_tol, inner_maxit, (float)ptol, 500, &its, st));
         info.inner_iterations += its;
         add_block32_kernel<<<gx, 256, 0, st>>>(n2, nrhs, R, bs->t1.p, bs->scl.p, X);
         dim3 grid((n2 + RS_TM - 1) / RS_TM, (nrhs + RS_TR - 1) / RS_TR);
@@ -849,11 +947,10 @@ extern "C" int osrc_dense_batched_solve(osrc_problem *pb, const void *b, void *x
     return worst <= tol ? OSRC_OK : OSRC_NOT_CONVERGED;
 }
 
-// y = op(x) with the inner (mixed-precision) pieces, for tests: what 0 the
-// BF16 far + exact near operator, 1 the FP32 preconditioner P M^-1, 2 both.
-extern "C" int osrc_dense_batched_apply(osrc_problem *pb, const void *x, void *y, int nrhs, int what,
-                                        void *stream) {
+extern "C" int osrc_dense_batched_apply_ex(osrc_problem *pb, const void *x, void *y, int nrhs, int what,
+                                           double ptol, int pmaxit, int *pits_max, void *stream) {
     if (!pb || !x || !y || nrhs < 1 || nrhs > 128 || what < 0 || what > 2) return OSRC_INVALID_ARG;
+    if (!(ptol > 0.0) || pmaxit < 1) return OSRC_INVALID_ARG;
     if (pb->p.precision != OSRC_FP64_DENSE) return OSRC_UNSUPPORTED;
     OSRC_CK(cudaSetDevice(pb->mesh->ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
@@ -871,8 +968,17 @@ extern "C" int osrc_dense_batched_apply(osrc_problem *pb, const void *x, void *y
         out = bs->w.p;
     }
     if (what == 1 || what == 2) {
-        OSRC_TRY(batched_precond(pb, out, bs->t1.p, 1e-6f, 1000, st));
+        OSRC_TRY(batched_precond(pb, out, bs->t1.p, (float)ptol, pmaxit, st));
         out = bs->t1.p;
+        if (pits_max) {
+            const int ns = 2 * pb->p.n_pade + 2;
+            std::vector<int> k((size_t)ns * R);
+            OSRC_CK(cudaMemcpyAsync(k.data(), bs->kits.p, k.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+            OSRC_CK(cudaStreamSynchronize(st));
+            int mx = 0;
+            for (int v : k) mx = v > mx ? v : mx;
+            *pits_max = mx;
+        }
     }
     from_block32_kernel<<<(unsigned)(((size_t)n2 * nrhs + 255) / 256), 256, 0, st>>>(n2, nrhs, R, out,
                                                                                      (double2 *)y);
@@ -881,4 +987,11 @@ extern "C" int osrc_dense_batched_apply(osrc_problem *pb, const void *x, void *y
     OSRC_CK(cudaMemcpyAsync(&err, bs->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     OSRC_CK(cudaStreamSynchronize(st));
     return err ? OSRC_TIMEOUT : OSRC_OK;
+}
+
+// y = op(x) with the inner (mixed-precision) pieces, for tests: what 0 the
+// BF16 far + exact near operator, 1 the FP32 preconditioner P M^-1, 2 both.
+extern "C" int osrc_dense_batched_apply(osrc_problem *pb, const void *x, void *y, int nrhs, int what,
+                                        void *stream) {
+    return osrc_dense_batched_apply_ex(pb, x, y, nrhs, what, 1e-6, 1000, nullptr, stream);
 }

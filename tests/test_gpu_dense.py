@@ -66,6 +66,13 @@ def test_batched_inner_pieces(B):
         B.osrc_precond_apply(S.pb, t1, ref, 12)
         e1 = float(torch.linalg.norm(y - ref) / torch.linalg.norm(ref))
         assert e0 < 1e-2 and e1 < 1e-4, (e0, e1)
+        # looser inner tolerance: fewer shifted-solve iterations, error of that order
+        k_tight = B.osrc_dense_batched_apply_ex(S.pb, x, y, 1, 1e-6, 1000)
+        k_loose = B.osrc_dense_batched_apply_ex(S.pb, x, y, 1, 1e-2, 1000)
+        e2 = float(torch.linalg.norm(y - ref) / torch.linalg.norm(ref))
+        assert 1 <= k_loose < k_tight <= 1000 and e2 < 5e-2, (k_loose, k_tight, e2)
+        with pytest.raises(B.OsrcError):
+            B.osrc_dense_batched_apply_ex(S.pb, x, y, 1, 0.0, 1000)
     finally:
         S.close()
 
@@ -91,5 +98,12 @@ def test_batched_mixed_precision_solve_matches_direct(B):
         ref = np.linalg.solve(Bm, b.cpu().numpy().T).T
         err = np.linalg.norm(x.cpu().numpy() - ref, axis=1) / np.linalg.norm(ref, axis=1)
         assert err.max() < 1e-8, err.max()
+        # an explicit, looser preconditioner tolerance reaches the same solution
+        x2 = torch.zeros_like(b)
+        info2 = B.osrc_dense_batched_solve(S.pb, b, x2, tol=1e-10, max_refine=12, inner_tol=1e-3,
+                                           inner_maxit=100, precond_tol=1e-3)
+        assert info2["residual"] <= 1e-10
+        err2 = np.linalg.norm(x2.cpu().numpy() - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert err2.max() < 1e-8, err2.max()
     finally:
         S.close()
