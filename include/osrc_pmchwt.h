@@ -232,9 +232,25 @@ int osrc_dense_batched_solve(osrc_problem *pb, const void *b, void *x, int nrhs,
 int osrc_dense_batched_apply(osrc_problem *pb, const void *x, void *y, int nrhs, int what,
                              void *stream);
 
+/* Explicit preconditioner for the batched dense solve: P M^-1 (Sec. 2.4,
+ * 2.6) is applied once to every unit vector (blocks of 128 columns, FP32
+ * shifted solves to relative tolerance tol, at most maxit iterations each)
+ * and stored as a 2nv x 2nv complex matrix in BF16, packed like the system
+ * matrix (1 GB at nv = 8000).  From then on osrc_dense_batched_solve
+ * applies the preconditioner as one tensor-core GEMM per inner iteration
+ * instead of 2 N_p + 2 shifted Krylov solves.  The rounding of this matrix
+ * changes the inner iteration count, not the solution: the inner GMRES
+ * still solves A d = r, and the FP64 residual decides convergence.
+ * Synchronises the stream.  osrc_dense_precond_drop frees the matrix and
+ * returns to the iterative preconditioner. */
+int osrc_dense_precond_build(osrc_problem *pb, double tol, int maxit, void *stream);
+int osrc_dense_precond_drop(osrc_problem *pb);
+
 /* As osrc_dense_batched_apply (which uses ptol 1e-6, pmaxit 1000), with the
  * relative tolerance ptol and iteration cap pmaxit of the FP32 shifted
- * solves inside P M^-1 (Sec. 2.6) given explicitly.  pits_max (host, may be
+ * solves inside P M^-1 (Sec. 2.6) given explicitly, and what 3: P M^-1
+ * through the explicit BF16 matrix of osrc_dense_precond_build
+ * (OSRC_UNSUPPORTED if it has not been built).  pits_max (host, may be
  * NULL): the largest iteration count any of those solves took; passing it
  * synchronises the stream. */
 int osrc_dense_batched_apply_ex(osrc_problem *pb, const void *x, void *y, int nrhs, int what,

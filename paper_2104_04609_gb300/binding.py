@@ -150,6 +150,8 @@ SIGNATURES = {
     "osrc_dense_batched_apply_ex": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int,
                                                    ctypes.c_double, ctypes.c_int,
                                                    ctypes.POINTER(ctypes.c_int), _VP]),
+    "osrc_dense_precond_build": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int, _VP]),
+    "osrc_dense_precond_drop": (ctypes.c_int, [_VP]),
     "osrc_launch_count": (ctypes.c_longlong, [_VP]),
     "osrc_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "osrc_far_kernel_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong),
@@ -451,6 +453,16 @@ def osrc_dense_batched_apply_ex(pb, x, y, what, ptol, pmaxit, stream=None):
                                              float(ptol), int(pmaxit), ctypes.byref(k),
                                              _stream(stream)), "osrc_dense_batched_apply_ex")
     return k.value
+
+
+def osrc_dense_precond_build(pb, tol=1e-3, maxit=500, stream=None):
+    """Store P M^-1 as an explicit BF16 matrix for the batched dense solve."""
+    _check(lib().osrc_dense_precond_build(pb, float(tol), int(maxit), _stream(stream)),
+           "osrc_dense_precond_build")
+
+
+def osrc_dense_precond_drop(pb):
+    _check(lib().osrc_dense_precond_drop(pb), "osrc_dense_precond_drop")
 
 
 def osrc_launch_count(pb):

@@ -129,6 +129,35 @@ __global__ void unpack_near_kernel(int nv, int R, int ldc, const float *__restri
     Y[(size_t)(nv + i) * R + r] = y2;
 }
 
+// Y[m][c] = 1 if m == k0 + c else 0 (a block of R identity columns)
+__global__ void identity_block_kernel(int n2, int R, int k0, float2 *__restrict__ Y) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n2 * R) return;
+    const int m = (int)(idx / R), c = (int)(idx % R);
+    Y[idx] = f2c(m == k0 + c ? 1.f : 0.f, 0.f);
+}
+
+// Columns k0 .. k0 + R - 1 of the packed preconditioner matrix from the
+// block Z = P M^-1 [e_k0 .. e_k0+R-1]: Pcat[m][k] = Re, Pcat[m][n2 + k] = Im.
+__global__ void pack_p_block_kernel(int n2, int R, int k0, int Kp, const float2 *__restrict__ Z,
+                                    __nv_bfloat16 *__restrict__ Pcat) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n2 * R) return;
+    const int m = (int)(idx / R), c = (int)(idx % R);
+    if (k0 + c >= n2) return;
+    const float2 z = Z[idx];
+    Pcat[(size_t)m * Kp + k0 + c] = __float2bfloat16_rn(z.x);
+    Pcat[(size_t)m * Kp + n2 + k0 + c] = __float2bfloat16_rn(z.y);
+}
+
+// Y[m][r] = (C[m][r], C[m][R + r]) for the complex product of a packed matrix
+__global__ void unpack_plain_kernel(int n2, int R, int ldc, const float *__restrict__ C, float2 *__restrict__ Y) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n2 * R) return;
+    const int m = (int)(idx / R), r = (int)(idx % R);
+    Y[idx] = f2c(C[(size_t)m * ldc + r], C[(size_t)m * ldc + R + r]);
+}
+
 // ---------------------------------------------------------------------------
 // FP32 multi-right-hand-side CG / COCG: one CTA per (system, group of 8
 // right-hand sides).  System s: (M + beta_s S) w = f, rows n = nv, input f
@@ -665,6 +694,8 @@ int umma_gemm_bf16(const void *A, int M, int K, const void *Bm, int N, float *C,
 struct BatchedState {
     int n2 = 0, Mp = 0, Kp = 0, R = 0;
     DBuf<__nv_bfloat16> Acat, Bcat;
+    DBuf<__nv_bfloat16> Pcat;   // explicit preconditioner matrix P M^-1 (packed like Acat), if built
+    bool pdense = false;
     DBuf<float> C;
     DBuf<float> M32, S32;
     DBuf<int> err;
@@ -814,6 +845,26 @@ static int batched_precond(osrc_problem *pb, const float2 *y, float2 *z, float t
     return OSRC_OK;
 }
 
+// z = P M^-1 y through the explicit BF16 preconditioner matrix (one
+// tensor-core GEMM); used once osrc_dense_precond_build has run
+static int batched_precond_dense(osrc_problem *pb, const float2 *y, float2 *z, cudaStream_t st) {
+    BatchedState *bs = pb->batched;
+    const int n2 = bs->n2, R = bs->R;
+    dim3 gb((n2 + 31) / 32, (R + 31) / 32);
+    pack_b_kernel<<<gb, dim3(32, 8), 0, st>>>(n2, R, bs->Kp, y, bs->Bcat.p);
+    OSRC_TRY(umma_gemm_bf16(bs->Pcat.p, bs->Mp, bs->Kp, bs->Bcat.p, 2 * R, bs->C.p, 2 * R, bs->err.p, st));
+    const size_t plane = (size_t)n2 * R;
+    unpack_plain_kernel<<<(unsigned)((plane + 255) / 256), 256, 0, st>>>(n2, R, 2 * R, bs->C.p, z);
+    pb->launches += 3;
+    OSRC_CK(cudaGetLastError());
+    return OSRC_OK;
+}
+
+static int batched_apply_precond(osrc_problem *pb, const float2 *y, float2 *z, float ptol, int pmaxit,
+                                 cudaStream_t st) {
+    return pb->batched->pdense ? batched_precond_dense(pb, y, z, st) : batched_precond(pb, y, z, ptol, pmaxit, st);
+}
+
 // Inner solve: GMRES (FP32, classical Gram-Schmidt twice) on P M^-1 A_inner d = P M^-1 c
 // for a block c ([n2][R]); d returned in bs->t1.  Returns the largest
 // iteration count.
@@ -835,7 +886,7 @@ static int batched_inner_gmres(osrc_problem *pb, const float2 *c, float tol, int
         bdots_fin_kernel<<<(R + 255) / 256, 256, 0, st>>>(bs->part.p, 1, nchunk, R, nullptr, bs->nrm.p);
     };
     // rhs of the preconditioned system
-    OSRC_TRY(batched_precond(pb, c, bs->w.p, ptol, pmaxit, st));
+    OSRC_TRY(batched_apply_precond(pb, c, bs->w.p, ptol, pmaxit, st));
     norm(bs->w.p);
     binit_kernel<<<(R + 127) / 128, 128, 0, st>>>(R, bs->nrm.p, bs->beta.p, bs->g.p, bs->done.p, bs->its.p);
     OSRC_CK(cudaMemsetAsync(bs->g.p + R, 0, (size_t)maxit * R * sizeof(float2), st));
@@ -845,7 +896,7 @@ static int batched_inner_gmres(osrc_problem *pb, const float2 *c, float tol, int
     for (j = 0; j < maxit; ++j) {
         float2 *vj = bs->V.p + (size_t)j * plane;
         OSRC_TRY(batched_matvec(pb, vj, bs->t2.p, st));
-        OSRC_TRY(batched_precond(pb, bs->t2.p, bs->w.p, ptol, pmaxit, st));
+        OSRC_TRY(batched_apply_precond(pb, bs->t2.p, bs->w.p, ptol, pmaxit, st));
         dots(j + 1, bs->w.p, bs->hcol.p);
         bupdate_kernel<<<gp, 256, 0, st>>>(bs->V.p, plane, j + 1, bs->hcol.p, bs->w.p, n2, R);
         dots(j + 1, bs->w.p, bs->h2.p);
@@ -949,7 +1000,7 @@ extern "C" int osrc_dense_batched_solve(osrc_problem *pb, const void *b, void *x
 
 extern "C" int osrc_dense_batched_apply_ex(osrc_problem *pb, const void *x, void *y, int nrhs, int what,
                                            double ptol, int pmaxit, int *pits_max, void *stream) {
-    if (!pb || !x || !y || nrhs < 1 || nrhs > 128 || what < 0 || what > 2) return OSRC_INVALID_ARG;
+    if (!pb || !x || !y || nrhs < 1 || nrhs > 128 || what < 0 || what > 3) return OSRC_INVALID_ARG;
     if (!(ptol > 0.0) || pmaxit < 1) return OSRC_INVALID_ARG;
     if (pb->p.precision != OSRC_FP64_DENSE) return OSRC_UNSUPPORTED;
     OSRC_CK(cudaSetDevice(pb->mesh->ctx->device));
@@ -963,6 +1014,14 @@ extern "C" int osrc_dense_batched_apply_ex(osrc_problem *pb, const void *x, void
     to_block32_kernel<<<(unsigned)((plane + 255) / 256), 256, 0, st>>>(n2, nrhs, R, (const double2 *)x,
                                                                       bs->scl.p, bs->t2.p);
     float2 *out = bs->t2.p;
+    if (what == 3) {
+        if (!bs->pdense) {
+            osrc_set_error("no explicit preconditioner matrix: call osrc_dense_precond_build first");
+            return OSRC_UNSUPPORTED;
+        }
+        OSRC_TRY(batched_precond_dense(pb, bs->t2.p, bs->t1.p, st));
+        out = bs->t1.p;
+    }
     if (what == 0 || what == 2) {
         OSRC_TRY(batched_matvec(pb, bs->t2.p, bs->w.p, st));
         out = bs->w.p;
@@ -994,4 +1053,43 @@ extern "C" int osrc_dense_batched_apply_ex(osrc_problem *pb, const void *x, void
 extern "C" int osrc_dense_batched_apply(osrc_problem *pb, const void *x, void *y, int nrhs, int what,
                                         void *stream) {
     return osrc_dense_batched_apply_ex(pb, x, y, nrhs, what, 1e-6, 1000, nullptr, stream);
+}
+
+extern "C" int osrc_dense_precond_build(osrc_problem *pb, double tol, int maxit, void *stream) {
+    if (!pb || !(tol > 0.0) || !(tol < 1.0) || maxit < 1 || maxit > 1000) return OSRC_INVALID_ARG;
+    if (pb->p.precision != OSRC_FP64_DENSE) {
+        osrc_set_error("osrc_dense_precond_build needs a problem created with OSRC_FP64_DENSE");
+        return OSRC_UNSUPPORTED;
+    }
+    OSRC_CK(cudaSetDevice(pb->mesh->ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int R = 128;
+    OSRC_TRY(batched_prepare(pb, R, pb->batched ? std::max(8, pb->batched->basis_cap) : 8, st));
+    BatchedState *bs = pb->batched;
+    const int n2 = bs->n2;
+    bs->pdense = false;
+    if (!bs->Pcat.p) OSRC_TRY(bs->Pcat.alloc(pb->mesh->ctx, (size_t)bs->Mp * bs->Kp));
+    OSRC_CK(cudaMemsetAsync(bs->Pcat.p, 0, (size_t)bs->Mp * bs->Kp * sizeof(__nv_bfloat16), st));
+    const size_t plane = (size_t)n2 * R;
+    const unsigned gp = (unsigned)((plane + 255) / 256);
+    for (int k0 = 0; k0 < n2; k0 += R) {
+        identity_block_kernel<<<gp, 256, 0, st>>>(n2, R, k0, bs->t2.p);
+        OSRC_TRY(batched_precond(pb, bs->t2.p, bs->t1.p, (float)tol, maxit, st));
+        pack_p_block_kernel<<<gp, 256, 0, st>>>(n2, R, k0, bs->Kp, bs->t1.p, bs->Pcat.p);
+        pb->launches += 2;
+    }
+    OSRC_CK(cudaGetLastError());
+    OSRC_CK(cudaStreamSynchronize(st));
+    bs->pdense = true;
+    return OSRC_OK;
+}
+
+extern "C" int osrc_dense_precond_drop(osrc_problem *pb) {
+    if (!pb) return OSRC_INVALID_ARG;
+    if (pb->batched) {
+        OSRC_CK(cudaSetDevice(pb->mesh->ctx->device));
+        pb->batched->pdense = false;
+        pb->batched->Pcat.release();
+    }
+    return OSRC_OK;
 }
