@@ -208,8 +208,9 @@ typedef struct osrc_batched_info {
 
 /* Solves A x_r = b_r for up to 128 right-hand sides at once on a problem
  * created with OSRC_FP64_DENSE (A = the assembled permuted PMCHWT system of
- * Sec. 2.7): FP64 outer iterative refinement x += d, r = b - A x (FP64
- * residual on the FP64 matrix), each correction solved approximately for all
+ * Sec. 2.7): outer iterative refinement x += d (x in FP64), r = b - A x
+ * (residual of the FP64 matrix in float-float arithmetic, about 48
+ * significant bits), each correction solved approximately for all
  * right-hand sides together by GMRES on P M^-1 A d = P M^-1 r (OSRC and mass
  * preconditioning of Sec. 2.4-2.7, inner Krylov solves in FP32) whose
  * operator applies the far-field part of A in BF16 on the tensor cores (FP32
@@ -240,7 +241,7 @@ int osrc_dense_batched_apply(osrc_problem *pb, const void *x, void *y, int nrhs,
  * applies the preconditioner as one tensor-core GEMM per inner iteration
  * instead of 2 N_p + 2 shifted Krylov solves.  The rounding of this matrix
  * changes the inner iteration count, not the solution: the inner GMRES
- * still solves A d = r, and the FP64 residual decides convergence.
+ * still solves A d = r, and the outer residual decides convergence.
  * Synchronises the stream.  osrc_dense_precond_drop frees the matrix and
  * returns to the iterative preconditioner. */
 int osrc_dense_precond_build(osrc_problem *pb, double tol, int maxit, void *stream);

@@ -6,10 +6,12 @@
 //   - packing / unpacking of blocks of right-hand sides around the GEMM,
 //     fused with the near-field CSR product;
 //   - an FP32 multi-right-hand-side CG / COCG for the fused OSRC
-//     preconditioner (Sec. 2.6, 2.7), one CTA per (system, group of 8
-//     right-hand sides);
+//     preconditioner (Sec. 2.6, 2.7), one thread-block cluster per (system,
+//     group of 8 right-hand sides), and the explicit BF16 preconditioner
+//     matrix built from it;
 //   - FP32 batched Arnoldi helpers (projections, updates, norms, Givens);
-//   - the FP64 residual product R = B - A X of the outer refinement.
+//   - the residual product R = B - A X of the outer refinement in
+//     float-float arithmetic (about 48 significant bits) on the FP32 pipes.
 // Block vectors of the inner solver are stored [row][rhs] (right-hand sides
 // fastest, complex FP32), so every row access is coalesced across the block.
 #include <cooperative_groups.h>
@@ -109,7 +111,7 @@ __global__ void zero_pad_b_kernel(int n2, int NN, int Kp, __nv_bfloat16 *__restr
 // y[m][r] = (C[m][r], C[m][R + r]) + (near CSR product)[m][r]
 __global__ void unpack_near_kernel(int nv, int R, int ldc, const float *__restrict__ C,
                                    const int *__restrict__ ptr, const int *__restrict__ col,
-                                   const double2 *__restrict__ val, const float2 *__restrict__ X,
+                                   const float2 *__restrict__ val, const float2 *__restrict__ X,
                                    float2 *__restrict__ Y) {
     const int i = blockIdx.x;  // vertex
     const int r = threadIdx.x;
@@ -118,10 +120,9 @@ __global__ void unpack_near_kernel(int nv, int R, int ldc, const float *__restri
     float2 y2 = f2c(C[(size_t)(nv + i) * ldc + r], C[(size_t)(nv + i) * ldc + R + r]);
     for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
         const int j = col[e];
-        const double2 *b = val + 4 * (size_t)e;
+        const float2 *b = val + 4 * (size_t)e;
         const float2 xa = X[(size_t)j * R + r], xb = X[(size_t)(nv + j) * R + r];
-        const float2 b0 = f2c((float)b[0].x, (float)b[0].y), b1 = f2c((float)b[1].x, (float)b[1].y);
-        const float2 b2 = f2c((float)b[2].x, (float)b[2].y), b3 = f2c((float)b[3].x, (float)b[3].y);
+        const float2 b0 = b[0], b1 = b[1], b2 = b[2], b3 = b[3];
         y1 = fadd(y1, fadd(fmulc(b0, xa), fmulc(b1, xb)));
         y2 = fadd(y2, fadd(fmulc(b2, xa), fmulc(b3, xb)));
     }
@@ -406,6 +407,11 @@ __global__ void osrc_combine32_kernel(int nv, int R, OsrcComb32 c, const float2 
 }
 
 // M and S values in FP32
+__global__ void d2f2_kernel(size_t n, const double2 *__restrict__ a, float2 *__restrict__ b) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
 __global__ void d2f_kernel(int n, const double *__restrict__ a, float *__restrict__ b) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (float)a[i];
@@ -585,47 +591,99 @@ __global__ void binit_kernel(int R, const float *__restrict__ nrm, float *__rest
 }
 
 // ---------------------------------------------------------------------------
-// FP64 residual of the outer refinement: R[r][m] = B[r][m] - sum_k A[m][k] X[r][k]
-// (A [n2][n2] row-major complex FP64; B, X, R [nrhs][n2]).  Tile 32 rows x
-// 16 right-hand sides per block, K staged through shared memory.
+// Residual of the outer refinement in float-float arithmetic on the FP32
+// pipes (this part's FP64 rate is 1/64 of its FP32 rate).  Every real value
+// is an unevaluated sum hi + lo of two floats (Dekker 1971): products by
+// TwoProd with an FMA (exact), accumulation by Knuth's TwoSum (exact) with
+// the rounding errors and cross terms carried in the low word, about 48
+// significant bits.  A is split once (AFF: {Re hi, Im hi, Re lo, Im lo} per
+// entry); X is split as it is staged.  R[r][m] = B[r][m] - sum_k A[m][k] X[r][k].
 // ---------------------------------------------------------------------------
-constexpr int RS_TM = 32, RS_TR = 16, RS_TK = 32;
-
-__global__ void __launch_bounds__(RS_TM * RS_TR / 2)
-resid64_kernel(int n2, int nrhs, const double2 *__restrict__ A, const double2 *__restrict__ X,
-               const double2 *__restrict__ B, double2 *__restrict__ Rr) {
-    __shared__ double2 sa[RS_TM][RS_TK + 1];
-    __shared__ double2 sx[RS_TR][RS_TK + 1];
-    const int m0 = blockIdx.x * RS_TM, r0 = blockIdx.y * RS_TR;
-    const int tid = threadIdx.x;           // 256 threads: each 2 outputs
-    const int tm = tid % RS_TM, tr = (tid / RS_TM) * 2;
-    double2 acc0 = cd(0, 0), acc1 = cd(0, 0);
-    for (int k0 = 0; k0 < n2; k0 += RS_TK) {
-        for (int e = tid; e < RS_TM * RS_TK; e += blockDim.x) {
-            const int mm = e / RS_TK, kk = e % RS_TK;
-            sa[mm][kk] = (m0 + mm < n2 && k0 + kk < n2) ? A[(size_t)(m0 + mm) * n2 + k0 + kk] : cd(0, 0);
-        }
-        for (int e = tid; e < RS_TR * RS_TK; e += blockDim.x) {
-            const int rr = e / RS_TK, kk = e % RS_TK;
-            sx[rr][kk] = (r0 + rr < nrhs && k0 + kk < n2) ? X[(size_t)(r0 + rr) * n2 + k0 + kk] : cd(0, 0);
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int kk = 0; kk < RS_TK; ++kk) {
-            const double2 a = sa[tm][kk];
-            acc0 = cadd(acc0, cmul(a, sx[tr][kk]));
-            acc1 = cadd(acc1, cmul(a, sx[tr + 1][kk]));
-        }
-        __syncthreads();
-    }
-    const int m = m0 + tm;
-    if (m < n2) {
-        if (r0 + tr < nrhs)
-            Rr[(size_t)(r0 + tr) * n2 + m] = csub(B[(size_t)(r0 + tr) * n2 + m], acc0);
-        if (r0 + tr + 1 < nrhs)
-            Rr[(size_t)(r0 + tr + 1) * n2 + m] = csub(B[(size_t)(r0 + tr + 1) * n2 + m], acc1);
-    }
+__global__ void split_ff_kernel(size_t n, const double2 *__restrict__ A, float4 *__restrict__ out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 a = A[i];
+    const float rh = (float)a.x, ih = (float)a.y;
+    out[i] = make_float4(rh, ih, (float)(a.x - (double)rh), (float)(a.y - (double)ih));
 }
+
+// (sh, sl) += (ah + al) (xh + xl)
+__device__ __forceinline__ void ff_mac(float &sh, float &sl, float ah, float al, float xh, float xl) {
+    const float ph = __fmul_rn(ah, xh);
+    float pl = fmaf(ah, xh, -ph);
+    pl = fmaf(ah, xl, pl);
+    pl = fmaf(al, xh, pl);
+    const float t = __fadd_rn(sh, ph);
+    const float bb = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(ph, bb));
+    sl = __fadd_rn(sl, __fadd_rn(err, pl));
+    sh = t;
+}
+
+constexpr int FF_TM = 64, FF_TR = 16, FF_TK = 16;
+
+__global__ void __launch_bounds__(256)
+resid_ff_kernel(int n2, int nrhs, const float4 *__restrict__ AFF, const double2 *__restrict__ X,
+                const double2 *__restrict__ B, double2 *__restrict__ Rr) {
+    __shared__ float4 sa[FF_TM][FF_TK + 1];
+    __shared__ float4 sx[FF_TR][FF_TK + 1];
+    const int m0 = blockIdx.x * FF_TM, r0 = blockIdx.y * FF_TR;
+    const int tid = threadIdx.x;
+    const int tm = tid % 32, tr = (tid / 32) * 2;  // rows tm, tm + 32; right-hand sides tr, tr + 1
+    float acc[2][2][4];                             // [row][rhs][re h, re l, im h, im l]
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+    for (int k0 = 0; k0 < n2; k0 += FF_TK) {
+        for (int e = tid; e < FF_TM * FF_TK; e += 256) {
+            const int mm = e / FF_TK, kk = e % FF_TK;
+            sa[mm][kk] = (m0 + mm < n2 && k0 + kk < n2) ? AFF[(size_t)(m0 + mm) * n2 + k0 + kk]
+                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int e = tid; e < FF_TR * FF_TK; e += 256) {
+            const int rr = e / FF_TK, kk = e % FF_TK;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r0 + rr < nrhs && k0 + kk < n2) {
+                const double2 x = X[(size_t)(r0 + rr) * n2 + k0 + kk];
+                const float rh = (float)x.x, ih = (float)x.y;
+                v = make_float4(rh, ih, (float)(x.x - (double)rh), (float)(x.y - (double)ih));
+            }
+            sx[rr][kk] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < FF_TK; ++kk) {
+            const float4 a[2] = {sa[tm][kk], sa[tm + 32][kk]};
+            const float4 x[2] = {sx[tr][kk], sx[tr + 1][kk]};
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    float *c = acc[i][j];
+                    ff_mac(c[0], c[1], a[i].x, a[i].z, x[j].x, x[j].z);    // + Re a Re x
+                    ff_mac(c[0], c[1], -a[i].y, -a[i].w, x[j].y, x[j].w);  // - Im a Im x
+                    ff_mac(c[2], c[3], a[i].x, a[i].z, x[j].y, x[j].w);    // + Re a Im x
+                    ff_mac(c[2], c[3], a[i].y, a[i].w, x[j].x, x[j].z);    // + Im a Re x
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int m = m0 + tm + 32 * i, r = r0 + tr + j;
+            if (m < n2 && r < nrhs) {
+                const float *c = acc[i][j];
+                const double2 ax = cd((double)c[0] + (double)c[1], (double)c[2] + (double)c[3]);
+                Rr[(size_t)r * n2 + m] = csub(B[(size_t)r * n2 + m], ax);
+            }
+        }
+}
+
 
 // per right-hand side: nrm[r] = |v[r][:]| (FP64, [nrhs][n2])
 __global__ void norm_rows64_kernel(int n2, const double2 *__restrict__ v, double *__restrict__ nrm) {
@@ -698,6 +756,8 @@ struct BatchedState {
     bool pdense = false;
     DBuf<float> C;
     DBuf<float> M32, S32;
+    DBuf<float4> AFF;           // float-float split of the FP64 system matrix (residuals)
+    DBuf<float2> nr32;          // touching-pair CSR values in FP32
     DBuf<int> err;
     DBuf<float2> kwork, kW;     // multi-RHS Krylov work and solutions
     DBuf<float2> kdinv;         // Jacobi inverse diagonals [system][row]
@@ -728,6 +788,12 @@ int batched_prepare(osrc_problem *pb, int R, int maxit_inner, cudaStream_t st) {
         pack_a_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n2, bs->Mp, bs->Kp, pb->d_dense.p, bs->Acat.p);
         far_part_near_kernel<<<(nv + 127) / 128, 128, 0, st>>>(nv, bs->Kp, pb->d_nr_ptr.p, pb->d_nr_col.p,
                                                                pb->d_nr_val.p, pb->d_dense.p, bs->Acat.p);
+        const size_t nn = (size_t)n2 * n2;
+        OSRC_TRY(bs->AFF.alloc(ctx, nn));
+        split_ff_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(nn, pb->d_dense.p, bs->AFF.p);
+        const size_t nq = 4 * (size_t)pb->near_nnz;
+        OSRC_TRY(bs->nr32.alloc(ctx, nq));
+        d2f2_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(nq, pb->d_nr_val.p, bs->nr32.p);
         OSRC_TRY(bs->M32.alloc(ctx, pb->ms_nnz));
         OSRC_TRY(bs->S32.alloc(ctx, pb->ms_nnz));
         d2f_kernel<<<(pb->ms_nnz + 255) / 256, 256, 0, st>>>(pb->ms_nnz, pb->d_M.p, bs->M32.p);
@@ -781,8 +847,8 @@ static int batched_matvec(osrc_problem *pb, const float2 *x, float2 *y, cudaStre
     dim3 gb((n2 + 31) / 32, (R + 31) / 32);
     pack_b_kernel<<<gb, dim3(32, 8), 0, st>>>(n2, R, bs->Kp, x, bs->Bcat.p);
     OSRC_TRY(umma_gemm_bf16(bs->Acat.p, bs->Mp, bs->Kp, bs->Bcat.p, 2 * R, bs->C.p, 2 * R, bs->err.p, st));
-    unpack_near_kernel<<<nv, R, 0, st>>>(nv, R, 2 * R, bs->C.p, pb->d_nr_ptr.p, pb->d_nr_col.p, pb->d_nr_val.p,
-                                         x, y);
+    unpack_near_kernel<<<nv, R, 0, st>>>(nv, R, 2 * R, bs->C.p, pb->d_nr_ptr.p, pb->d_nr_col.p, bs->nr32.p, x,
+                                         y);
     pb->launches += 3;
     OSRC_CK(cudaGetLastError());
     return OSRC_OK;
@@ -979,8 +1045,8 @@ extern "C" int osrc_dense_batched_solve(osrc_problem *pb, const void *b, void *x
         OSRC_TRY(batched_inner_gmres(pb, bs->w.p, (float)inner_tol, inner_maxit, (float)ptol, 500, &its, st));
         info.inner_iterations += its;
         add_block32_kernel<<<gx, 256, 0, st>>>(n2, nrhs, R, bs->t1.p, bs->scl.p, X);
-        dim3 grid((n2 + RS_TM - 1) / RS_TM, (nrhs + RS_TR - 1) / RS_TR);
-        resid64_kernel<<<grid, RS_TM * RS_TR / 2, 0, st>>>(n2, nrhs, pb->d_dense.p, X, B, bs->R64.p);
+        dim3 grid((n2 + FF_TM - 1) / FF_TM, (nrhs + FF_TR - 1) / FF_TR);
+        resid_ff_kernel<<<grid, 256, 0, st>>>(n2, nrhs, bs->AFF.p, X, B, bs->R64.p);
         pb->launches += 3;
         OSRC_CK(cudaGetLastError());
     }

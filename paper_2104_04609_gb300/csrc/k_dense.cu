@@ -1,8 +1,8 @@
 // k_dense.cu -- dense mixed-precision building blocks of the assembled path:
 // a BF16 tensor-core GEMM on the 5th-generation tensor cores (tcgen05 MMA
-// with the accumulator in tensor memory, operands staged by TMA), the
-// packing of the complex system into BF16 real planes, and an FP64 residual
-// product for the outer iterative refinement.
+// with the accumulator in tensor memory, operands staged by TMA), used by
+// the batched dense solve for the far-field product and the explicit
+// preconditioner matrix.
 //
 // GEMM: C[M x N] = A[M x K] * B[N x K]^T, A and B BF16 and K-major (row-major
 // with K contiguous), C FP32.  One CTA of 128 threads computes a 128 x N tile
