@@ -173,3 +173,23 @@ def test_sauter_schwab_edge_pair_brute_force():
         ref += wi * 2.0 * area_t * potential(x)
     ref /= 4.0 * math.pi
     assert abs(V.sum().real - ref) / abs(ref) < 1e-5
+
+
+def test_quad6_matches_published_table():
+    """The oracle's 6-point rule equals Dunavant's published degree-4 table
+    (tests/golden/dunavant_p4_n6.txt) up to the order of the points."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "dunavant_p4_n6.txt")
+    rows = [list(map(float, l.split())) for l in open(path) if l.strip() and not l.startswith("#")]
+    ref = []
+    for w, a, b, c in rows:
+        for perm in {(a, b, c), (b, c, a), (c, a, b)}:
+            ref.append((w, perm))
+    b, w = O.quad6()
+    assert len(ref) == 6 == len(w)
+    used = set()
+    for k in range(6):
+        hit = [i for i, (rw, rp) in enumerate(ref)
+               if i not in used and abs(rw - w[k]) < 1e-14 and np.allclose(rp, b[k], atol=1e-14)]
+        assert hit, (k, b[k], w[k])
+        used.add(hit[0])
