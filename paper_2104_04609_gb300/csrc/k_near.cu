@@ -237,92 +237,131 @@ __global__ void near_csr_kernel(int nnz, const int *__restrict__ cptr, const int
 }
 
 // ---------------------------------------------------------------------------
-// dense FP64 system (assembled path): far pairs with the 6-point rule, one
-// thread per (test triangle, source triangle), accumulated with FP64 atomics.
+// dense FP64 system (assembled path): far pairs with the 6-point rule,
+// accumulated with FP64 atomics.  Each unordered pair {t, s} (t < s, sharing
+// no vertex) is evaluated once and written in both orientations: V and D are
+// symmetric in (x, y), and with the point roles swapped the K integrand of
+// the reversed pair is minus the T integrand of the forward pair (and vice
+// versa), so the reversed 3x3 blocks are V^T, -T^T, -K^T, D^T.
+// Six threads per pair, one per test point p: each sums over the source
+// points q into the three source vertices (Z_p[b] = sum_q phi_b(y_q) w_pq f_pq),
+// the six partial rows meet in shared memory, and block entry (a, b) is
+// sum_p phi_a(x_p) Z_p[b] (the 6x6 -> 3x3 contraction done in two steps).
 // ---------------------------------------------------------------------------
 constexpr double kDa1 = 0.445948490915965, kDw1 = 0.223381589678011;
 constexpr double kDa2 = 0.091576213509771, kDw2 = 0.109951743655322;
+constexpr int DA_PAIRS = 16;  // triangle pairs per block (6 threads each)
 
-__device__ inline void dense_rule(int q, double b[3], double &w) {
+__device__ __forceinline__ double dense_bary(int q, int j) {
     const double a = q < 3 ? kDa1 : kDa2;
-    w = q < 3 ? kDw1 : kDw2;
-    for (int j = 0; j < 3; ++j) b[j] = (j == q % 3) ? 1.0 - 2.0 * a : a;
+    return (j == q % 3) ? 1.0 - 2.0 * a : a;
 }
 
-__global__ void dense_far_kernel(int nv, int nt, const double *__restrict__ verts,
-                                 const int *__restrict__ tris, const double *__restrict__ tgeo,
-                                 NearConst c, double2 *__restrict__ A) {
-    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= (long long)nt * nt) return;
-    const int t = (int)(id / nt), s = (int)(id % nt);
-    int vt[3], vs[3];
-    for (int a = 0; a < 3; ++a) {
-        vt[a] = tris[3 * t + a];
-        vs[a] = tris[3 * s + a];
+__device__ __forceinline__ double dense_w(int q) { return q < 3 ? kDw1 : kDw2; }
+
+// Folded triangular enumeration of the pairs t < s: folded row f holds row f
+// (s in (f, nt)) followed by row nt - 1 - f, nt - 1 entries in all.
+__global__ void __launch_bounds__(DA_PAIRS * 6)
+dense_far_kernel(int nv, int nt, const double *__restrict__ verts, const int *__restrict__ tris,
+                 const double *__restrict__ tgeo, NearConst c, double2 *__restrict__ A) {
+    __shared__ double2 zs[DA_PAIRS][6][13];  // per pair, per test point: V[3], K[3], T[3], D[3], dc
+    const int lp = threadIdx.x / 6, p = threadIdx.x % 6;
+    const int f = blockIdx.y;
+    const long long j = (long long)blockIdx.x * DA_PAIRS + lp;
+    int t = -1, s = -1;
+    if (j < nt - 1 - f) {
+        t = f;
+        s = f + 1 + (int)j;
+    } else if (nt - 1 - f != f && j < nt - 1) {
+        t = nt - 1 - f;
+        s = t + 1 + (int)(j - (nt - 1 - f));
     }
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-            if (vt[a] == vs[b]) return;  // touching: near field
-    const double *gt = tgeo + 16 * (size_t)t, *gs = tgeo + 16 * (size_t)s;
-    double X[6][3], Y[6][3], bx[6][3], wq[6];
-    for (int q = 0; q < 6; ++q) {
-        dense_rule(q, bx[q], wq[q]);
-        for (int j = 0; j < 3; ++j) {
-            X[q][j] = bx[q][0] * verts[3 * vt[0] + j] + bx[q][1] * verts[3 * vt[1] + j] +
-                      bx[q][2] * verts[3 * vt[2] + j];
-            Y[q][j] = bx[q][0] * verts[3 * vs[0] + j] + bx[q][1] * verts[3 * vs[1] + j] +
-                      bx[q][2] * verts[3 * vs[2] + j];
+    bool live = t >= 0 && s < nt;
+    int vt[3] = {0, 0, 0}, vs[3] = {0, 0, 0};
+    if (live) {
+        for (int a = 0; a < 3; ++a) {
+            vt[a] = tris[3 * t + a];
+            vs[a] = tris[3 * s + a];
         }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                if (vt[a] == vs[b]) live = false;  // touching: near field
     }
-    const double nn = gt[1] * gs[1] + gt[2] * gs[2] + gt[3] * gs[3];
-    const double scale = gt[0] * gs[0];
-    double2 V[9], K[9], T[9], D[9];
-    for (int i = 0; i < 9; ++i) V[i] = K[i] = T[i] = D[i] = cd(0, 0);
-    double2 dc = cd(0, 0);
-    const double dk0 = c.k0 * c.k0, dk1 = c.k1 * c.k1 / c.rho;
-    for (int p = 0; p < 6; ++p)
+    const double *gt = tgeo + 16 * (size_t)(live ? t : 0), *gs = tgeo + 16 * (size_t)(live ? s : 0);
+    double2 Z[13];
+    for (int i = 0; i < 13; ++i) Z[i] = cd(0, 0);
+    if (live) {
+        double X[3], Vs[3][3];
+        for (int k = 0; k < 3; ++k)
+            for (int b = 0; b < 3; ++b) Vs[b][k] = verts[3 * vs[b] + k];
+        for (int k = 0; k < 3; ++k)
+            X[k] = dense_bary(p, 0) * verts[3 * vt[0] + k] + dense_bary(p, 1) * verts[3 * vt[1] + k] +
+                   dense_bary(p, 2) * verts[3 * vt[2] + k];
+        const double scale = gt[0] * gs[0] * dense_w(p);
+        const double dk0 = c.k0 * c.k0, dk1 = c.k1 * c.k1 / c.rho;
         for (int q = 0; q < 6; ++q) {
-            const double w = wq[p] * wq[q] * scale;
-            const double d0 = X[p][0] - Y[q][0], d1 = X[p][1] - Y[q][1], d2 = X[p][2] - Y[q][2];
+            const double b0 = dense_bary(q, 0), b1 = dense_bary(q, 1), b2 = dense_bary(q, 2);
+            const double d0 = X[0] - (b0 * Vs[0][0] + b1 * Vs[1][0] + b2 * Vs[2][0]);
+            const double d1 = X[1] - (b0 * Vs[0][1] + b1 * Vs[1][1] + b2 * Vs[2][1]);
+            const double d2 = X[2] - (b0 * Vs[0][2] + b1 * Vs[1][2] + b2 * Vs[2][2]);
+            const double w = dense_w(q) * scale;
             const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2), ri = 1.0 / r;
             double s0, c0, s1, c1;
             sincos(c.k0 * r, &s0, &c0);
             sincos(c.k1 * r, &s1, &c1);
             const double kr0 = c.k0 * r, kr1 = c.k1 * r;
-            const double f = kInv4Pi * ri, f3 = f * ri * ri;
-            const double2 g0 = cd(c0 * f, s0 * f), g1 = cd(c1 * f, s1 * f);
-            const double2 hs = cd((-c0 - kr0 * s0 - c1 - kr1 * s1) * f3,
-                                  (kr0 * c0 - s0 + kr1 * c1 - s1) * f3);
+            const double fw = kInv4Pi * ri * w, f3 = fw * ri * ri;
+            const double2 g0 = cd(c0 * fw, s0 * fw), g1 = cd(c1 * fw, s1 * fw);
+            const double2 hs = cd((-c0 - kr0 * s0 - c1 - kr1 * s1) * f3, (kr0 * c0 - s0 + kr1 * c1 - s1) * f3);
             const double2 gp = cadd(g0, cscale(g1, c.rho));
-            const double2 gd = cadd(g0, cscale(g1, 1.0 / c.rho));
             const double2 gk = cadd(cscale(g0, dk0), cscale(g1, dk1));
-            const double dny = -(d0 * gs[1] + d1 * gs[2] + d2 * gs[3]);
-            const double dnx = d0 * gt[1] + d1 * gt[2] + d2 * gt[3];
-            dc = cadd(dc, cscale(gd, w));
-            for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b) {
-                    const double ll = bx[p][a] * bx[q][b] * w;
-                    const int i = 3 * a + b;
-                    V[i] = cadd(V[i], cscale(gp, ll));
-                    K[i] = csub(K[i], cscale(hs, dny * ll));
-                    T[i] = cadd(T[i], cscale(hs, dnx * ll));
-                    D[i] = cadd(D[i], cscale(gk, ll));
-                }
+            const double2 hk = cscale(hs, d0 * gs[1] + d1 * gs[2] + d2 * gs[3]);  // -hs (y - x).n_y
+            const double2 ht = cscale(hs, d0 * gt[1] + d1 * gt[2] + d2 * gt[3]);  //  hs (x - y).n_x
+            Z[12] = cadd(Z[12], cadd(g0, cscale(g1, 1.0 / c.rho)));
+            const double bq[3] = {b0, b1, b2};
+            for (int b = 0; b < 3; ++b) {
+                Z[b] = cadd(Z[b], cscale(gp, bq[b]));
+                Z[3 + b] = cadd(Z[3 + b], cscale(hk, bq[b]));
+                Z[6 + b] = cadd(Z[6 + b], cscale(ht, bq[b]));
+                Z[9 + b] = cadd(Z[9 + b], cscale(gk, bq[b]));
+            }
         }
+    }
+    for (int i = 0; i < 13; ++i) zs[lp][p][i] = Z[i];
+    __syncthreads();
+    if (!live) return;
+    const double nn = gt[1] * gs[1] + gt[2] * gs[2] + gt[3] * gs[3];
+    double2 dc = cd(0, 0);
+    for (int pp = 0; pp < 6; ++pp) dc = cadd(dc, zs[lp][pp][12]);
     const size_t n2 = 2 * (size_t)nv;
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
-            const int i = 3 * a + b;
-            const double *ca = gt + 4 + 3 * a, *cb = gs + 4 + 3 * b;
-            const double cc = ca[0] * cb[0] + ca[1] * cb[1] + ca[2] * cb[2];
-            const double2 dd = csub(cscale(dc, cc), cscale(D[i], nn));
-            const size_t r1 = vt[a], r2 = nv + vt[a], c1 = vs[b], c2 = nv + vs[b];
-            double *p;
-            p = (double *)&A[r1 * n2 + c1]; atomicAdd(p, V[i].x); atomicAdd(p + 1, V[i].y);
-            p = (double *)&A[r1 * n2 + c2]; atomicAdd(p, K[i].x); atomicAdd(p + 1, K[i].y);
-            p = (double *)&A[r2 * n2 + c1]; atomicAdd(p, T[i].x); atomicAdd(p + 1, T[i].y);
-            p = (double *)&A[r2 * n2 + c2]; atomicAdd(p, dd.x); atomicAdd(p + 1, dd.y);
+    // thread p writes entries (a, b) = (e / 3, e % 3) for e = p, p + 6 (the 9
+    // entries of the four blocks: 36 values over 6 threads)
+    for (int e = p; e < 9; e += 6) {
+        const int a = e / 3, b = e % 3;
+        double2 v = cd(0, 0), k = cd(0, 0), tt = cd(0, 0), d = cd(0, 0);
+        for (int pp = 0; pp < 6; ++pp) {
+            const double ba = dense_bary(pp, a);
+            v = cadd(v, cscale(zs[lp][pp][b], ba));
+            k = cadd(k, cscale(zs[lp][pp][3 + b], ba));
+            tt = cadd(tt, cscale(zs[lp][pp][6 + b], ba));
+            d = cadd(d, cscale(zs[lp][pp][9 + b], ba));
         }
+        const double *ca = gt + 4 + 3 * a, *cb = gs + 4 + 3 * b;
+        const double cc = ca[0] * cb[0] + ca[1] * cb[1] + ca[2] * cb[2];
+        const double2 dd = csub(cscale(dc, cc), cscale(d, nn));
+        const size_t ra = vt[a], rb = vs[b];
+        double *q;
+        // forward (test t, source s)
+        q = (double *)&A[ra * n2 + rb];                     atomicAdd(q, v.x);   atomicAdd(q + 1, v.y);
+        q = (double *)&A[ra * n2 + nv + rb];                atomicAdd(q, k.x);   atomicAdd(q + 1, k.y);
+        q = (double *)&A[(nv + ra) * n2 + rb];              atomicAdd(q, tt.x);  atomicAdd(q + 1, tt.y);
+        q = (double *)&A[(nv + ra) * n2 + nv + rb];         atomicAdd(q, dd.x);  atomicAdd(q + 1, dd.y);
+        // reversed (test s, source t)
+        q = (double *)&A[rb * n2 + ra];                     atomicAdd(q, v.x);   atomicAdd(q + 1, v.y);
+        q = (double *)&A[rb * n2 + nv + ra];                atomicAdd(q, -tt.x); atomicAdd(q + 1, -tt.y);
+        q = (double *)&A[(nv + rb) * n2 + ra];              atomicAdd(q, -k.x);  atomicAdd(q + 1, -k.y);
+        q = (double *)&A[(nv + rb) * n2 + nv + ra];         atomicAdd(q, dd.x);  atomicAdd(q + 1, dd.y);
+    }
 }
 
 // Adds the near CSR blocks into the dense matrix (one thread per vertex row).
@@ -442,9 +481,15 @@ int dense_assemble(osrc_problem *pb, cudaStream_t st) {
     OSRC_TRY(pb->d_dense.alloc(m->ctx, n2 * n2));
     OSRC_CK(cudaMemsetAsync(pb->d_dense.p, 0, n2 * n2 * sizeof(double2), st));
     NearConst c{pb->p.k_ext, pb->p.k_int, pb->p.rho_ratio, pb->p.n_ss};
-    const long long npair = (long long)nt * nt;
-    dense_far_kernel<<<(unsigned)((npair + 127) / 128), 128, 0, st>>>(
-        nv, nt, m->d_verts.p, m->d_tris.p, pb->d_tgeo.p, c, pb->d_dense.p);
+    const int folded = (nt + 1) / 2;
+    if (folded > 65535) {
+        osrc_set_error("dense assembly: too many triangles for the dense path");
+        return OSRC_UNSUPPORTED;
+    }
+    dim3 grid((unsigned)((nt - 1 + DA_PAIRS - 1) / DA_PAIRS), (unsigned)folded);
+    if (nt > 1)
+        dense_far_kernel<<<grid, DA_PAIRS * 6, 0, st>>>(nv, nt, m->d_verts.p, m->d_tris.p, pb->d_tgeo.p, c,
+                                                         pb->d_dense.p);
     pb->launches++;
     dense_add_near_kernel<<<(nv + 127) / 128, 128, 0, st>>>(nv, pb->d_nr_ptr.p, pb->d_nr_col.p,
                                                             pb->d_nr_val.p, pb->d_dense.p);
