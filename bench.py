@@ -64,6 +64,11 @@ def parse():
                     help="right-hand sides of the batched dense leg (ellipsoid8000; 0: skip)")
     ap.add_argument("--dense-matfree-rhs", type=int, default=1,
                     help="right-hand sides of the same workload solved matrix-free for comparison")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the far-field apply on the 80000-vertex bumpy ellipsoid")
+    ap.add_argument("--large-sweep", type=int, default=0, metavar="NV",
+                    help="instead of the benchmark: GMRES iterations vs ka on the bumpy "
+                         "ellipsoid with NV vertices, k_ext in {15, 30, 45, 60}")
     return ap.parse_args()
 
 
@@ -310,8 +315,12 @@ def run_ours(args, D):
     if peaks is not None:
         out["measured_peaks_file"] = True
     S.close()
+    if D.rank == 0:
+        out["small_dense"] = run_small_dense(D.local)
     if args.dense_rhs > 0 and D.rank == 0:
         out["dense_batched"] = run_dense(args.dense_rhs, args.dense_matfree_rhs, D.local)
+    if not args.no_large and D.rank == 0:
+        out["large"] = run_large(D.local)
     if args.serve_requests > 0 and D.rank == 0:
         out["serving"] = run_serving(args.serve_requests, D.local)
     return out, (infos[-1]["iterations"] if infos else REF_ITERATIONS)
@@ -368,6 +377,15 @@ def run_dense(nrhs, n_matfree, device):
         torch.cuda.synchronize()
         t_solve = e0.elapsed_time(e1) / 1000.0
         launches = S.launches()
+        # one FP64 GEMV of the assembled system (single right-hand side)
+        xv = b[0:1].contiguous()
+        S.apply(xv)
+        e0.record(stream)
+        for _ in range(5):
+            S.apply(xv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        gemv_ms = e0.elapsed_time(e1) / 5
         # tensor-core GEMM of the inner products at this shape, timed alone
         Mp, Kp, N = (S.nv * 2 + 127) // 128 * 128, (4 * S.nv + 63) // 64 * 64, 2 * ((nrhs + 7) // 8 * 8)
         gA = torch.randn(Mp, Kp, device=dev).to(torch.bfloat16)
@@ -401,6 +419,7 @@ def run_dense(nrhs, n_matfree, device):
             "solves_per_s": nrhs / t_solve,
             "solves_per_s_incl_setup": nrhs / (t_solve + t_assembly + t_pbuild),
             "solve_s": t_solve, "assembly_s": t_assembly, "precond_build_s": t_pbuild,
+            "fp64_gemv_ms": gemv_ms,
             "refinements": info["refinements"], "inner_iterations": info["inner_iterations"],
             "residual": info["residual"], "gpu_launches": int(launches),
             "gemm": {"bound": "tensor", "M": Mp, "N": N, "K": Kp, "avg_ms": gemm_ms,
@@ -433,6 +452,93 @@ def run_dense(nrhs, n_matfree, device):
     finally:
         S.close()
     return out
+
+
+# --------------------------------------------------------------------------
+# small dense leg (level-3 icosphere, FP64 dense, GMRES to 1e-8) and the large
+# far-field apply (80000-vertex bumpy ellipsoid, k 60 / 144)
+# --------------------------------------------------------------------------
+SMALL_WORKLOAD = "sphere642"
+LARGE_WORKLOAD = "bumpy80000"
+# FP32 flops per far point pair of the large-ka (centred) variant: the 89 of the
+# plain kernel plus 23 for the phase from the centroid distance (3 ADD for the
+# offsets, r_c-relative r^2 - r_c^2 in 2 x (1 MUL + 2 FMA) + 1 FMA, 1 ADD and
+# 1 MUL for r - r_c, 2 x (FMA + MUL) for both phases)
+FLOPS_PER_PAIR_CENTRED = 112
+
+
+def run_small_dense(device):
+    """Unit sphere, level-3 icosphere (642 vertices), k 2 / 3, rho 1.5, plane
+    wave +z: FP64 dense assembly and OSRC GMRES to 1e-8 (set-up included)."""
+    import torch
+
+    from paper_2104_04609_gb300 import binding as B
+    from paper_2104_04609_gb300.inputs import workload
+
+    W = workload(SMALL_WORKLOAD)
+    times = []
+    for _ in range(2):  # the first pass warms up the library
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S = B.Solver(W["verts"], W["tris"], W["k_ext"], W["k_int"], W["rho_ratio"], device=device,
+                     precision=B.OSRC_FP64_DENSE)
+        b = S.rhs_planewave(W["dirs"][:1])
+        x, info = S.solve(b, tol=1e-8, maxit=500)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        S.close()
+    return {"workload": f"{SMALL_WORKLOAD}: level-3 icosphere, 642 vertices, k 2 / 3, rho 1.5, "
+                        "plane wave +z", "tol": 1e-8, "solve_incl_setup_s": times[-1],
+            "iterations": info.iterations, "true_residual": info.true_residual}
+
+
+def run_large(device):
+    """Bumpy ellipsoid (2, 1, 1) + 32 bumps, 80000 vertices / 159996 triangles,
+    k 60 / 144, rho 1.9, point source at (3, 0, 0): one weak-form apply of the
+    permuted PMCHWT operator (large-ka far kernel + near field), timed."""
+    import torch
+
+    from paper_2104_04609_gb300 import binding as B
+    from paper_2104_04609_gb300.inputs import workload
+
+    W = workload(LARGE_WORKLOAD)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S = B.Solver(W["verts"], W["tris"], W["k_ext"], W["k_int"], W["rho_ratio"], device=device)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    try:
+        x = S.rhs_pointsource(W["src"])
+        S.apply(x)
+        B.osrc_profile_enable(S.pb, True)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        e0.record(stream)
+        for _ in range(reps):
+            S.apply(x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        apply_s = e0.elapsed_time(e1) / 1000.0 / reps
+        far_n, far_ms = B.osrc_far_kernel_stats(S.pb)
+        B.osrc_profile_enable(S.pb, False)
+        pairs = B.osrc_far_pairs(S.pb)
+        far_avg = far_ms / max(far_n, 1)
+        achieved = FLOPS_PER_PAIR_CENTRED * pairs / (far_avg * 1e-3) / 1e12
+        props = torch.cuda.get_device_properties(torch.device("cuda", device))
+        peak = props.multi_processor_count * 128 * 2 * 2070.0 * 1e6 / 1e12
+        return {
+            "workload": f"{LARGE_WORKLOAD}: bumpy ellipsoid (2, 1, 1), {S.nv} vertices, k "
+                        f"{W['k_ext']:g} / {W['k_int']:g}, rho {W['rho_ratio']:g}, point source "
+                        "(3, 0, 0)",
+            "setup_s": t_setup, "apply_s": apply_s, "rows_per_s": 2 * S.nv / apply_s,
+            "far_kernel": {"variant": "centred (float-float centroid phase)", "avg_ms": far_avg,
+                           "pairs": pairs, "flops_per_pair": FLOPS_PER_PAIR_CENTRED,
+                           "achieved_tflops": achieved, "peak_tflops": peak,
+                           "frac": achieved / peak},
+        }
+    finally:
+        S.close()
 
 
 # --------------------------------------------------------------------------
@@ -586,6 +692,63 @@ def cpu_baseline(iterations, seconds):
                       f"iterations)"}
 
 
+def cpu_other_configs(out, seconds=4.0):
+    """The oracle on the other workloads beside the GPU numbers of this run:
+    the full small dense solve, sampled rows of the assembled ellipsoid system
+    (assembly + one GEMV, extrapolated to all rows), sampled rows of the large
+    operator (rows/s)."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2104_04609_gb300.inputs import workload
+
+    res = {}
+    if "small_dense" in out:
+        W = workload(SMALL_WORKLOAD)
+        t0 = time.perf_counter()
+        P = O.Problem(W["verts"], W["tris"], W["k_ext"], W["k_int"], W["rho_ratio"], nss=4)
+        b = P.rhs()
+        P.solve_gmres(b, tol=1e-8)
+        t = time.perf_counter() - t0
+        g = out["small_dense"]["solve_incl_setup_s"]
+        res["sphere642_solve"] = {"oracle_s": t, "gpu_s": g, "speedup": t / g,
+                                  "sample": "full FP64 dense assembly + OSRC GMRES to 1e-8"}
+
+    def rows_rate(name, nss=4):
+        W = workload(name)
+        nv = W["verts"].shape[0]
+        rng = np.random.default_rng(5)
+        x = rng.standard_normal(2 * nv) + 1j * rng.standard_normal(2 * nv)
+        n = 2
+        while True:
+            rows = rng.choice(nv, n, replace=False)
+            t0 = time.perf_counter()
+            R1, R2 = O.pmchwt_rows(W["verts"], W["tris"], W["k_ext"], W["k_int"], W["rho_ratio"],
+                                   rows, nss=nss)
+            _ = R1 @ x, R2 @ x
+            t = time.perf_counter() - t0
+            if t > seconds / 4 or n >= nv:
+                return nv, n, t
+            n = min(nv, n * 4)
+
+    if "dense_batched" in out:
+        nv, n, t = rows_rate(DENSE_WORKLOAD)
+        t_all = t / n * nv
+        d = out["dense_batched"]
+        g = d["assembly_s"] + d["fp64_gemv_ms"] * 1e-3
+        res["ellipsoid8000_assembly_gemv"] = {
+            "oracle_s": t_all, "gpu_s": g, "speedup": t_all / g,
+            "sample": f"{n} of {nv} vertex rows (both block rows) assembled and applied in "
+                      f"{t:.1f} s, extrapolated to all rows"}
+    if "large" in out:
+        nv, n, t = rows_rate(LARGE_WORKLOAD)
+        r = 2 * n / t
+        gr = out["large"]["rows_per_s"]
+        res["bumpy80000_rows"] = {"oracle_rows_per_s": r, "gpu_rows_per_s": gr, "speedup": gr / r,
+                                  "sample": f"{n} of {nv} vertex rows (both block rows) in {t:.1f} s"}
+    return res
+
+
 def run_reference(args, D):
     if D.world > 1 and D.rank != 0:
         return None
@@ -620,8 +783,41 @@ def run_reference(args, D):
     return out
 
 
+def large_sweep(nv, device=0, maxit=600):
+    """GMRES iteration count vs frequency on the bumpy ellipsoid (point source
+    at (3, 0, 0), k_int = 2.4 k_ext, rho 1.9, tol 1e-5): one JSON line per k."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2104_04609_gb300 import binding as B
+    from paper_2104_04609_gb300.inputs import bumpy_ellipsoid
+
+    v, t = bumpy_ellipsoid(nv)
+    for k0 in (15.0, 30.0, 45.0, 60.0):
+        S = B.Solver(v, t, k0, k0 * 3600.0 / 1500.0, 1.9, device=device)
+        try:
+            b = S.rhs_pointsource([[3.0, 0.0, 0.0]])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x, info = S.solve(b, tol=TOL, maxit=maxit, raise_on_nonconvergence=False)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            print(json.dumps({"mesh": f"bumpy ellipsoid (2, 1, 1), {S.nv} vertices",
+                              "k_ext": k0, "k_int": k0 * 2.4, "ka": 2.0 * k0,
+                              "iterations": info.iterations, "converged": bool(info.converged),
+                              "precond_residual": info.precond_residual,
+                              "true_residual": info.true_residual, "solve_s": dt}), flush=True)
+        finally:
+            S.close()
+
+
 def main():
     args = parse()
+    if args.large_sweep > 0:
+        large_sweep(args.large_sweep)
+        return
     if args.impl == "reference":
         D = Dist(want_cuda=False)
         out = run_reference(args, D)
@@ -634,6 +830,7 @@ def main():
     if D.rank == 0:
         if D.world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(iters, args.cpu_seconds)
+            out["cpu_baseline"]["other_workloads"] = cpu_other_configs(out)
         print(json.dumps(out), flush=True)
     D.close()
 
