@@ -461,10 +461,10 @@ def run_dense(nrhs, n_matfree, device):
 SMALL_WORKLOAD = "sphere642"
 LARGE_WORKLOAD = "bumpy80000"
 # FP32 flops per far point pair of the large-ka (centred) variant: the 89 of the
-# plain kernel plus 23 for the phase from the centroid distance (3 ADD for the
-# offsets, r_c-relative r^2 - r_c^2 in 2 x (1 MUL + 2 FMA) + 1 FMA, 1 ADD and
-# 1 MUL for r - r_c, 2 x (FMA + MUL) for both phases)
-FLOPS_PER_PAIR_CENTRED = 112
+# plain kernel plus 21 for the phase from the centroid distance (3 ADD for the
+# offsets, r^2 - r_c^2 in 2 x (1 MUL + 2 FMA) + 1 FMA, 1 ADD and 1 MUL for
+# r - r_c, one FMA per wavenumber for the phase)
+FLOPS_PER_PAIR_CENTRED = 110
 
 
 def run_small_dense(device):

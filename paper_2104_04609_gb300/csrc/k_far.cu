@@ -174,7 +174,7 @@ __device__ __forceinline__ f2 dup2(float a) { return make_float2(a, a); }
 
 // Constants as (value, value) pairs for the packed instructions.
 struct FarConst2 {
-    f2 k0, k1, nk0, nk1, k0r, k1r, rho, irho, dk0, dk1;
+    f2 k0, k1, nk0, nk1, rho, irho, dk0, dk1;
 };
 
 // Accumulators of the two test points of a thread, packed (point a, point b):
@@ -217,6 +217,14 @@ __device__ __forceinline__ float ff_phase_rev(float rh, float rl, float kh, floa
     return (p - n) + pe;
 }
 
+// 1/x to about one ulp (PTX rcp.approx), used where the result scales a
+// small quantity
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ CenterPair center_pair(const float4 &cth, const float4 &ctl,
                                                   const float4 &csh, const float4 &csl,
                                                   float k0h, float k0l, float k1h, float k1l) {
@@ -234,9 +242,11 @@ __device__ __forceinline__ CenterPair center_pair(const float4 &cth, const float
         sh = s;
         sl += t + e;
     }
-    // square root with one Newton correction
-    const float rs = sqrtf(sh);
-    const float corr = (fmaf(-rs, rs, sh) + sl) * (0.5f / rs);
+    // square root with one Newton correction (the correction only needs a
+    // few significant bits of 1/(2 sqrt(sh)), so approximate rsqrt suffices)
+    const float y = rsqrtf(sh);
+    const float rs = sh * y;
+    const float corr = (fmaf(-rs, rs, sh) + sl) * (0.5f * y);
     const float rh = rs + corr;
     const float rl = corr - (rh - rs);
     CenterPair c;
@@ -244,8 +254,9 @@ __device__ __forceinline__ CenterPair center_pair(const float4 &cth, const float
     c.Dy = dup2(dh[1]);
     c.Dz = dup2(dh[2]);
     c.rc = dup2(rh);
-    c.b0 = dup2(ff_phase_rev(rh, rl, k0h, k0l));
-    c.b1 = dup2(ff_phase_rev(rh, rl, k1h, k1l));
+    // reduced centroid phases in radians (in [-pi, pi])
+    c.b0 = dup2(6.28318530717958647692f * ff_phase_rev(rh, rl, k0h, k0l));
+    c.b1 = dup2(6.28318530717958647692f * ff_phase_rev(rh, rl, k1h, k1l));
     return c;
 }
 
@@ -299,9 +310,9 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
         dd = fma2(ddz, cp.Dz, dd);
         num = fma2(dd, dup2(2.f), num);  // r^2 - r_c^2
         const f2 den = add2(r, cp.rc);
-        const f2 dlt = mul2(num, make_float2(__frcp_rn(den.x), __frcp_rn(den.y)));  // r - r_c
-        const f2 ph0 = mul2(fma2(c.k0r, dlt, cp.b0), dup2(6.28318530717958647692f));
-        const f2 ph1 = mul2(fma2(c.k1r, dlt, cp.b1), dup2(6.28318530717958647692f));
+        const f2 dlt = mul2(num, make_float2(rcp_approx(den.x), rcp_approx(den.y)));  // r - r_c
+        const f2 ph0 = fma2(c.k0, dlt, cp.b0);
+        const f2 ph1 = fma2(c.k1, dlt, cp.b1);
         __sincosf(ph0.x, &s0.x, &c0.x);
         __sincosf(ph0.y, &s0.y, &c0.y);
         __sincosf(ph1.x, &s1.x, &c1.x);
@@ -353,7 +364,7 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
 // CENTRED: pt holds offsets from the test-triangle centroid and cen the
 // float-float centroids (see far_pair2).
 template <bool CENTRED>
-__global__ void __launch_bounds__(FAR_THREADS)
+__global__ void __launch_bounds__(FAR_THREADS, 4)
 far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
            const float4 *__restrict__ tn, const int4 *__restrict__ tv,
            const float4 *__restrict__ sP, const float2 *__restrict__ sP5,
@@ -596,8 +607,6 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
         c.k1 = d2(k1);
         c.nk0 = d2(-k0);
         c.nk1 = d2(-k1);
-        c.k0r = d2(k0 * inv2pi);
-        c.k1r = d2(k1 * inv2pi);
         c.rho = d2(rho);
         c.irho = d2(1.0 / rho);
         c.dk0 = d2(k0 * k0);
