@@ -19,6 +19,10 @@ Functions and the passages they follow:
   osrc_apply()        strong-form OSRC DtN / NtD maps (Sec. 2.6, 2.7)
   gmres()             GMRES without restart, x0 = 0, preconditioned residual
                       (Sec. 3.1)
+  potentials()        single- and double-layer potentials off the surface
+                      (Sec. 2.2, representation formulas)
+  field()             total field outside / inside from a PMCHWT solution
+                      (Sec. 2.2, with the transmission conditions of Sec. 2.1)
 
 Readings where the paper is silent or ambiguous (each is listed in the design doc):
 quadrature orders (6-point rule for separated pairs, Sauter-Schwab with n
@@ -39,7 +43,7 @@ __all__ = [
     "lib", "quad6", "gauss_legendre", "ss_rule", "pair_matrices", "assemble",
     "assemble_rows", "pmchwt_matrix", "pmchwt_rows", "mass_stiffness", "rhs",
     "pade", "pade_eval", "ntd_partial_fractions", "damped_wavenumber",
-    "mean_edge_length", "osrc_apply", "strong_apply", "gmres", "Problem",
+    "mean_edge_length", "osrc_apply", "strong_apply", "gmres", "Problem", "potentials", "field",
 ]
 
 _LIB = None
@@ -68,6 +72,8 @@ def lib():
         L.orc_mass_stiffness_coo.argtypes = [dp, ip, ctypes.c_int, ip, ip, dp, dp]
         L.orc_rhs.argtypes = [dp, ctypes.c_int, ip, ctypes.c_int, ctypes.c_double,
                               ctypes.c_double, ctypes.c_int, dp, dp]
+        L.orc_potentials.argtypes = [dp, ctypes.c_int, ip, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_double, dp, dp, dp, ctypes.c_int, dp, dp]
         L.orc_num_threads.restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -204,6 +210,57 @@ def rhs(verts, tris, k_ext, kind="planewave", src=(0.0, 0.0, 1.0)):
     lib().orc_rhs(_dp(v), v.shape[0], _ip(t), t.shape[0], float(np.real(k_ext)),
                   float(np.imag(k_ext)), 0 if kind == "planewave" else 1, _dp(s), _dp(out))
     return out.view(np.complex128).copy()
+
+
+def potentials(verts, tris, k, psi, phi, pts):
+    """(SLP psi, DLP phi) at points off the surface, 6-point rule per triangle:
+    SLP psi(x) = int G(x, y) psi(y) dy, DLP phi(x) = int dG/dn_y phi(y) dy with
+    G = exp(ikr)/(4 pi r) (Sec. 2.2); psi, phi P1 coefficients (n_v,)."""
+    v, t = _mesh(verts, tris)
+    P = np.ascontiguousarray(np.atleast_2d(pts), dtype=np.float64)
+    ps = np.ascontiguousarray(psi, dtype=np.complex128)
+    ph = np.ascontiguousarray(phi, dtype=np.complex128)
+    n = P.shape[0]
+    S = np.zeros(2 * n)
+    D = np.zeros(2 * n)
+    lib().orc_potentials(_dp(v), v.shape[0], _ip(t), t.shape[0], float(np.real(k)),
+                         float(np.imag(k)), _dp(ps.view(np.float64)), _dp(ph.view(np.float64)),
+                         _dp(P), n, _dp(S), _dp(D))
+    return S.view(np.complex128).copy(), D.view(np.complex128).copy()
+
+
+def inside(verts, tris, pts):
+    """Region of each point: the Laplace double layer of the constant 1,
+    -DLP_0 1 = 1 inside the closed surface and 0 outside (Gauss)."""
+    nv = np.asarray(verts).shape[0]
+    _, D = potentials(verts, tris, 0.0, np.zeros(nv), np.ones(nv), pts)
+    return -D.real > 0.5
+
+
+def field(verts, tris, k_ext, k_int, rho_ratio, x, pts, inc="planewave", src=(0.0, 0.0, 1.0)):
+    """Total pressure at points from a solution x = [psi; phi] of the permuted
+    PMCHWT system (psi = exterior normal derivative, phi = trace of the total
+    field, outward normal).  Outside (Sec. 2.2, exterior representation of the
+    scattered field plus the incident field):
+        u = u_inc + DLP_0 phi - SLP_0 psi;
+    inside (interior representation with the interior traces phi and
+    rho psi from the transmission conditions, rho = rho_int / rho_ext):
+        u = rho SLP_1 psi - DLP_1 phi.
+    Returns (u, inside mask)."""
+    P = np.atleast_2d(np.asarray(pts, dtype=np.float64))
+    nv = np.asarray(verts).shape[0]
+    psi, phi = np.asarray(x)[:nv], np.asarray(x)[nv:]
+    ins = inside(verts, tris, P)
+    S0, D0 = potentials(verts, tris, k_ext, psi, phi, P)
+    S1, D1 = potentials(verts, tris, k_int, psi, phi, P)
+    s = np.asarray(src, dtype=np.float64)
+    if inc == "planewave":
+        uinc = np.exp(1j * k_ext * (P @ s))
+    else:
+        R = np.linalg.norm(P - s[None, :], axis=1)
+        uinc = np.exp(1j * k_ext * R) / (4.0 * math.pi * R)
+    u = np.where(ins, rho_ratio * S1 - D1, uinc + D0 - S0)
+    return u, ins
 
 
 # --------------------------------------------------------------------------

@@ -565,6 +565,58 @@ int orc_rhs(const double *verts, int nv, const int *tris, int nt,
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Single- and double-layer potentials at points off the surface (Sec. 2.2,  */
+/* the representation formulas): for densities psi, phi given as P1          */
+/* coefficients (n_v complex each),                                          */
+/*   slp(x) = int G(x, y) psi(y) dy,                                          */
+/*   dlp(x) = int dG(x, y)/dn_y phi(y) dy,                                    */
+/*   dG/dn_y = exp(ikr) (ikr - 1) (y - x).n_y / (4 pi r^3),                   */
+/* each integral by the 6-point rule on every triangle.  out_slp, out_dlp:   */
+/* npts complex interleaved.                                                  */
+/* ------------------------------------------------------------------------ */
+int orc_potentials(const double *verts, int nv, const int *tris, int nt,
+                   double kre, double kim, const double *psi, const double *phi,
+                   const double *pts, int npts, double *out_slp, double *out_dlp)
+{
+    (void)nv;
+    double bary[18], w6[6];
+    orc_quad6(bary, w6);
+    cplx k = kre + I * kim;
+    const cplx *ps = (const cplx *)psi, *ph = (const cplx *)phi;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int i = 0; i < npts; ++i) {
+        const double *x = pts + 3 * i;
+        cplx S = 0.0, D = 0.0;
+        for (int t = 0; t < nt; ++t) {
+            tri_geom g;
+            make_geom(verts, &tris[3 * t], &g);
+            const int *v = &tris[3 * t];
+            for (int q = 0; q < 6; ++q) {
+                double y[3];
+                for (int j = 0; j < 3; ++j)
+                    y[j] = bary[3 * q] * g.P[0][j] + bary[3 * q + 1] * g.P[1][j] +
+                           bary[3 * q + 2] * g.P[2][j];
+                cplx psq = bary[3 * q] * ps[v[0]] + bary[3 * q + 1] * ps[v[1]] +
+                           bary[3 * q + 2] * ps[v[2]];
+                cplx phq = bary[3 * q] * ph[v[0]] + bary[3 * q + 1] * ph[v[1]] +
+                           bary[3 * q + 2] * ph[v[2]];
+                double d[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]};  /* y - x */
+                double r = sqrt(dot3(d, d));
+                cplx e = cexp(I * k * r);
+                double w = w6[q] * g.area;
+                S += w * e / (4.0 * ORC_PI * r) * psq;
+                D += w * e * (I * k * r - 1.0) / (4.0 * ORC_PI * r * r * r) * dot3(d, g.n) * phq;
+            }
+        }
+        out_slp[2 * i] = creal(S);
+        out_slp[2 * i + 1] = cimag(S);
+        out_dlp[2 * i] = creal(D);
+        out_dlp[2 * i + 1] = cimag(D);
+    }
+    return 0;
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

@@ -30,6 +30,32 @@ def mie_traces(k0, k1, rho, a, cth):
     return phi, psi
 
 
+def mie_field(k0, k1, rho, a, pts):
+    """Total field of the penetrable sphere of radius a for the plane wave
+    exp(i k0 z): outside sum (2l+1) i^l [j_l(k0 r) + a_l h_l(k0 r)] P_l(cos th),
+    inside sum (2l+1) i^l c_l j_l(k1 r) P_l(cos th) with c_l from continuity of
+    the pressure at r = a."""
+    P = np.atleast_2d(pts)
+    r = np.linalg.norm(P, axis=1)
+    cth = np.where(r > 0, P[:, 2] / np.where(r > 0, r, 1.0), 1.0)
+    L = int(max(k0, k1) * max(a, r.max()) + 4 * (k1 * a) ** (1 / 3) + 20)
+    u = np.zeros(P.shape[0], dtype=complex)
+    out = r > a
+    for l in range(L):
+        j0, j0p = spherical_jn(l, k0 * a), spherical_jn(l, k0 * a, True)
+        h0 = j0 + 1j * spherical_yn(l, k0 * a)
+        h0p = j0p + 1j * spherical_yn(l, k0 * a, True)
+        j1, j1p = spherical_jn(l, k1 * a), spherical_jn(l, k1 * a, True)
+        al = ((k1 / rho) * j1p * j0 - k0 * j1 * j0p) / (k0 * j1 * h0p - (k1 / rho) * j1p * h0)
+        cl = (j0 + al * h0) / j1
+        Pl = eval_legendre(l, cth)
+        ro = np.where(out, r, a)
+        ext = spherical_jn(l, k0 * ro) + al * (spherical_jn(l, k0 * ro) + 1j * spherical_yn(l, k0 * ro))
+        inn = cl * spherical_jn(l, k1 * np.where(out, a, r))
+        u += (2 * l + 1) * 1j ** l * np.where(out, ext, inn) * Pl
+    return u
+
+
 def _merr(M, a, e):
     d = a - e
     return math.sqrt(abs(np.vdot(d, M @ d)) / abs(np.vdot(e, M @ e)))
