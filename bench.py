@@ -270,6 +270,7 @@ def run_ours(args, D):
     sol_diff = float(np.linalg.norm(hxn.ravel() - x.cpu().numpy().ravel()) /
                      np.linalg.norm(x.cpu().numpy().ravel()))
 
+    field = run_field(S, x, W, B) if D.rank == 0 else None
     far_pairs = B.osrc_far_pairs(S.pb)
     far_avg_ms = far_ms / max(far_n, 1)
     achieved = FLOPS_PER_PAIR * far_pairs / (far_avg_ms * 1e-3) / 1e12
@@ -311,6 +312,8 @@ def run_ours(args, D):
                           f"{sm_max:.0f} MHz (derived; no FP32 entry in MEASURED_PEAKS.json)",
         },
     }
+    if field is not None:
+        out["field"] = field
     peaks = measured_peaks()
     if peaks is not None:
         out["measured_peaks_file"] = True
@@ -452,6 +455,66 @@ def run_dense(nrhs, n_matfree, device):
     finally:
         S.close()
     return out
+
+
+# --------------------------------------------------------------------------
+# field on the paper's grid (Sec. 3.2): 101 x 101 points on a square of 6 radii
+# in the plane z = 0, error of the amplitude against the Mie series
+# --------------------------------------------------------------------------
+def mie_total_field(k0, k1, rho, a, pts):
+    """Total field of the penetrable sphere (radius a, rho = rho_int/rho_ext)
+    for the plane wave exp(i k0 z), by the Mie series."""
+    import numpy as np
+    from scipy.special import eval_legendre, spherical_jn, spherical_yn
+
+    r = np.linalg.norm(pts, axis=1)
+    cth = np.where(r > 0, pts[:, 2] / np.where(r > 0, r, 1.0), 1.0)
+    L = int(max(k0, k1) * max(a, r.max()) + 4 * (k1 * a) ** (1 / 3) + 20)
+    out = r > a
+    ro, ri = np.where(out, r, a), np.where(out, a, r)
+    u = np.zeros(len(r), dtype=complex)
+    for l in range(L):
+        j0, j0p = spherical_jn(l, k0 * a), spherical_jn(l, k0 * a, True)
+        h0 = j0 + 1j * spherical_yn(l, k0 * a)
+        h0p = j0p + 1j * spherical_yn(l, k0 * a, True)
+        j1, j1p = spherical_jn(l, k1 * a), spherical_jn(l, k1 * a, True)
+        al = ((k1 / rho) * j1p * j0 - k0 * j1 * j0p) / (k0 * j1 * h0p - (k1 / rho) * j1p * h0)
+        ext = spherical_jn(l, k0 * ro) + al * (spherical_jn(l, k0 * ro) + 1j * spherical_yn(l, k0 * ro))
+        inn = (j0 + al * h0) / j1 * spherical_jn(l, k1 * ri)
+        u += (2 * l + 1) * 1j ** l * np.where(out, ext, inn) * eval_legendre(l, cth)
+    return u
+
+
+def run_field(S, x, W, B):
+    import numpy as np
+    import torch
+
+    g = np.linspace(-3.0, 3.0, 101)
+    X, Y = np.meshgrid(g, g)
+    pts = np.stack([X.ravel(), Y.ravel(), np.zeros(X.size)], axis=1)
+    tp = torch.tensor(pts, device=x.device)
+    S.field(x, tp, B.OSRC_INC_PLANEWAVE, [0.0, 0.0, 1.0])
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    u, reg = S.field(x, tp, B.OSRC_INC_PLANEWAVE, [0.0, 0.0, 1.0])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    u = u.cpu().numpy()
+    ue = mie_total_field(W["k_ext"], W["k_int"], W["rho_ratio"], 1.0, pts)
+    r = np.linalg.norm(pts, axis=1)
+    h = B.osrc_mesh_mean_edge(S.mesh)
+    away = np.abs(r - 1.0) > 2.0 * h
+
+    def err(m):
+        return float(np.linalg.norm(np.abs(u[m]) - np.abs(ue[m])) / np.linalg.norm(np.abs(ue[m])))
+
+    return {"grid": "101 x 101 points, [-3, 3]^2 in the plane z = 0 (the paper's 3 cm square "
+                    "around a 5 mm sphere)", "eval_ms": e0.elapsed_time(e1),
+            "amplitude_l2_error_vs_mie": err(np.ones(len(r), dtype=bool)),
+            "amplitude_l2_error_vs_mie_away_from_surface": err(away),
+            "surface_band": "points within two mean edge lengths of the surface left out",
+            "points_inside": int(reg.sum().item())}
 
 
 # --------------------------------------------------------------------------

@@ -257,6 +257,28 @@ int osrc_dense_precond_drop(osrc_problem *pb);
 int osrc_dense_batched_apply_ex(osrc_problem *pb, const void *x, void *y, int nrhs, int what,
                                 double ptol, int pmaxit, int *pits_max, void *stream);
 
+/* ---- field evaluation --------------------------------------------------------------- */
+enum { OSRC_INC_NONE = 0, OSRC_INC_PLANEWAVE = 1, OSRC_INC_POINTSOURCE = 2 };
+
+/* Total pressure at npts points off the surface from one solution
+ * x = [psi; phi] of the permuted PMCHWT system (Sec. 2.2, representation
+ * formulas; the paper's accuracy measure evaluates it on a grid, Sec. 3.2):
+ * outside u = u_inc + DLP_0 phi - SLP_0 psi, inside u = rho SLP_1 psi -
+ * DLP_1 phi (rho = rho_int / rho_ext, interior Neumann trace rho psi), every
+ * potential by the 6-point rule per triangle with the P1 densities.  A
+ * point is inside when the Laplace double layer of 1 exceeds 1/2 (Gauss's
+ * solid angle; unreliable within about one mesh size of the surface, where
+ * the rule itself loses accuracy).  inc_kind / inc_param: the incident
+ * field added outside (OSRC_INC_PLANEWAVE: unit direction d, u_inc =
+ * exp(i k_ext d.x); OSRC_INC_POINTSOURCE: position x0, u_inc =
+ * exp(i k_ext |x - x0|) / (4 pi |x - x0|); OSRC_INC_NONE: scattered field
+ * only; inc_param host, 3 doubles).  x: device, 2nv complex FP64; pts:
+ * device, npts x 3 FP64; u: device, npts complex FP64 (out); region:
+ * device int[npts] (out, 1 inside / 0 outside) or NULL.  FP64 throughout
+ * (region test in FP32).  Asynchronous on stream. */
+int osrc_field_eval(osrc_problem *pb, const void *x, const double *pts, int npts, int inc_kind,
+                    const double *inc_param, void *u, int *region, void *stream);
+
 /* ---- serving loop ------------------------------------------------------------------ */
 /* A continuous-batching server for solve requests of uneven mesh size and
  * frequency (the serving pattern that the solver is deployed in).  A worker

@@ -34,6 +34,9 @@ OSRC_PART_FAR = 1
 OSRC_PART_NEAR = 2
 OSRC_PART_ALL = 3
 OSRC_HOST_BUFFERS = 1
+OSRC_INC_NONE = 0
+OSRC_INC_PLANEWAVE = 1
+OSRC_INC_POINTSOURCE = 2
 
 
 class OsrcError(RuntimeError):
@@ -152,6 +155,8 @@ SIGNATURES = {
                                                    ctypes.POINTER(ctypes.c_int), _VP]),
     "osrc_dense_precond_build": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int, _VP]),
     "osrc_dense_precond_drop": (ctypes.c_int, [_VP]),
+    "osrc_field_eval": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _DP, _VP, _VP,
+                                       _VP]),
     "osrc_launch_count": (ctypes.c_longlong, [_VP]),
     "osrc_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "osrc_far_kernel_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong),
@@ -465,6 +470,23 @@ def osrc_dense_precond_drop(pb):
     _check(lib().osrc_dense_precond_drop(pb), "osrc_dense_precond_drop")
 
 
+def osrc_field_eval(pb, x, pts, u, inc_kind=OSRC_INC_NONE, inc_param=None, region=None,
+                    stream=None):
+    """Total field at points off the surface; x (2nv,) complex128, pts (n, 3)
+    float64, u (n,) complex128, region (n,) int32 or None: CUDA tensors."""
+    import torch
+
+    assert pts.dtype == torch.float64 and pts.is_cuda and pts.is_contiguous()
+    n = int(pts.shape[0])
+    par = None
+    if inc_kind != OSRC_INC_NONE:
+        par = np.ascontiguousarray(inc_param, dtype=np.float64).reshape(3)
+    _check(lib().osrc_field_eval(pb, _dev(x), ctypes.c_void_p(pts.data_ptr()), n, int(inc_kind),
+                                 None if par is None else par.ctypes.data_as(_DP), _dev(u),
+                                 None if region is None else ctypes.c_void_p(region.data_ptr()),
+                                 _stream(stream)), "osrc_field_eval")
+
+
 def osrc_launch_count(pb):
     return lib().osrc_launch_count(pb)
 
@@ -562,6 +584,18 @@ class Solver:
         info = osrc_gmres_solve(self.pb, b, x, b.shape[0] if b.ndim == 2 else 1, tol, maxit,
                                 raise_on_nonconvergence=raise_on_nonconvergence)
         return x, info
+
+    def field(self, x, pts, inc_kind=OSRC_INC_NONE, inc_param=None):
+        """(u, region) at points pts ((n, 3) float64 CUDA tensor) for one
+        solution x ((2nv,) or (1, 2nv) complex128 CUDA tensor)."""
+        import torch
+
+        x = x.reshape(-1).contiguous()
+        pts = pts.contiguous()
+        u = torch.empty(pts.shape[0], dtype=torch.complex128, device=pts.device)
+        reg = torch.empty(pts.shape[0], dtype=torch.int32, device=pts.device)
+        osrc_field_eval(self.pb, x, pts, u, inc_kind, inc_param, reg)
+        return u, reg
 
     def launches(self):
         return osrc_launch_count(self.pb)

@@ -387,15 +387,26 @@ __global__ void dense_gemv_kernel(int n, const double2 *__restrict__ A, const do
     const int lane = threadIdx.x & 31;
     if (row >= n) return;
     const double2 *a = A + (size_t)row * n;
-    double sr = 0.0, si = 0.0;
-    for (int j = lane; j < n; j += 32) {
-        const double2 u = a[j], v = x[j];
-        sr += u.x * v.x - u.y * v.y;
-        si += u.x * v.y + u.y * v.x;
+    // four independent loads in flight per lane (the row is streamed once)
+    double sr[4] = {0.0, 0.0, 0.0, 0.0}, si[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j0 = lane; j0 < n; j0 += 128) {
+        double2 u[4], v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int j = j0 + 32 * k;
+            u[k] = j < n ? __ldcs(a + j) : cd(0, 0);
+            v[k] = j < n ? x[j] : cd(0, 0);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            sr[k] += u[k].x * v[k].x - u[k].y * v[k].y;
+            si[k] += u[k].x * v[k].y + u[k].y * v[k].x;
+        }
     }
-    sr = warp_sum(sr);
-    si = warp_sum(si);
-    if (lane == 0) y[row] = cd(sr, si);
+    double tr = (sr[0] + sr[1]) + (sr[2] + sr[3]), ti = (si[0] + si[1]) + (si[2] + si[3]);
+    tr = warp_sum(tr);
+    ti = warp_sum(ti);
+    if (lane == 0) y[row] = cd(tr, ti);
 }
 
 // Gauss-Legendre nodes and weights on [0,1] (Newton on the three-term

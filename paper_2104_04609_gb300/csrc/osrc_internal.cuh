@@ -167,6 +167,9 @@ struct osrc_problem {
     DBuf<double> d_scalars;   // reduction scratch
     DBuf<double2> d_w, d_y, d_x1, d_b1, d_cvec;  // 2nv vectors
     double *h_res = nullptr;  // pinned host block: doubles [0, 16), then ints (inner status)
+    // ---- field evaluation off the surface (k_field.cu) -------------------------
+    DBuf<double4> d_fsrc;     // [6nt][3] rule points, normals, densities
+    DBuf<int> d_freg;         // region scratch when the caller passes none
     // ---- far-kernel event timing -------------------------------------------------
     bool prof_on = false, prof_pending = false;
     cudaEvent_t prof_ev[2] = {nullptr, nullptr};
