@@ -326,6 +326,7 @@ def run_ours(args, D):
         out["large"] = run_large(D.local)
     if args.serve_requests > 0 and D.rank == 0:
         out["serving"] = run_serving(args.serve_requests, D.local)
+        out["serving_batched"] = run_serving(args.serve_requests, D.local, batched=True)
     return out, (infos[-1]["iterations"] if infos else REF_ITERATIONS)
 
 
@@ -634,7 +635,11 @@ def serving_workload(n_req):
     return out
 
 
-def run_serving(n_req, device):
+def run_serving(n_req, device, batched=False):
+    """batched=False: every right-hand side is its own FP32 matrix-free GMRES
+    job.  batched=True: requests with two or more right-hand sides ask for the
+    batched mixed-precision route (OSRC_FP64_DENSE: one block per request,
+    tolerance on the true residual); single right-hand sides stay matrix-free."""
     import numpy as np
 
     from paper_2104_04609_gb300 import binding as B
@@ -650,6 +655,8 @@ def run_serving(n_req, device):
             if delay > 0:
                 time.sleep(delay)
             p = B.osrc_params_default(k_ext=w["k_ext"], k_int=w["k_int"], rho_ratio=w["rho"])
+            if batched and len(w["dirs"]) >= 2:
+                p.precision = B.OSRC_FP64_DENSE
             ids.append(B.osrc_server_submit(sv, w["verts"], w["tris"], p, w["dirs"], tol=TOL,
                                             maxit=1000))
         lat, its, ok = [], 0, 0
@@ -674,7 +681,9 @@ def run_serving(n_req, device):
                        "max": float(lat[-1])},
         "gmres_iterations": its, "max_active": 4, "active_peak": stats["active_peak"],
         "cache_hits": stats["cache_hits"], "cache_misses": stats["cache_misses"],
-        "mem_peak_bytes": stats["mem_peak"],
+        "mem_peak_bytes": stats["mem_peak"], "batched_requests": stats["batched_jobs"],
+        "route": "multi-RHS requests batched (BF16 tensor cores, outer refinement)" if batched
+                 else "one FP32 matrix-free GMRES job per right-hand side",
         "sample": f"first {len(work)} requests of the seeded Poisson stream (50/s, seed 2), "
                   f"vertices capped at {SERVE_MAX_NV}, ka at {SERVE_MAX_KA:g}, right-hand sides "
                   f"at {SERVE_MAX_RHS}; latency = submit to completion of all right-hand sides",

@@ -293,7 +293,19 @@ int osrc_field_eval(osrc_problem *pb, const void *x, const double *pts, int npts
  * unreferenced entries are evicted least-recently-used when memory is
  * needed.  While a server exists its worker is the only user of the context:
  * create no other handles on it.  Requests that cannot fit even alone finish
- * with OSRC_OUT_OF_MEMORY. */
+ * with OSRC_OUT_OF_MEMORY.
+ *
+ * Requests whose params.precision is OSRC_FP64_DENSE are not split: all their
+ * right-hand sides (same mesh, same frequency) are solved together as one
+ * block by the batched mixed-precision solve (see osrc_dense_batched_solve;
+ * tol applies to the true residual, 1e-3 inner tolerance, at most 400 inner
+ * iterations per refinement, blocks of up to 128), on the cached problem,
+ * whose assembled system, BF16 matrices and explicit preconditioner stay
+ * resident for later requests on the same mesh and frequency.  The worker
+ * runs such a block to completion before it advances the other slots.
+ * Results equal a direct osrc_dense_batched_solve of the same block within
+ * the solve's tolerance, not bit for bit: the FP64 assembly accumulates with
+ * atomics, so each assembly differs in the last bits. */
 typedef struct osrc_server osrc_server;
 
 typedef struct osrc_request {
@@ -315,6 +327,7 @@ typedef struct osrc_server_stats {
     long long active_peak;  /* most slots busy at once */
     size_t mem_peak;        /* most device bytes allocated through the context */
     size_t mem_used;        /* device bytes allocated now */
+    long long batched_jobs; /* requests solved as one block of right-hand sides */
 } osrc_server_stats;
 
 /* Starts a server with max_active slots (1..64) on the context. */

@@ -94,6 +94,7 @@ class osrc_server_stats(ctypes.Structure):
         ("cache_hits", ctypes.c_longlong), ("cache_misses", ctypes.c_longlong),
         ("evictions", ctypes.c_longlong), ("active_peak", ctypes.c_longlong),
         ("mem_peak", ctypes.c_size_t), ("mem_used", ctypes.c_size_t),
+        ("batched_jobs", ctypes.c_longlong),
     ]
 
     def as_dict(self):

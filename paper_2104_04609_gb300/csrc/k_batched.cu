@@ -1159,3 +1159,21 @@ extern "C" int osrc_dense_precond_drop(osrc_problem *pb) {
     }
     return OSRC_OK;
 }
+
+// Device bytes the batched solve of a problem with nv vertices adds for R
+// right-hand sides (rounded up to 8) and an inner cap maxit: packed BF16
+// system and preconditioner matrices, the float-float split of the system,
+// the inner basis and block vectors, the FP32 shifted-solve work.
+size_t estimate_batched_bytes(int nv, int n_pade, int nrhs, int maxit) {
+    const size_t R = (size_t)((nrhs + 7) / 8 * 8), n2 = 2 * (size_t)nv;
+    const size_t Mp = (n2 + 127) / 128 * 128, Kp = (2 * n2 + 63) / 64 * 64;
+    const size_t nsys = 2 * (size_t)n_pade + 2;
+    size_t b = 2 * Mp * Kp * 2 + n2 * n2 * 16;                 // Acat, Pcat, AFF
+    b += (size_t)(maxit + 1) * n2 * R * 8;                      // inner basis
+    b += (size_t)(maxit + 1) * (maxit + 1) * R * 8;             // Hessenberg
+    b += (size_t)(maxit + 1) * 64 * R * 8 + 8 * (size_t)(maxit + 1) * R * 8;
+    b += 4 * n2 * R * 8 + Mp * 2 * R * 4 + 2 * R * Kp * 2;     // block vectors, GEMM in/out
+    b += nsys * (4 * (size_t)nv * R + nv) * 8;                  // shifted solves
+    b += (size_t)nrhs * n2 * 16;                                // FP64 residual block
+    return b;
+}

@@ -263,3 +263,4 @@ int problem_clone(osrc_problem *master, osrc_problem **out);
 // for admission by device memory)
 size_t estimate_problem_bytes(int nv, int nt, const osrc_params &p);
 size_t estimate_work_bytes(int nv, int nt, const osrc_params &p, int maxit);
+size_t estimate_batched_bytes(int nv, int n_pade, int nrhs, int maxit);

@@ -13,6 +13,7 @@
 // and parameters: right-hand sides of one request, and requests on the same
 // mesh and frequency, reuse them.  Unreferenced cache entries are evicted in
 // least-recently-used order when memory is needed.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -25,7 +26,17 @@
 
 #include "osrc_internal.cuh"
 
+extern "C" int osrc_dense_batched_solve(osrc_problem *pb, const void *b, void *x, int nrhs, double tol,
+                                        int max_refine, double inner_tol, int inner_maxit, double precond_tol,
+                                        osrc_batched_info *info, void *stream);
+extern "C" int osrc_dense_precond_build(osrc_problem *pb, double tol, int maxit, void *stream);
+
 namespace {
+
+constexpr int BATCH_MAX = 128;        // right-hand sides per batched block
+constexpr int BATCH_INNER_MAXIT = 400;
+constexpr double BATCH_INNER_TOL = 1e-3;
+constexpr int BATCH_MAX_REFINE = 10;
 
 using Clock = std::chrono::steady_clock;
 
@@ -56,6 +67,7 @@ struct CacheEntry {
     osrc_problem *pb = nullptr;
     int refs = 0;
     uint64_t last_use = 0;
+    bool precond_built = false;  // explicit preconditioner matrix of the batched solve
 };
 
 struct Slot {
@@ -113,6 +125,7 @@ struct osrc_server {
 
     void run();
     int admit_one(Slot &slot);
+    int run_batched(Slot &slot, Request *r);
     int acquire_entry(Request *r, CacheEntry **out);
     void release_slot_workspace(Slot &slot);
     bool evict_one();
@@ -191,6 +204,7 @@ int osrc_server::admit_one(Slot &slot) {
         if (pending.empty()) return OSRC_TIMEOUT;  // nothing to do
         r = pending.front();
     }
+    if (r->params.precision == OSRC_FP64_DENSE) return run_batched(slot, r);
     // workspace: reuse the slot's clone if it serves the same problem
     CacheEntry *entry = nullptr;
     if (slot.entry && slot.entry_key == r->key) {
@@ -242,6 +256,90 @@ int osrc_server::admit_one(Slot &slot) {
     }
     stats.jobs_started++;
     if (ctx->used > stats.mem_peak) stats.mem_peak = ctx->used;
+    return OSRC_OK;
+}
+
+// Solves every right-hand side of request r as blocks of up to BATCH_MAX on
+// the cached problem (the batched mixed-precision solve), to completion.
+// Returns OSRC_OUT_OF_MEMORY (request left queued) if the block's memory
+// cannot be found yet; otherwise the request is finished here.
+int osrc_server::run_batched(Slot &slot, Request *r) {
+    release_slot_workspace(slot);  // the block runs on the resident problem, not on a clone
+    CacheEntry *entry = nullptr;
+    int s = acquire_entry(r, &entry);
+    if (s != OSRC_OK) return s;
+    entry->refs++;
+    const int blk = std::min(r->nrhs, BATCH_MAX);
+    const size_t need = estimate_batched_bytes(r->nv, r->params.n_pade, blk, BATCH_INNER_MAXIT) +
+                        (size_t)blk * 2 * r->nv * 32;
+    const size_t have = entry->pb->batched ? 0 : need;  // state of an earlier block is reused
+    while (ctx->budget && ctx->used + have > ctx->budget)
+        if (!evict_one()) {
+            entry->refs--;
+            return OSRC_OUT_OF_MEMORY;
+        }
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        r->next_rhs = r->nrhs;
+        r->inflight++;
+        pending.pop_front();
+    }
+    entry->last_use = ++tick;
+    stats.jobs_started++;
+    stats.batched_jobs++;
+    const int n2 = 2 * r->nv;
+    int status = OSRC_OK;
+    osrc_solve_info agg{};
+    agg.converged = 1;
+    if ((s = slot.d_b.alloc(ctx, (size_t)blk * n2)) || (s = slot.d_x.alloc(ctx, (size_t)blk * n2))) status = s;
+    if (status == OSRC_OK && !entry->precond_built) {
+        status = osrc_dense_precond_build(entry->pb, 1e-3, 500, slot.st);
+        entry->precond_built = status == OSRC_OK;
+    }
+    for (int r0 = 0; status == OSRC_OK && r0 < r->nrhs; r0 += BATCH_MAX) {
+        const int nb = std::min(BATCH_MAX, r->nrhs - r0);
+        for (int i = 0; i < nb && status == OSRC_OK; ++i)
+            status = rhs_build(entry->pb, r->kind, r->src.data() + 3 * (size_t)(r0 + i), slot.d_b.p + (size_t)i * n2,
+                               slot.st);
+        if (status != OSRC_OK) break;
+        osrc_batched_info bi{};
+        const int bs = osrc_dense_batched_solve(entry->pb, slot.d_b.p, slot.d_x.p, nb, r->tol, BATCH_MAX_REFINE,
+                                                BATCH_INNER_TOL, BATCH_INNER_MAXIT, 0.0, &bi, slot.st);
+        if (bs != OSRC_OK && bs != OSRC_NOT_CONVERGED) {
+            status = bs;
+            break;
+        }
+        if (bs == OSRC_NOT_CONVERGED) agg.converged = 0;
+        if (cudaMemcpyAsync(r->x.data() + (size_t)r0 * n2, slot.d_x.p, (size_t)nb * n2 * sizeof(double2),
+                            cudaMemcpyDeviceToHost, slot.st) != cudaSuccess ||
+            cudaStreamSynchronize(slot.st) != cudaSuccess) {
+            status = OSRC_CUDA_ERROR;
+            break;
+        }
+        agg.iterations += bi.inner_iterations;
+        agg.total_iterations += bi.inner_iterations;
+        agg.true_residual = fmax(agg.true_residual, bi.residual);
+    }
+    slot.d_b.release();
+    slot.d_x.release();
+    entry->refs--;
+    if (ctx->used > stats.mem_peak) stats.mem_peak = ctx->used;
+    std::lock_guard<std::mutex> lock(mu);
+    r->info.iterations = agg.iterations;
+    r->info.total_iterations = agg.total_iterations;
+    r->info.true_residual = agg.true_residual;
+    r->info.precond_residual = agg.true_residual;
+    r->info.converged = agg.converged;
+    if (status == OSRC_OK && !agg.converged) status = OSRC_NOT_CONVERGED;
+    r->status = status;
+    r->rhs_done = r->nrhs;
+    r->inflight--;
+    r->finished = true;
+    r->t_done = Clock::now();
+    r->info.ms_total = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    stats.completed++;
+    if (status != OSRC_OK) stats.failed++;
+    cv.notify_all();
     return OSRC_OK;
 }
 

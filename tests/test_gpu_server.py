@@ -98,3 +98,65 @@ def test_server_rejects_what_never_fits(B):
     finally:
         B.osrc_server_destroy(sv)
         B.osrc_destroy(ctx)
+
+
+def test_server_batches_dense_requests(B):
+    """A request with precision OSRC_FP64_DENSE is solved as one block of
+    right-hand sides by the batched mixed-precision solve on the resident
+    problem: the result equals the direct batched solve of the same block,
+    alone and in a mix with matrix-free requests, within the dense path's
+    solution tolerance (1e-8), and matches the oracle's FP64 direct solve."""
+    import oracle as O
+
+    va, ta = fibonacci_hull(150)
+    dirs = np.array([[0.0, 0.0, 1.0], [0.6, 0.0, 0.8], [0.0, -0.8, 0.6]])
+    k = (2.0, 3.0, 1.5)
+
+    def serve(jobs, max_active):
+        ctx = B.osrc_create(0, 0)
+        sv = B.osrc_server_create(ctx, max_active)
+        try:
+            ids = []
+            for v, t, kk, d, prec in jobs:
+                p = _params(B, *kk)
+                p.precision = prec
+                ids.append(B.osrc_server_submit(sv, v, t, p, d, tol=1e-10, maxit=300))
+            out = []
+            for rid, (v, t, kk, d, prec) in zip(ids, jobs):
+                assert B.osrc_server_wait(sv, rid, 300.0) == B.OSRC_OK
+                done, st, lat, info = B.osrc_server_poll(sv, rid)
+                assert done and st == B.OSRC_OK
+                s, x = B.osrc_server_result(sv, rid, len(d), v.shape[0])
+                out.append(x)
+            return out, B.osrc_server_get_stats(sv)
+        finally:
+            B.osrc_server_destroy(sv)
+            B.osrc_destroy(ctx)
+
+    dense_job = (va, ta, k, dirs, B.OSRC_FP64_DENSE)
+    alone, st1 = serve([dense_job], 1)
+    assert st1["batched_jobs"] == 1
+    vb, tb = icosphere(2)
+    mix = [(vb, tb, (3.0, 4.0, 1.2), np.array([[1.0, 0.0, 0.0]]), B.OSRC_FP32_MATFREE), dense_job,
+           (vb, tb, (3.0, 4.0, 1.2), np.array([[0.0, 1.0, 0.0]]), B.OSRC_FP32_MATFREE), dense_job]
+    mixed, st2 = serve(mix, 3)
+    assert st2["batched_jobs"] == 2 and st2["cache_hits"] >= 1
+    xa = alone[0]
+    # each server assembles its own FP64 system (atomic accumulation, so the
+    # last bits differ), and each solution meets the 1e-10 residual: equal to
+    # the dense path's solution tolerance
+    for x in (mixed[1], mixed[3]):
+        assert np.abs(x - xa).max() <= 1e-8 * np.abs(xa).max()
+    S = B.Solver(va, ta, *k, precision=B.OSRC_FP64_DENSE)
+    try:
+        b = S.rhs_planewave(dirs)
+        x = torch.zeros_like(b)
+        B.osrc_dense_precond_build(S.pb, tol=1e-3, maxit=500)  # as the server does
+        B.osrc_dense_batched_solve(S.pb, b, x, tol=1e-10, max_refine=10, inner_tol=1e-3,
+                                   inner_maxit=400)
+        assert np.abs(x.cpu().numpy() - xa).max() <= 1e-8 * np.abs(xa).max()
+        Bm = O.pmchwt_matrix(va, ta, *k, nss=S.params.n_ss)
+        ref = np.linalg.solve(Bm, b.cpu().numpy().T).T
+        assert np.abs(xa - ref).max() <= 1e-8 * np.abs(ref).max()
+    finally:
+        S.close()
