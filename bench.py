@@ -417,7 +417,7 @@ def run_dense(nrhs, n_matfree, device):
             "workload": f"{DENSE_WORKLOAD}: ellipsoid (1, 0.7, 0.5), {S.nv} vertices, k_ext "
                         f"{W['k_ext']:g}, k_int {W['k_int']:g}, rho ratio {W['rho_ratio']:g}, "
                         f"{nrhs} plane waves (seed 1)",
-            "path": "FP64 dense assembly; explicit BF16 P M^-1 matrix; inner GMRES (FP32, CGS2) on "
+            "path": "FP64 dense assembly; explicit BF16 P M^-1 matrix; inner GMRES (FP32, CGS) on "
                     "BF16 tcgen05 far field + exact near field; float-float outer residual",
             "tol": DENSE_TOL, "right_hand_sides": nrhs,
             "solves_per_s": nrhs / t_solve,
