@@ -424,7 +424,7 @@ class Problem:
     vertices at most."""
 
     def __init__(self, verts, tris, k_ext, k_int, rho_ratio, n_pade=4,
-                 theta=math.pi / 3, damping_R=None, osrc_side=1, nss=6):
+                 theta=math.pi / 3, damping_R=None, osrc_side=1, nss=6, precond="osrc"):
         self.verts = np.asarray(verts, dtype=np.float64)
         self.tris = np.asarray(tris, dtype=np.int32)
         self.nv = self.verts.shape[0]
@@ -436,13 +436,23 @@ class Problem:
         self.B = pmchwt_matrix(self.verts, self.tris, k_ext, k_int, rho_ratio, nss)
         self.M, self.S = mass_stiffness(self.verts, self.tris)
         self._solver = _ShiftedSolver(self.M, self.S)
+        self.precond_kind = precond
 
     def rhs(self, kind="planewave", src=(0.0, 0.0, 1.0)):
         return rhs(self.verts, self.tris, self.k_ext, kind, src)
 
     def precond(self, y):
-        """P u = diag(DtN, NtD) u on strong-form coefficient vectors."""
+        """P u on strong-form coefficient vectors: diag(DtN, NtD) u (OSRC,
+        Sec. 2.6); u itself (mass preconditioning only, Sec. 2.4); or the
+        Calderon preconditioner of Sec. 2.5 for one object, C = A_0 + A^_1,
+        which is the PMCHWT operator in the unpermuted ordering [phi; psi]:
+        with the permuted B acting on [psi; phi], P u = M^-1 B [u2; u1]."""
         nv = self.nv
+        if self.precond_kind == "mass":
+            return np.asarray(y).copy()
+        if self.precond_kind == "calderon":
+            y = np.asarray(y)
+            return strong_apply(self.M, self.B @ np.concatenate([y[nv:], y[:nv]]))
         z1, z2 = osrc_apply(self.M, self.S, y[:nv], y[nv:], self.k_osrc,
                             self.k_eps, self.n_pade, self.theta, self._solver)
         return np.concatenate([z1, z2])
