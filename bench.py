@@ -66,6 +66,9 @@ def parse():
                     help="right-hand sides of the same workload solved matrix-free for comparison")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the far-field apply on the 80000-vertex bumpy ellipsoid")
+    ap.add_argument("--precond-sweep", action="store_true",
+                    help="instead of the benchmark: GMRES iterations vs frequency on the "
+                         "10242-vertex sphere for the OSRC, mass-only and Calderon preconditioners")
     ap.add_argument("--large-sweep", type=int, default=0, metavar="NV",
                     help="instead of the benchmark: GMRES iterations vs ka on the bumpy "
                          "ellipsoid with NV vertices, k_ext in {15, 30, 45, 60}")
@@ -885,10 +888,46 @@ def large_sweep(nv, device=0, maxit=600):
             S.close()
 
 
+def precond_sweep(device=0, maxit=800):
+    """Iteration counts of the paper's comparison (Sec. 3.3): unit sphere
+    (level-5 icosphere, 10242 vertices), k_int = 1.3 k_ext, rho 1.5, plane wave,
+    tol 1e-5, for OSRC, mass-only and Calderon preconditioning."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2104_04609_gb300 import binding as B
+    from paper_2104_04609_gb300.inputs import icosphere
+
+    v, t = icosphere(5)
+    kinds = (("osrc", B.OSRC_PRECOND_OSRC), ("mass", B.OSRC_PRECOND_MASS),
+             ("calderon", B.OSRC_PRECOND_CALDERON))
+    for k0 in (5.0, 10.0, 20.0):
+        for name, code in kinds:
+            S = B.Solver(v, t, k0, 1.3 * k0, 1.5, device=device, precond=code)
+            try:
+                b = S.rhs_planewave([[0.0, 0.0, 1.0]])
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                x, info = S.solve(b, tol=TOL, maxit=maxit, raise_on_nonconvergence=False)
+                torch.cuda.synchronize()
+                print(json.dumps({"mesh": "unit sphere, 10242 vertices", "k_ext": k0,
+                                  "k_int": 1.3 * k0, "precond": name,
+                                  "iterations": info.iterations, "converged": bool(info.converged),
+                                  "true_residual": info.true_residual,
+                                  "solve_s": time.perf_counter() - t0}), flush=True)
+            finally:
+                S.close()
+
+
 def main():
     args = parse()
     if args.large_sweep > 0:
         large_sweep(args.large_sweep)
+        return
+    if args.precond_sweep:
+        precond_sweep()
         return
     if args.impl == "reference":
         D = Dist(want_cuda=False)

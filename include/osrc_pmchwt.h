@@ -80,10 +80,23 @@ typedef struct osrc_params {
     int precision;       /* OSRC_FP32_MATFREE or OSRC_FP64_DENSE */
     double inner_tol;    /* relative residual of the inner mass / shifted solves (<= 1e-8) */
     int inner_maxit;     /* iteration cap of the inner solves */
+    int precond;         /* preconditioner P of the GMRES solve: OSRC_PRECOND_* */
 } osrc_params;
 
+/* Preconditioners of the matrix-free and FP64 dense GMRES solves; GMRES runs
+ * on P B x = P b with, for a weak-form vector y,
+ *   OSRC_PRECOND_OSRC:     P y = diag(L_DtN, L_NtD) M^-1 y (Sec. 2.6, 2.7);
+ *   OSRC_PRECOND_MASS:     P y = M^-1 y (mass preconditioning, Sec. 2.4);
+ *   OSRC_PRECOND_CALDERON: P y = M^-1 B Pi M^-1 y, the block Calderon
+ *     preconditioner of Sec. 2.5 for one object (the PMCHWT operator in its
+ *     unpermuted ordering; Pi swaps the two block rows), one more operator
+ *     apply and two mass solves per iteration.
+ * The batched dense solve always uses OSRC. */
+enum { OSRC_PRECOND_OSRC = 0, OSRC_PRECOND_MASS = 1, OSRC_PRECOND_CALDERON = 2 };
+
 /* Fills p with the paper's defaults: n_pade 4, theta pi/3, interior OSRC
- * wavenumber, R = mean edge length, n_ss 4, FP32 matrix-free, inner_tol 1e-10. */
+ * wavenumber, R = mean edge length, n_ss 4, FP32 matrix-free, inner_tol 1e-10,
+ * OSRC preconditioner. */
 void osrc_params_default(osrc_params *p);
 
 /* Result record of osrc_gmres_solve (per right-hand side: the last one). */
@@ -169,7 +182,9 @@ int osrc_mass_solve(osrc_problem *pb, const void *x, void *y, int nrhs, void *st
  * with the rotated-branch Pade coefficients C0, A_j, B_j of sqrt(1+z) and
  * the partial fractions g0, g_j of its product with (1+z)^-1.  The 2 N_Pade + 1
  * complex-symmetric shifted systems are solved together by a batched COCG to
- * params.inner_tol.  x, y: device, nrhs x 2nv complex. */
+ * params.inner_tol.  With params.precond = OSRC_PRECOND_MASS, y = x; with
+ * OSRC_PRECOND_CALDERON, y = M^-1 B Pi x (see OSRC_PRECOND_*).  x, y:
+ * device, nrhs x 2nv complex. */
 int osrc_precond_apply(osrc_problem *pb, const void *x, void *y, int nrhs, void *stream);
 
 /* ---- solve ----------------------------------------------------------------------- */

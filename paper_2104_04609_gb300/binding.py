@@ -34,6 +34,9 @@ OSRC_PART_FAR = 1
 OSRC_PART_NEAR = 2
 OSRC_PART_ALL = 3
 OSRC_HOST_BUFFERS = 1
+OSRC_PRECOND_OSRC = 0
+OSRC_PRECOND_MASS = 1
+OSRC_PRECOND_CALDERON = 2
 OSRC_INC_NONE = 0
 OSRC_INC_PLANEWAVE = 1
 OSRC_INC_POINTSOURCE = 2
@@ -52,7 +55,7 @@ class osrc_params(ctypes.Structure):
         ("theta", ctypes.c_double), ("damping_R", ctypes.c_double),
         ("osrc_side", ctypes.c_int), ("n_ss", ctypes.c_int),
         ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double),
-        ("inner_maxit", ctypes.c_int),
+        ("inner_maxit", ctypes.c_int), ("precond", ctypes.c_int),
     ]
 
 

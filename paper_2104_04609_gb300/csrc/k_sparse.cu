@@ -412,7 +412,24 @@ int mass_solve(osrc_problem *pb, const double2 *x, double2 *y, cudaStream_t st) 
 //   (1 + B X)^-1 u2 = (M - B S / k_eps^2)^-1 y2
 // so the mass solve of row 1 and all 2 N_Pade + 1 shifted systems run as one
 // batched launch (row 2 needs no mass solve at all).
-int osrc_precond_nsys(const osrc_problem *pb) { return 2 * pb->p.n_pade + 2; }
+int osrc_precond_nsys(const osrc_problem *pb) {
+    return pb->p.precond == OSRC_PRECOND_OSRC ? 2 * pb->p.n_pade + 2 : 2;
+}
+
+// both block rows of M^-1 y; rows swapped in the output when swap is set
+static int mass_solve_async(osrc_problem *pb, const double2 *y, double2 *z, bool swap, cudaStream_t st) {
+    const int n = pb->nv;
+    KryBatch b{};
+    b.nsys = 2;
+    for (int k = 0; k < 2; ++k) {
+        b.s[k].alpha = cd(1.0, 0.0);
+        b.s[k].beta = cd(0.0, 0.0);
+        b.s[k].f = y + (size_t)k * n;
+        b.s[k].x = z + (size_t)(swap ? 1 - k : k) * n;
+        b.s[k].conj = 1;
+    }
+    return launch_kry(pb, b, st);
+}
 
 int kry_status_host(osrc_problem *pb, const int *stat, int nsys) {
     int worst = 0;
@@ -432,6 +449,15 @@ int osrc_precond_fused(osrc_problem *pb, const double2 *y, double2 *z, cudaStrea
 
 int osrc_precond_fused_async(osrc_problem *pb, const double2 *y, double2 *z, cudaStream_t st) {
     const int n = pb->nv, np = pb->p.n_pade;
+    if (pb->p.precond == OSRC_PRECOND_MASS) return mass_solve_async(pb, y, z, false, st);
+    if (pb->p.precond == OSRC_PRECOND_CALDERON) {
+        // z = M^-1 B Pi M^-1 y: the first mass solve writes its rows swapped
+        double2 *t = pb->d_kry_rhs.p + 2 * (size_t)n, *w = pb->d_tmp2.p + 2 * (size_t)n;
+        OSRC_TRY(mass_solve_async(pb, y, t, true, st));
+        if (pb->p.precision == OSRC_FP64_DENSE) OSRC_TRY(dense_apply(pb, t, w, st));
+        else OSRC_TRY(far_apply(pb, t, w, OSRC_PART_ALL, st));
+        return mass_solve_async(pb, w, z, false, st);
+    }
     const double2 ke2 = cmul(pb->k_eps, pb->k_eps);
     const double2 inv_ke2 = cdiv(cd(1.0, 0.0), ke2);
     double2 *sol = pb->d_kry_rhs.p + 2 * (size_t)n;

@@ -70,6 +70,7 @@ extern "C" void osrc_params_default(osrc_params *p) {
     p->precision = OSRC_FP32_MATFREE;
     p->inner_tol = 1e-10;
     p->inner_maxit = 2000;
+    p->precond = OSRC_PRECOND_OSRC;
 }
 
 // ---------------------------------------------------------------------------
@@ -300,6 +301,7 @@ extern "C" int osrc_problem_create(osrc_mesh *mesh, const osrc_params *prm, osrc
         !(p.rho_ratio > 0.0) || !std::isfinite(p.rho_ratio) || p.n_pade < 1 || p.n_pade > 16 ||
         p.n_ss < 2 || p.n_ss > 12 || !(p.inner_tol > 0.0) || p.inner_tol > 1e-4 ||
         p.inner_maxit < 1 || (p.precision != OSRC_FP32_MATFREE && p.precision != OSRC_FP64_DENSE) ||
+        p.precond < OSRC_PRECOND_OSRC || p.precond > OSRC_PRECOND_CALDERON ||
         (p.osrc_side != 0 && p.osrc_side != 1) || !std::isfinite(p.theta)) {
         osrc_set_error("invalid problem parameters");
         return OSRC_INVALID_ARG;

@@ -166,6 +166,27 @@ def test_oracle_gmres_iterations_agree(B, small):
     assert abs(info.iterations - it_ref) <= 2
 
 
+@pytest.mark.parametrize("kind", ["mass", "calderon"])
+def test_other_preconditioners(B, small, small_ref, kind):
+    """Mass-only and Calderon preconditioning (Sec. 2.4, 2.5): the solution is
+    the direct solve's and the iteration count the oracle's (+-2)."""
+    v, t, S0 = small
+    far, near, _, _ = small_ref
+    code = {"mass": B.OSRC_PRECOND_MASS, "calderon": B.OSRC_PRECOND_CALDERON}[kind]
+    S = B.Solver(v, t, K0, K1, RHO, precond=code)
+    try:
+        b = S.rhs_planewave([[0.0, 0.0, 1.0]])
+        x, info = S.solve(b, tol=1e-8, maxit=400)
+        ref = np.linalg.solve(far + near, b.cpu().numpy().ravel())
+        assert info.converged == 1 and _rel(x.cpu().numpy().ravel(), ref) < 1e-5
+        P = O.Problem(v, t, K0, K1, RHO, nss=S.params.n_ss, precond=kind)
+        _, it_ref, _ = P.solve_gmres(P.rhs(), tol=1e-6, maxit=400)
+        _, info6 = S.solve(b, tol=1e-6, maxit=400)
+        assert abs(info6.iterations - it_ref) <= 2, (info6.iterations, it_ref)
+    finally:
+        S.close()
+
+
 def test_dense_fp64_path(B):
     v, t = icosphere(2)
     S = B.Solver(v, t, K0, K1, RHO, precision=B.OSRC_FP64_DENSE)
