@@ -23,6 +23,9 @@ Functions and the passages they follow:
                       (Sec. 2.2, representation formulas)
   field()             total field outside / inside from a PMCHWT solution
                       (Sec. 2.2, with the transmission conditions of Sec. 2.1)
+  pmchwt_matrix_objects(), field_objects()
+                      the same for disjoint objects with their own materials
+                      (Sec. 2.2, multiple scattering)
 
 Readings where the paper is silent or ambiguous (each is listed in the design doc):
 quadrature orders (6-point rule for separated pairs, Sauter-Schwab with n
@@ -44,6 +47,7 @@ __all__ = [
     "assemble_rows", "pmchwt_matrix", "pmchwt_rows", "mass_stiffness", "rhs",
     "pade", "pade_eval", "ntd_partial_fractions", "damped_wavenumber",
     "mean_edge_length", "osrc_apply", "strong_apply", "gmres", "Problem", "potentials", "field",
+    "components", "pmchwt_matrix_objects", "field_objects",
 ]
 
 _LIB = None
@@ -175,6 +179,48 @@ def pmchwt_matrix(verts, tris, k_ext, k_int, rho_ratio, nss=6, part=3):
                      [T0 + T1, D0 + D1 / rho_ratio]])
 
 
+def components(tris):
+    """Objects of a mesh of disjoint closed surfaces: the connected components
+    of the triangle-adjacency graph (triangles sharing a vertex), numbered in
+    the order of their first triangle.  Returns (per-triangle ids,
+    per-vertex ids)."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+
+    t = np.asarray(tris, dtype=np.int64)
+    nv = int(t.max()) + 1
+    rows = np.repeat(t[:, 0], 2)
+    cols = t[:, 1:].ravel()
+    G = sp.coo_matrix((np.ones(len(rows)), (rows, cols)), shape=(nv, nv))
+    _, lab = connected_components(G, directed=False)
+    # renumber by first triangle
+    order, seen = {}, []
+    for c in lab[t[:, 0]]:
+        if c not in order:
+            order[c] = len(order)
+    vcomp = np.array([order[c] for c in lab])
+    return vcomp[t[:, 0]], vcomp
+
+
+def pmchwt_matrix_objects(verts, tris, k_ext, k_int, rho_ratio, nss=6, part=3):
+    """Permuted PMCHWT matrix of disjoint objects (Sec. 2.2, multiple
+    scattering): object m has its own k_int[m] and rho_ratio[m]; the interior
+    operators act within each object only (diagonal blocks A_0,mm + A^_m),
+    the exterior ones between all surfaces (cross blocks A_0,mn):
+        [[V0 + sum_m rho_m V_m|mm, -K0 - sum_m K_m|mm],
+         [T0 + sum_m T_m|mm,        D0 + sum_m D_m|mm / rho_m]]."""
+    _, vc = components(tris)
+    V, K, T, D = (a.copy() for a in assemble(verts, tris, k_ext, nss, part))
+    for m in range(vc.max() + 1):
+        sel = np.outer(vc == m, vc == m)
+        Vm, Km, Tm, Dm = assemble(verts, tris, k_int[m], nss, part)
+        V = V + rho_ratio[m] * np.where(sel, Vm, 0)
+        K = K + np.where(sel, Km, 0)
+        T = T + np.where(sel, Tm, 0)
+        D = D + np.where(sel, Dm, 0) / rho_ratio[m]
+    return np.block([[V, -K], [T, D]])
+
+
 def pmchwt_rows(verts, tris, k_ext, k_int, rho_ratio, rows, nss=6, part=3):
     """Rows of the permuted PMCHWT matrix: for test vertex i in ``rows`` the
     returned arrays R1, R2 (len(rows), 2 n_v) are rows i and n_v + i."""
@@ -261,6 +307,37 @@ def field(verts, tris, k_ext, k_int, rho_ratio, x, pts, inc="planewave", src=(0.
         uinc = np.exp(1j * k_ext * R) / (4.0 * math.pi * R)
     u = np.where(ins, rho_ratio * S1 - D1, uinc + D0 - S0)
     return u, ins
+
+
+def field_objects(verts, tris, k_ext, k_int, rho_ratio, x, pts, inc="planewave",
+                  src=(0.0, 0.0, 1.0)):
+    """Total pressure at points for disjoint objects with their own materials
+    (k_int[m], rho_ratio[m]): outside every object the exterior
+    representation over all surfaces plus the incident field; inside object m
+    the interior representation over its own surface only.  Returns (u,
+    region) with region m + 1 inside object m and 0 outside."""
+    P = np.atleast_2d(np.asarray(pts, dtype=np.float64))
+    t = np.asarray(tris)
+    tc, _ = components(t)
+    nv = np.asarray(verts).shape[0]
+    psi, phi = np.asarray(x)[:nv], np.asarray(x)[nv:]
+    region = np.zeros(P.shape[0], dtype=int)
+    for m in range(tc.max() + 1):
+        region[inside(verts, t[tc == m], P)] = m + 1
+    S0, D0 = potentials(verts, t, k_ext, psi, phi, P)
+    s = np.asarray(src, dtype=np.float64)
+    if inc == "planewave":
+        uinc = np.exp(1j * k_ext * (P @ s))
+    else:
+        R = np.linalg.norm(P - s[None, :], axis=1)
+        uinc = np.exp(1j * k_ext * R) / (4.0 * math.pi * R)
+    u = uinc + D0 - S0
+    for m in range(tc.max() + 1):
+        sel = region == m + 1
+        if sel.any():
+            Sm, Dm = potentials(verts, t[tc == m], k_int[m], psi, phi, P[sel])
+            u[sel] = rho_ratio[m] * Sm - Dm
+    return u, region
 
 
 # --------------------------------------------------------------------------
@@ -424,16 +501,26 @@ class Problem:
     vertices at most."""
 
     def __init__(self, verts, tris, k_ext, k_int, rho_ratio, n_pade=4,
-                 theta=math.pi / 3, damping_R=None, osrc_side=1, nss=6, precond="osrc"):
+                 theta=math.pi / 3, damping_R=None, osrc_side=1, nss=6, precond="osrc",
+                 objects=None):
+        """objects = (k_int list, rho_ratio list): one material per connected
+        component (disjoint objects); k_int and rho_ratio are then unused."""
         self.verts = np.asarray(verts, dtype=np.float64)
         self.tris = np.asarray(tris, dtype=np.int32)
         self.nv = self.verts.shape[0]
         self.k_ext, self.k_int, self.rho = k_ext, k_int, rho_ratio
         self.n_pade, self.theta, self.nss = n_pade, theta, nss
         self.R = damping_R if damping_R else mean_edge_length(self.verts, self.tris)
-        self.k_osrc = k_int if osrc_side == 1 else k_ext
-        self.k_eps = damped_wavenumber(self.k_osrc, self.R)
-        self.B = pmchwt_matrix(self.verts, self.tris, k_ext, k_int, rho_ratio, nss)
+        self.objects = objects
+        if objects is None:
+            self.k_osrc = k_int if osrc_side == 1 else k_ext
+            self.k_eps = damped_wavenumber(self.k_osrc, self.R)
+            self.B = pmchwt_matrix(self.verts, self.tris, k_ext, k_int, rho_ratio, nss)
+        else:
+            _, self.vcomp = components(self.tris)
+            kl = list(objects[0])
+            self.k_osrc_obj = [kl[m] if osrc_side == 1 else k_ext for m in range(len(kl))]
+            self.B = pmchwt_matrix_objects(self.verts, self.tris, k_ext, kl, list(objects[1]), nss)
         self.M, self.S = mass_stiffness(self.verts, self.tris)
         self._solver = _ShiftedSolver(self.M, self.S)
         self.precond_kind = precond
@@ -453,6 +540,19 @@ class Problem:
         if self.precond_kind == "calderon":
             y = np.asarray(y)
             return strong_apply(self.M, self.B @ np.concatenate([y[nv:], y[:nv]]))
+        if self.objects is not None:
+            # block-diagonal OSRC: each object with its own wavenumber
+            y = np.asarray(y)
+            z1 = np.zeros(nv, dtype=complex)
+            z2 = np.zeros(nv, dtype=complex)
+            for m, k in enumerate(self.k_osrc_obj):
+                idx = np.nonzero(self.vcomp == m)[0]
+                Mm = self.M[idx][:, idx]
+                Sm = self.S[idx][:, idx]
+                z1[idx], z2[idx] = osrc_apply(Mm, Sm, y[idx], y[nv + idx], k,
+                                              damped_wavenumber(k, self.R), self.n_pade,
+                                              self.theta)
+            return np.concatenate([z1, z2])
         z1, z2 = osrc_apply(self.M, self.S, y[:nv], y[nv:], self.k_osrc,
                             self.k_eps, self.n_pade, self.theta, self._solver)
         return np.concatenate([z1, z2])
