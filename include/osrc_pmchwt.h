@@ -147,6 +147,23 @@ double osrc_mesh_mean_edge(const osrc_mesh *mesh);
  * outlive the problem. */
 int osrc_problem_create(osrc_mesh *mesh, const osrc_params *params,
                         osrc_problem **out, void *stream);
+
+/* Disjoint objects (Sec. 2.2, multiple scattering; the paper's four-sphere
+ * experiment, Sec. 3.5): the objects are the connected components of the
+ * mesh (triangles sharing vertices), numbered in the order of their first
+ * triangle (osrc_mesh_objects gives their count).  Object m has its own
+ * interior wavenumber k_int[m] and density ratio rho_ratio[m]; the system's
+ * diagonal blocks are A_0,mm + A^_m (interior operators within the object),
+ * its cross blocks A_0,mn exterior operators only; the OSRC preconditioner
+ * is block diagonal with each object's wavenumber (interior side) and the
+ * common damping length; the field inside object m uses its material.
+ * prm->k_int and prm->rho_ratio are ignored.  nobj must equal the mesh's
+ * object count (OSRC_INVALID_ARG otherwise).  osrc_problem_create on a mesh
+ * with several objects gives every object prm's material. */
+int osrc_problem_create_objects(osrc_mesh *mesh, const osrc_params *prm, int nobj,
+                                const double *k_int, const double *rho_ratio, osrc_problem **out,
+                                void *stream);
+int osrc_mesh_objects(const osrc_mesh *mesh);
 void osrc_problem_destroy(osrc_problem *pb);
 int osrc_problem_nv(const osrc_problem *pb);
 
@@ -289,7 +306,9 @@ enum { OSRC_INC_NONE = 0, OSRC_INC_PLANEWAVE = 1, OSRC_INC_POINTSOURCE = 2 };
  * exp(i k_ext |x - x0|) / (4 pi |x - x0|); OSRC_INC_NONE: scattered field
  * only; inc_param host, 3 doubles).  x: device, 2nv complex FP64; pts:
  * device, npts x 3 FP64; u: device, npts complex FP64 (out); region:
- * device int[npts] (out, 1 inside / 0 outside) or NULL.  FP64 throughout
+ * device int[npts] (out: m + 1 inside object m, 0 outside) or NULL.  With
+ * several objects a point inside object m takes the interior representation
+ * over that object's surface with its material.  FP64 throughout
  * (region test in FP32).  Asynchronous on stream. */
 int osrc_field_eval(osrc_problem *pb, const void *x, const double *pts, int npts, int inc_kind,
                     const double *inc_param, void *u, int *region, void *stream);

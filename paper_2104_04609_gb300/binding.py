@@ -122,6 +122,9 @@ SIGNATURES = {
     "osrc_mesh_mean_edge": (ctypes.c_double, [_VP]),
     "osrc_problem_create": (ctypes.c_int, [_VP, ctypes.POINTER(osrc_params),
                                            ctypes.POINTER(_VP), _VP]),
+    "osrc_problem_create_objects": (ctypes.c_int, [_VP, ctypes.POINTER(osrc_params), ctypes.c_int,
+                                                   _DP, _DP, ctypes.POINTER(_VP), _VP]),
+    "osrc_mesh_objects": (ctypes.c_int, [_VP]),
     "osrc_problem_destroy": (None, [_VP]),
     "osrc_problem_nv": (ctypes.c_int, [_VP]),
     "osrc_rhs_planewave": (ctypes.c_int, [_VP, _DP, ctypes.c_int, _VP, _VP]),
@@ -280,6 +283,21 @@ def osrc_problem_create(mesh, params, stream=None):
     _check(lib().osrc_problem_create(mesh, ctypes.byref(params), ctypes.byref(h), _stream(stream)),
            "osrc_problem_create")
     return h
+
+
+def osrc_problem_create_objects(mesh, params, k_int, rho_ratio, stream=None):
+    """Problem on a mesh of disjoint objects, object m with k_int[m], rho_ratio[m]."""
+    k = np.ascontiguousarray(k_int, dtype=np.float64)
+    r = np.ascontiguousarray(rho_ratio, dtype=np.float64)
+    h = _VP()
+    _check(lib().osrc_problem_create_objects(mesh, ctypes.byref(params), len(k), k.ctypes.data_as(_DP),
+                                             r.ctypes.data_as(_DP), ctypes.byref(h), _stream(stream)),
+           "osrc_problem_create_objects")
+    return h
+
+
+def osrc_mesh_objects(mesh):
+    return lib().osrc_mesh_objects(mesh)
 
 
 def osrc_problem_destroy(pb):
@@ -527,7 +545,9 @@ class Solver:
     tensors in and out.  Parameters are those of ``osrc_params``."""
 
     def __init__(self, verts, tris, k_ext, k_int, rho_ratio, device=0, mem_budget_bytes=0,
-                 **params):
+                 objects=None, **params):
+        """objects = (k_int list, rho_ratio list): one material per object
+        (connected component) of the mesh; k_int and rho_ratio are then unused."""
         import torch
 
         self.device = torch.device("cuda", device)
@@ -536,12 +556,16 @@ class Solver:
         self.pb = None
         try:
             self.mesh = osrc_mesh_create(self.ctx, verts, tris)
-            p = osrc_params_default(k_ext=float(k_ext), k_int=float(k_int),
-                                    rho_ratio=float(rho_ratio))
+            kk = float(k_int) if objects is None else float(objects[0][0])
+            rr = float(rho_ratio) if objects is None else float(objects[1][0])
+            p = osrc_params_default(k_ext=float(k_ext), k_int=kk, rho_ratio=rr)
             for k, v in params.items():
                 setattr(p, k, v)
             self.params = p
-            self.pb = osrc_problem_create(self.mesh, p)
+            if objects is None:
+                self.pb = osrc_problem_create(self.mesh, p)
+            else:
+                self.pb = osrc_problem_create_objects(self.mesh, p, objects[0], objects[1])
         except Exception:
             self.close()
             raise

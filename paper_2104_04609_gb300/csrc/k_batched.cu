@@ -172,14 +172,21 @@ constexpr int K32_G = 8;
 
 struct Kry32Sys {
     float2 beta;
-    int half;   // 0: rows [0, nv), 1: rows [nv, 2nv) of F
-    int conj;   // 1: Hermitian CG, 0: COCG
+    int half;    // 0: rows [0, nv), 1: rows [nv, 2nv) of F
+    int conj;    // 1: Hermitian CG, 0: COCG
+    int scaled;  // disjoint objects: row i uses beta * bscale[vcomp[i]]
 };
 
 struct Kry32Batch {
     int nsys;
+    const int *vcomp;      // object of each row
+    const float2 *bscale;  // per object (1 / k_eps^2 of the object)
     Kry32Sys s[34];
 };
+
+__device__ __forceinline__ float2 kry32_beta(const Kry32Batch &b, const Kry32Sys &s, int i) {
+    return s.scaled ? fmulc(s.beta, b.bscale[b.vcomp[i]]) : s.beta;
+}
 
 __device__ float2 dotf(float2 a, float2 b, int conj) {
     return conj ? f2c(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x) : fmulc(a, b);
@@ -198,7 +205,7 @@ __global__ void kry32_diag_kernel(Kry32Batch batch, int nv, const int *__restric
             md = Mv[e];
             sd = Sv[e];
         }
-    const float2 be = batch.s[sid].beta;
+    const float2 be = kry32_beta(batch, batch.s[sid], i);
     dinv[(size_t)sid * nv + i] = fdivc(f2c(1.f, 0.f), f2c(md + be.x * sd, be.y * sd));
 }
 
@@ -327,7 +334,7 @@ kry32_kernel(Kry32Batch batch, int nv, int R, int ngroups, const int *__restrict
                     mp = fadd(mp, fscale(pj, Mv[e]));
                     sp = fadd(sp, fscale(pj, Sv[e]));
                 }
-                const float2 acc = fadd(mp, fmulc(sy.beta, sp));
+                const float2 acc = fadd(mp, fmulc(kry32_beta(batch, sy, i), sp));
                 qq[(size_t)i * R + r] = acc;
                 const float2 t = dotf(pi, acc, cj);
                 w0 += t.x;
@@ -391,6 +398,8 @@ struct OsrcComb32 {
     int np;
     float2 ik, iik, cu, g0;
     float2 a[16], g[16];
+    const float2 *ik_obj;  // disjoint objects: i k of each object (else ik)
+    const int *vcomp;
 };
 
 // z1 = i k [cu u1 - sum_j a_j v_j],  z2 = [g0 v'_0 + sum_j g_j v'_j] / (i k)
@@ -403,8 +412,13 @@ __global__ void osrc_combine32_kernel(int nv, int R, OsrcComb32 c, const float2 
     for (int j = 0; j < c.np; ++j) a = fsub(a, fmulc(c.a[j], W[(size_t)(1 + j) * plane + k]));
     float2 b = fmulc(c.g0, W[(size_t)(c.np + 1) * plane + k]);
     for (int j = 0; j < c.np; ++j) b = fadd(b, fmulc(c.g[j], W[(size_t)(c.np + 2 + j) * plane + k]));
-    Z[k] = fmulc(c.ik, a);
-    Z[plane + k] = fmulc(c.iik, b);
+    float2 ik = c.ik, iik = c.iik;
+    if (c.ik_obj) {
+        ik = c.ik_obj[c.vcomp[k / R]];
+        iik = fdivc(f2c(1.f, 0.f), ik);
+    }
+    Z[k] = fmulc(ik, a);
+    Z[plane + k] = fmulc(iik, b);
 }
 
 // M and S values in FP32
@@ -753,6 +767,7 @@ struct BatchedState {
     DBuf<float> M32, S32;
     DBuf<float4> AFF;           // float-float split of the FP64 system matrix (residuals)
     DBuf<float2> nr32;          // touching-pair CSR values in FP32
+    DBuf<float2> obj32;         // [2][objects]: i k_osrc, 1 / k_eps^2 in FP32
     DBuf<int> err;
     DBuf<float2> kwork, kW;     // multi-RHS Krylov work and solutions
     DBuf<float2> kdinv;         // Jacobi inverse diagonals [system][row]
@@ -789,6 +804,18 @@ int batched_prepare(osrc_problem *pb, int R, int maxit_inner, cudaStream_t st) {
         const size_t nq = 4 * (size_t)pb->near_nnz;
         OSRC_TRY(bs->nr32.alloc(ctx, nq));
         d2f2_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(nq, pb->d_nr_val.p, bs->nr32.p);
+        {
+            const int nc = pb->mesh->ncomp;
+            std::vector<float2> o(2 * (size_t)nc);
+            for (int m = 0; m < nc; ++m) {
+                const ObjMat &om = pb->obj[m];
+                const double2 ke2 = cmul(om.k_eps, om.k_eps), inv = cdiv(cd(1.0, 0.0), ke2);
+                o[m] = make_float2(0.f, (float)om.k_osrc);
+                o[nc + m] = make_float2((float)inv.x, (float)inv.y);
+            }
+            OSRC_TRY(bs->obj32.alloc(ctx, o.size()));
+            OSRC_CK(cudaMemcpy(bs->obj32.p, o.data(), o.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        }
         OSRC_TRY(bs->M32.alloc(ctx, pb->ms_nnz));
         OSRC_TRY(bs->S32.alloc(ctx, pb->ms_nnz));
         d2f_kernel<<<(pb->ms_nnz + 255) / 256, 256, 0, st>>>(pb->ms_nnz, pb->d_M.p, bs->M32.p);
@@ -853,17 +880,21 @@ static int batched_precond(osrc_problem *pb, const float2 *y, float2 *z, float t
     BatchedState *bs = pb->batched;
     const int nv = pb->nv, R = bs->R, np = pb->p.n_pade;
     const double2 ke2 = cmul(pb->k_eps, pb->k_eps);
-    const double2 inv = cdiv(cd(1.0, 0.0), ke2);
+    // disjoint objects: 1/k_eps^2 of each row's object through bscale
+    const double2 inv = pb->multi ? cd(1.0, 0.0) : cdiv(cd(1.0, 0.0), ke2);
+    const int sc = pb->multi ? 1 : 0;
     Kry32Batch b{};
     b.nsys = 2 * np + 2;
-    b.s[0] = Kry32Sys{make_float2(0.f, 0.f), 0, 1};
+    b.vcomp = pb->mesh->d_vcomp.p;
+    b.bscale = pb->multi ? bs->obj32.p + pb->mesh->ncomp : nullptr;
+    b.s[0] = Kry32Sys{make_float2(0.f, 0.f), 0, 1, 0};
     for (int j = 0; j < np; ++j) {
         const double2 be = cscale(cmul(pb->B[j], inv), -1.0);
-        b.s[1 + j] = Kry32Sys{make_float2((float)be.x, (float)be.y), 0, 0};
-        b.s[np + 2 + j] = Kry32Sys{make_float2((float)be.x, (float)be.y), 1, 0};
+        b.s[1 + j] = Kry32Sys{make_float2((float)be.x, (float)be.y), 0, 0, sc};
+        b.s[np + 2 + j] = Kry32Sys{make_float2((float)be.x, (float)be.y), 1, 0, sc};
     }
     const double2 be0 = cscale(inv, -1.0);
-    b.s[np + 1] = Kry32Sys{make_float2((float)be0.x, (float)be0.y), 1, 0};
+    b.s[np + 1] = Kry32Sys{make_float2((float)be0.x, (float)be0.y), 1, 0, sc};
     kry32_diag_kernel<<<dim3((nv + 255) / 256, b.nsys), 256, 0, st>>>(b, nv, pb->d_ms_ptr.p, pb->d_ms_col.p,
                                                                         bs->M32.p, bs->S32.p, bs->kdinv.p);
     const int ngroups = (R + K32_G - 1) / K32_G;
@@ -898,6 +929,8 @@ static int batched_precond(osrc_problem *pb, const float2 *y, float2 *z, float t
     }
     c.cu = make_float2((float)cu.x, (float)cu.y);
     c.g0 = make_float2((float)pb->g0.x, (float)pb->g0.y);
+    c.ik_obj = pb->multi ? bs->obj32.p : nullptr;
+    c.vcomp = pb->mesh->d_vcomp.p;
     const size_t plane = (size_t)nv * R;
     osrc_combine32_kernel<<<(unsigned)((plane + 255) / 256), 256, 0, st>>>(nv, R, c, bs->kW.p, z);
     pb->launches += 3;

@@ -270,10 +270,10 @@ __device__ __forceinline__ CenterPair center_pair(const float4 &cth, const float
 // from the triangle centroids, x - y = D + delta, and the phase is
 // k r = k r_c + k (2 D.delta + delta.delta) / (r + r_c) with k r_c reduced in
 // float-float arithmetic once per triangle pair.
-template <bool CENTRED>
+template <bool CENTRED, bool MULTI>
 __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, const f2 &P5, f2 mnx,
                                           f2 mny, f2 mnz, f2 wq2, const FarConst2 &c,
-                                          const CenterPair &cp, PairAcc &A) {
+                                          const CenterPair &cp, f2 m1, PairAcc &A) {
     const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3], P4 = P[4];
     f2 dx, dy, dz, ddx, ddy, ddz;
     if (CENTRED) {
@@ -323,6 +323,10 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
         __sincosf(kr1.x, &s1.x, &c1.x);
         __sincosf(kr1.y, &s1.y, &c1.y);
     }
+    if (MULTI) {  // source on another object: exterior wavenumber only
+        c1 = mul2(c1, m1);
+        s1 = mul2(s1, m1);
+    }
     const f2 psr = hi2(P1), psi = lo2(P2), mpsr = hi2(P2), mpsi = lo2(P3);
     const f2 phr = hi2(P3), phi = lo2(P4), mphr = hi2(P4), mphi = P5;
     (void)mpsr;
@@ -363,19 +367,23 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
 // run per 64-triangle tile, then tile sums are added to running sums.
 // CENTRED: pt holds offsets from the test-triangle centroid and cen the
 // float-float centroids (see far_pair2).
-template <bool CENTRED>
+// MULTI: disjoint objects (Sec. 2.2); the interior constants are the test
+// triangle's object's, and interior terms vanish for sources on other objects.
+template <bool CENTRED, bool MULTI>
 __global__ void __launch_bounds__(FAR_THREADS, 4)
 far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
            const float4 *__restrict__ tn, const int4 *__restrict__ tv,
            const float4 *__restrict__ sP, const float2 *__restrict__ sP5,
-           const float4 *__restrict__ sC, int nt, int npts, int tris_per_split, FarConst2 c,
-           float4 kff, float *__restrict__ part) {
+           const float4 *__restrict__ sC, int nt, int npts, int tris_per_split, FarConst2 c0,
+           float4 kff0, const int *__restrict__ tcomp, const FarObj *__restrict__ fobj,
+           float *__restrict__ part) {
     __shared__ float4 shP[FAR_TS * 6 * 5];
     __shared__ float2 shP5[FAR_TS * 6];
     __shared__ float4 shN[FAR_TS];
     __shared__ float4 shC[FAR_TS * 5];
     __shared__ int4 shV[FAR_TS];
     __shared__ float4 shCen[CENTRED ? 2 * FAR_TS : 1];
+    __shared__ int shComp[MULTI ? FAR_TS : 1];
 
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int split = blockIdx.y;
@@ -390,6 +398,20 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
     const int4 vt = tv[tau];
     const f2 mnx = dup2(-n4.x), mny = dup2(-n4.y), mnz = dup2(-n4.z);
     const f2 W1 = dup2((float)kQw1), W2 = dup2((float)kQw2);
+    FarConst2 c = c0;
+    float4 kff = kff0;
+    int ct = 0;
+    if (MULTI) {
+        ct = tcomp[tau];
+        const FarObj o = fobj[ct];
+        c.k1 = dup2(o.k1);
+        c.nk1 = dup2(o.nk1);
+        c.rho = dup2(o.rho);
+        c.irho = dup2(o.irho);
+        c.dk1 = dup2(o.dk1);
+        kff.z = o.k1h;
+        kff.w = o.k1l;
+    }
     float4 cth = make_float4(0.f, 0.f, 0.f, 0.f), ctl = cth;
     if (CENTRED) {
         cth = cen[2 * tau];
@@ -413,6 +435,8 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
         }
         if (CENTRED)
             for (int i = threadIdx.x; i < 2 * cnt; i += blockDim.x) shCen[i] = cen[2 * (size_t)t0 + i];
+        if (MULTI)
+            for (int i = threadIdx.x; i < cnt; i += blockDim.x) shComp[i] = tcomp[t0 + i];
         __syncthreads();
 
         PairAcc A;
@@ -437,10 +461,11 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
             }
             const float nxnyn = n4.x * mns.x + n4.y * mns.y + n4.z * mns.z;  // -n_x.n_y
             A.t1r = A.t1i = A.ur = A.ui = A.t3r = A.t3i = make_float2(0.f, 0.f);
+            const f2 m1 = dup2(MULTI && shComp[s] != ct ? 0.f : 1.f);
 #pragma unroll
             for (int q = 0; q < 6; ++q)
-                far_pair2<CENTRED>(X, Y, Z, &shP[30 * s + 5 * q], shP5[6 * s + q], mnx, mny, mnz,
-                                   q < 3 ? W1 : W2, c, cp, A);
+                far_pair2<CENTRED, MULTI>(X, Y, Z, &shP[30 * s + 5 * q], shP5[6 * s + q], mnx, mny, mnz,
+                                          q < 3 ? W1 : W2, c, cp, m1, A);
             // u1 += (x - y).n_y T1 = (-(x - y).n_y)(-T1);  u2 += (-n_x.n_y) U
             A.u1r = fma2(xnyn, A.t1r, A.u1r);
             A.u1i = fma2(xnyn, A.t1i, A.u1i);
@@ -554,16 +579,17 @@ int far_setup_geometry(osrc_problem *pb, cudaStream_t st) {
             }
         const double diag = sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
                                  (hi[2] - lo[2]) * (hi[2] - lo[2]));
-        const double kmax = fmax(pb->p.k_ext, pb->p.k_int);
+        double kmax = fmax(pb->p.k_ext, pb->p.k_int);
+        for (const ObjMat &o : pb->obj) kmax = fmax(kmax, o.k1);
         pb->far_reduce = kmax * diag > 64.0 * 3.14159265358979323846;
     }
     // split the source range so that the grid covers the GPU several times
     int dev = m->ctx->device, sms = 0, per_sm = 0;
     OSRC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (pb->far_reduce)
-        OSRC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far_kernel<true>, FAR_THREADS, 0));
+        OSRC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far_kernel<true, false>, FAR_THREADS, 0));
     else
-        OSRC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far_kernel<false>, FAR_THREADS, 0));
+        OSRC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far_kernel<false, false>, FAR_THREADS, 0));
     if (per_sm < 1) per_sm = 1;
     const int bx = (pb->npts / 2 + FAR_THREADS - 1) / FAR_THREADS;
     const int slots = sms * per_sm;
@@ -622,16 +648,26 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
             OSRC_TRY(far_prof_collect(pb));
             OSRC_CK(cudaEventRecord(pb->prof_ev[0], st));
         }
-        if (pb->far_reduce)
-            far_kernel<true><<<grid, FAR_THREADS, 0, st>>>(pb->d_poff.p, pb->d_cen.p, pb->d_tn.p,
-                                                           pb->d_tv.p, pb->d_sP.p, pb->d_sP5.p,
-                                                           pb->d_sC.p, nt, npts, tps, c, kff,
-                                                           pb->d_part.p);
+        const float4 *pts = pb->far_reduce ? pb->d_poff.p : pb->d_pt.p;
+        const int *tc = m->d_tcomp.p;
+        const FarObj *fo = pb->d_fobj.p;
+        float *prt = pb->d_part.p;
+        if (pb->far_reduce && pb->multi)
+            far_kernel<true, true><<<grid, FAR_THREADS, 0, st>>>(pts, pb->d_cen.p, pb->d_tn.p, pb->d_tv.p, pb->d_sP.p,
+                                                                 pb->d_sP5.p, pb->d_sC.p, nt, npts, tps, c, kff, tc,
+                                                                 fo, prt);
+        else if (pb->far_reduce)
+            far_kernel<true, false><<<grid, FAR_THREADS, 0, st>>>(pts, pb->d_cen.p, pb->d_tn.p, pb->d_tv.p, pb->d_sP.p,
+                                                                  pb->d_sP5.p, pb->d_sC.p, nt, npts, tps, c, kff, tc,
+                                                                  fo, prt);
+        else if (pb->multi)
+            far_kernel<false, true><<<grid, FAR_THREADS, 0, st>>>(pts, pb->d_cen.p, pb->d_tn.p, pb->d_tv.p, pb->d_sP.p,
+                                                                  pb->d_sP5.p, pb->d_sC.p, nt, npts, tps, c, kff, tc,
+                                                                  fo, prt);
         else
-            far_kernel<false><<<grid, FAR_THREADS, 0, st>>>(pb->d_pt.p, pb->d_cen.p, pb->d_tn.p,
-                                                            pb->d_tv.p, pb->d_sP.p, pb->d_sP5.p,
-                                                            pb->d_sC.p, nt, npts, tps, c, kff,
-                                                            pb->d_part.p);
+            far_kernel<false, false><<<grid, FAR_THREADS, 0, st>>>(pts, pb->d_cen.p, pb->d_tn.p, pb->d_tv.p,
+                                                                   pb->d_sP.p, pb->d_sP5.p, pb->d_sC.p, nt, npts, tps,
+                                                                   c, kff, tc, fo, prt);
         pb->launches++;
         if (pb->prof_on) {
             OSRC_CK(cudaEventRecord(pb->prof_ev[1], st));

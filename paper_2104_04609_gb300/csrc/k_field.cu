@@ -11,6 +11,9 @@
 // interpolated at the rule points.  A point's region comes from the Laplace
 // double layer of the constant 1 (Gauss: 1 inside, 0 outside), so each
 // target needs one wavenumber only and a warp never diverges in the pair loop.
+// Disjoint objects (Sec. 2.2): source points are stored object by object;
+// a point inside object m (region m + 1) takes the interior representation
+// over that object's surface with its own material.
 // Pass 1 (region) runs in FP32; pass 2 (field) in FP64, source points staged
 // through shared memory in tiles of FT.
 #include "osrc_internal.cuh"
@@ -25,11 +28,11 @@ constexpr int FT = 128;
 // Source data per rule point (6 per triangle): {y, w |tau|}, {n, 0},
 // {psi_q re, im, phi_q re, im}.
 __global__ void field_src_kernel(int nt, int nv, const int *__restrict__ tris, const double *__restrict__ verts,
-                                 const double *__restrict__ tgeo, const double2 *__restrict__ x,
-                                 double4 *__restrict__ src) {
+                                 const double *__restrict__ tgeo, const int *__restrict__ order,
+                                 const double2 *__restrict__ x, double4 *__restrict__ src) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 6 * nt) return;
-    const int t = idx / 6, q = idx % 6;
+    const int t = order[idx / 6], q = idx % 6;
     const double al = q < 3 ? kFa1 : kFa2, w = q < 3 ? kFw1 : kFw2;
     double bc[3] = {al, al, al};
     bc[q % 3] = 1.0 - 2.0 * al;
@@ -47,54 +50,64 @@ __global__ void field_src_kernel(int nt, int nv, const int *__restrict__ tris, c
     src[3 * (size_t)idx + 2] = make_double4(ps.x, ps.y, ph.x, ph.y);
 }
 
-// region[i] = 1 if sum_q w_q (y_q - x).n_q / (4 pi r^3) > 1/2 (inside), else 0
+// region[i] = m + 1 if the solid angle of object m's surface at the point,
+// sum_q w_q (y_q - x).n_q / (4 pi r^3), exceeds 1/2 (inside object m), else 0.
+// obeg: [nobj + 1] source-point ranges of the objects.
 __global__ void __launch_bounds__(FT)
-field_region_kernel(int npts, const double *__restrict__ pts, int ns, const double4 *__restrict__ src,
-                    int *__restrict__ region) {
+field_region_kernel(int npts, const double *__restrict__ pts, int nobj, const int *__restrict__ obeg,
+                    const double4 *__restrict__ src, int *__restrict__ region) {
     __shared__ float4 sy[FT], sn[FT];
     const int i = blockIdx.x * FT + threadIdx.x;
     const bool valid = i < npts;
     const float x0 = valid ? (float)pts[3 * (size_t)i] : 0.f, x1 = valid ? (float)pts[3 * (size_t)i + 1] : 0.f,
                 x2 = valid ? (float)pts[3 * (size_t)i + 2] : 0.f;
-    double total = 0.0;
-    for (int base = 0; base < ns; base += FT) {
-        const int j = base + threadIdx.x;
-        if (j < ns) {
-            const double4 a = src[3 * (size_t)j], b = src[3 * (size_t)j + 1];
-            sy[threadIdx.x] = make_float4((float)a.x, (float)a.y, (float)a.z, (float)a.w);
-            sn[threadIdx.x] = make_float4((float)b.x, (float)b.y, (float)b.z, 0.f);
+    int reg = 0;
+    for (int m = 0; m < nobj; ++m) {
+        const int b0 = obeg[m], b1 = obeg[m + 1];
+        double total = 0.0;
+        for (int base = b0; base < b1; base += FT) {
+            const int j = base + threadIdx.x;
+            if (j < b1) {
+                const double4 a = src[3 * (size_t)j], b = src[3 * (size_t)j + 1];
+                sy[threadIdx.x] = make_float4((float)a.x, (float)a.y, (float)a.z, (float)a.w);
+                sn[threadIdx.x] = make_float4((float)b.x, (float)b.y, (float)b.z, 0.f);
+            }
+            __syncthreads();
+            const int jn = min(FT, b1 - base);
+            float acc = 0.f;
+            for (int jj = 0; jj < jn; ++jj) {
+                const float4 y = sy[jj], n = sn[jj];
+                const float d0 = y.x - x0, d1 = y.y - x1, d2 = y.z - x2;
+                const float ri = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+                acc += y.w * (d0 * n.x + d1 * n.y + d2 * n.z) * ri * ri * ri;
+            }
+            total += (double)acc;
+            __syncthreads();
         }
-        __syncthreads();
-        const int jn = min(FT, ns - base);
-        float acc = 0.f;
-        for (int jj = 0; jj < jn; ++jj) {
-            const float4 y = sy[jj], n = sn[jj];
-            const float d0 = y.x - x0, d1 = y.y - x1, d2 = y.z - x2;
-            const float ri = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-            acc += y.w * (d0 * n.x + d1 * n.y + d2 * n.z) * ri * ri * ri;
-        }
-        total += (double)acc;
-        __syncthreads();
+        if (total * kFInv4Pi > 0.5) reg = m + 1;
     }
-    if (valid) region[i] = total * kFInv4Pi > 0.5 ? 1 : 0;
+    if (valid) region[i] = reg;
 }
 
 struct FieldConst {
-    double k0, k1, rho;
+    double k0;
     int inc_kind;  // 0 none, 1 plane wave (s = direction), 2 point source (s = position)
     double s0, s1, s2;
 };
 
 __global__ void __launch_bounds__(FT)
-field_kernel(int npts, const double *__restrict__ pts, int ns, const double4 *__restrict__ src,
-             const int *__restrict__ region, FieldConst c, double2 *__restrict__ u) {
+field_kernel(int npts, const double *__restrict__ pts, int ns, const int *__restrict__ obeg,
+             const ObjMat *__restrict__ obj, const double4 *__restrict__ src, const int *__restrict__ region,
+             FieldConst c, double2 *__restrict__ u) {
     __shared__ double4 sa[FT], sb[FT], sc[FT];
     const int i = blockIdx.x * FT + threadIdx.x;
     const bool valid = i < npts;
     const double x0 = valid ? pts[3 * (size_t)i] : 0.0, x1 = valid ? pts[3 * (size_t)i + 1] : 0.0,
                  x2 = valid ? pts[3 * (size_t)i + 2] : 0.0;
     const int ins = valid ? region[i] : 0;
-    const double k = ins ? c.k1 : c.k0;
+    // outside: every source point, k0; inside object m: its own points, k_m
+    const double k = ins ? obj[ins - 1].k1 : c.k0;
+    const int lo = ins ? obeg[ins - 1] : 0, hi = ins ? obeg[ins] : ns;
     double2 S = cd(0, 0), D = cd(0, 0);
     for (int base = 0; base < ns; base += FT) {
         const int j = base + threadIdx.x;
@@ -104,8 +117,8 @@ field_kernel(int npts, const double *__restrict__ pts, int ns, const double4 *__
             sc[threadIdx.x] = src[3 * (size_t)j + 2];
         }
         __syncthreads();
-        const int jn = min(FT, ns - base);
-        for (int jj = 0; jj < jn; ++jj) {
+        const int j0 = max(0, lo - base), j1 = min(FT, min(ns, hi) - base);
+        for (int jj = j0; jj < j1; ++jj) {
             const double4 a = sa[jj], n = sb[jj], dv = sc[jj];
             const double d0 = a.x - x0, d1 = a.y - x1, d2 = a.z - x2;  // y - x
             const double ri = rsqrt(d0 * d0 + d1 * d1 + d2 * d2);
@@ -124,7 +137,7 @@ field_kernel(int npts, const double *__restrict__ pts, int ns, const double4 *__
     if (!valid) return;
     double2 out;
     if (ins) {
-        out = csub(cscale(S, c.rho), D);
+        out = csub(cscale(S, obj[ins - 1].rho), D);
     } else {
         double2 inc = cd(0, 0);
         if (c.inc_kind == 1) {
@@ -161,17 +174,24 @@ extern "C" int osrc_field_eval(osrc_problem *pb, const void *x, const double *pt
         if (pb->d_freg.n < (size_t)npts) OSRC_TRY(pb->d_freg.alloc(m->ctx, npts));
         reg = pb->d_freg.p;
     }
+    if (pb->d_fobeg.n < (size_t)m->ncomp + 1) {
+        OSRC_TRY(pb->d_fobeg.alloc(m->ctx, m->ncomp + 1));
+        std::vector<int> ob(m->ncomp + 1);
+        for (int c = 0; c <= m->ncomp; ++c) ob[c] = 6 * m->comp_tbeg[c];
+        OSRC_CK(cudaMemcpy(pb->d_fobeg.p, ob.data(), ob.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
     field_src_kernel<<<(ns + 255) / 256, 256, 0, st>>>(nt, pb->nv, m->d_tris.p, m->d_verts.p, pb->d_tgeo.p,
-                                                       (const double2 *)x, pb->d_fsrc.p);
+                                                       m->d_tri_order.p, (const double2 *)x, pb->d_fsrc.p);
     const unsigned nb = (unsigned)((npts + FT - 1) / FT);
-    field_region_kernel<<<nb, FT, 0, st>>>(npts, pts, ns, pb->d_fsrc.p, reg);
-    FieldConst c{pb->p.k_ext, pb->p.k_int, pb->p.rho_ratio, inc_kind, 0.0, 0.0, 0.0};
+    field_region_kernel<<<nb, FT, 0, st>>>(npts, pts, m->ncomp, pb->d_fobeg.p, pb->d_fsrc.p, reg);
+    FieldConst c{pb->p.k_ext, inc_kind, 0.0, 0.0, 0.0};
     if (inc_kind) {
         c.s0 = inc_param[0];
         c.s1 = inc_param[1];
         c.s2 = inc_param[2];
     }
-    field_kernel<<<nb, FT, 0, st>>>(npts, pts, ns, pb->d_fsrc.p, reg, c, (double2 *)u);
+    field_kernel<<<nb, FT, 0, st>>>(npts, pts, ns, pb->d_fobeg.p, pb->d_obj.p, pb->d_fsrc.p, reg, c,
+                                    (double2 *)u);
     pb->launches += 3;
     OSRC_CK(cudaGetLastError());
     return OSRC_OK;

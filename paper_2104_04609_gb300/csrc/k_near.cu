@@ -80,6 +80,8 @@ __device__ __forceinline__ void ss_map(int kase, int m, double xi, double e1, do
 struct NearConst {
     double k0, k1, rho;
     int nss;
+    const ObjMat *obj;  // disjoint objects: material per object (else k1, rho)
+    const int *tcomp;   // object of each triangle
 };
 
 constexpr int NEAR_WARPS = 4;
@@ -108,6 +110,12 @@ near_ss_kernel(const NearPair *__restrict__ pairs, long long npairs,
     const long long pi = (long long)blockIdx.x * NEAR_WARPS + (threadIdx.x >> 5);
     if (pi >= npairs) return;
     const NearPair pr = pairs[pi];
+    double k1 = c.k1, rho = c.rho;  // touching triangles lie on one object
+    if (c.obj) {
+        const ObjMat o = c.obj[c.tcomp[pr.t]];
+        k1 = o.k1;
+        rho = o.rho;
+    }
     int pt[3], ps[3];
     for (int a = 0; a < 3; ++a) {
         pt[a] = (pr.perm >> (2 * a)) & 3;
@@ -159,15 +167,15 @@ near_ss_kernel(const NearPair *__restrict__ pairs, long long npairs,
         const double ri = 1.0 / r;
         double s0, c0, s1, c1;
         sincos(c.k0 * r, &s0, &c0);
-        sincos(c.k1 * r, &s1, &c1);
-        const double kr0 = c.k0 * r, kr1 = c.k1 * r;
+        sincos(k1 * r, &s1, &c1);
+        const double kr0 = c.k0 * r, kr1 = k1 * r;
         const double f = kInv4Pi * ri, f3 = f * ri * ri;
         const double g0r = c0 * f, g0i = s0 * f, g1r = c1 * f, g1i = s1 * f;
         const double hsr = (-c0 - kr0 * s0 - c1 - kr1 * s1) * f3;
         const double hsi = (kr0 * c0 - s0 + kr1 * c1 - s1) * f3;
-        const double gpr = g0r + c.rho * g1r, gpi = g0i + c.rho * g1i;
-        const double gdr = g0r + g1r / c.rho, gdi = g0i + g1i / c.rho;
-        const double dk0 = c.k0 * c.k0, dk1 = c.k1 * c.k1 / c.rho;
+        const double gpr = g0r + rho * g1r, gpi = g0i + rho * g1i;
+        const double gdr = g0r + g1r / rho, gdi = g0i + g1i / rho;
+        const double dk0 = c.k0 * c.k0, dk1 = k1 * k1 / rho;
         const double gkr = dk0 * g0r + dk1 * g1r, gki = dk0 * g0i + dk1 * g1i;
         const double dny = -(d0 * ns0 + d1 * ns1 + d2 * ns2);  // (y - x).n_y
         const double dnx = d0 * nt0 + d1 * nt1 + d2 * nt2;     // (x - y).n_x
@@ -288,6 +296,16 @@ dense_far_kernel(int nv, int nt, const double *__restrict__ verts, const int *__
                 if (vt[a] == vs[b]) live = false;  // touching: near field
     }
     const double *gt = tgeo + 16 * (size_t)(live ? t : 0), *gs = tgeo + 16 * (size_t)(live ? s : 0);
+    // disjoint objects: the pair's object material; interior terms only
+    // within one object
+    double k1 = c.k1, rho = c.rho, on1 = 1.0;
+    if (c.obj && live) {
+        const int ct = c.tcomp[t], cs = c.tcomp[s];
+        const ObjMat o = c.obj[ct];
+        k1 = o.k1;
+        rho = o.rho;
+        if (ct != cs) on1 = 0.0;
+    }
     double2 Z[13];
     for (int i = 0; i < 13; ++i) Z[i] = cd(0, 0);
     if (live) {
@@ -298,7 +316,7 @@ dense_far_kernel(int nv, int nt, const double *__restrict__ verts, const int *__
             X[k] = dense_bary(p, 0) * verts[3 * vt[0] + k] + dense_bary(p, 1) * verts[3 * vt[1] + k] +
                    dense_bary(p, 2) * verts[3 * vt[2] + k];
         const double scale = gt[0] * gs[0] * dense_w(p);
-        const double dk0 = c.k0 * c.k0, dk1 = c.k1 * c.k1 / c.rho;
+        const double dk0 = c.k0 * c.k0, dk1 = k1 * k1 / rho;
         for (int q = 0; q < 6; ++q) {
             const double b0 = dense_bary(q, 0), b1 = dense_bary(q, 1), b2 = dense_bary(q, 2);
             const double d0 = X[0] - (b0 * Vs[0][0] + b1 * Vs[1][0] + b2 * Vs[2][0]);
@@ -308,16 +326,18 @@ dense_far_kernel(int nv, int nt, const double *__restrict__ verts, const int *__
             const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2), ri = 1.0 / r;
             double s0, c0, s1, c1;
             sincos(c.k0 * r, &s0, &c0);
-            sincos(c.k1 * r, &s1, &c1);
-            const double kr0 = c.k0 * r, kr1 = c.k1 * r;
+            sincos(k1 * r, &s1, &c1);
+            s1 *= on1;
+            c1 *= on1;
+            const double kr0 = c.k0 * r, kr1 = k1 * r;
             const double fw = kInv4Pi * ri * w, f3 = fw * ri * ri;
             const double2 g0 = cd(c0 * fw, s0 * fw), g1 = cd(c1 * fw, s1 * fw);
             const double2 hs = cd((-c0 - kr0 * s0 - c1 - kr1 * s1) * f3, (kr0 * c0 - s0 + kr1 * c1 - s1) * f3);
-            const double2 gp = cadd(g0, cscale(g1, c.rho));
+            const double2 gp = cadd(g0, cscale(g1, rho));
             const double2 gk = cadd(cscale(g0, dk0), cscale(g1, dk1));
             const double2 hk = cscale(hs, d0 * gs[1] + d1 * gs[2] + d2 * gs[3]);  // -hs (y - x).n_y
             const double2 ht = cscale(hs, d0 * gt[1] + d1 * gt[2] + d2 * gt[3]);  //  hs (x - y).n_x
-            Z[12] = cadd(Z[12], cadd(g0, cscale(g1, 1.0 / c.rho)));
+            Z[12] = cadd(Z[12], cadd(g0, cscale(g1, 1.0 / rho)));
             const double bq[3] = {b0, b1, b2};
             for (int b = 0; b < 3; ++b) {
                 Z[b] = cadd(Z[b], cscale(gp, bq[b]));
@@ -466,7 +486,8 @@ int near_build(osrc_problem *pb, const std::vector<NearPair> &pairs,
     OSRC_CK(cudaMemcpyAsync(d_cptr.p, cptr.data(), cptr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     OSRC_CK(cudaMemcpyAsync(d_cidx.p, cidx.data(), cidx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     OSRC_CK(cudaMemcpyAsync(d_gl.p, gl, sizeof(gl), cudaMemcpyHostToDevice, st));
-    NearConst c{pb->p.k_ext, pb->p.k_int, pb->p.rho_ratio, pb->p.n_ss};
+    NearConst c{pb->p.k_ext, pb->p.k_int, pb->p.rho_ratio, pb->p.n_ss, pb->multi ? pb->d_obj.p : nullptr,
+                 pb->mesh->d_tcomp.p};
     const long long blocks = (np + NEAR_WARPS - 1) / NEAR_WARPS;
     if (blocks > 0) {
         near_ss_kernel<<<(unsigned)blocks, 32 * NEAR_WARPS, 0, st>>>(
@@ -491,7 +512,8 @@ int dense_assemble(osrc_problem *pb, cudaStream_t st) {
     const size_t n2 = 2 * (size_t)nv;
     OSRC_TRY(pb->d_dense.alloc(m->ctx, n2 * n2));
     OSRC_CK(cudaMemsetAsync(pb->d_dense.p, 0, n2 * n2 * sizeof(double2), st));
-    NearConst c{pb->p.k_ext, pb->p.k_int, pb->p.rho_ratio, pb->p.n_ss};
+    NearConst c{pb->p.k_ext, pb->p.k_int, pb->p.rho_ratio, pb->p.n_ss, pb->multi ? pb->d_obj.p : nullptr,
+                 pb->mesh->d_tcomp.p};
     const int folded = (nt + 1) / 2;
     if (folded > 65535) {
         osrc_set_error("dense assembly: too many triangles for the dense path");

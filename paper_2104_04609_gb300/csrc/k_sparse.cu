@@ -64,10 +64,14 @@ struct KrySys {
     const double2 *f;     // right-hand side
     double2 *x;           // solution
     int conj;             // 1: Hermitian CG, 0: COCG
+    // disjoint objects: row i uses beta * bscale[vcomp[i]] (S has no entries
+    // between objects, so the matrix stays complex symmetric); null: beta
+    const double2 *bscale;
 };
 
 struct KryBatch {
     int nsys;
+    const int *vcomp;  // object of each row (with KrySys::bscale)
     KrySys s[KRY_MAX_SYS];
 };
 
@@ -161,7 +165,8 @@ kry_kernel(KryBatch batch, int n, const int *__restrict__ ptr, const int *__rest
         double md = 0.0, sd = 0.0;
         for (int e = ptr[i]; e < ptr[i + 1]; ++e)
             if (col[e] == i) { md = M[e]; sd = S[e]; }
-        const double2 d = cadd(cscale(sy.alpha, md), cscale(sy.beta, sd));
+        const double2 bi = sy.bscale ? cmul(sy.beta, sy.bscale[batch.vcomp[i]]) : sy.beta;
+        const double2 d = cadd(cscale(sy.alpha, md), cscale(bi, sd));
         const double2 di = cdiv(cd(1.0, 0.0), d);
         const double2 b = sy.f[i];
         dinv[i] = di;
@@ -195,7 +200,8 @@ kry_kernel(KryBatch batch, int n, const int *__restrict__ ptr, const int *__rest
                     sp.x += se * pj.x;
                     sp.y += se * pj.y;
                 }
-                const double2 acc = cadd(cmul(sy.alpha, mp), cmul(sy.beta, sp));
+                const double2 bi = sy.bscale ? cmul(sy.beta, sy.bscale[batch.vcomp[i]]) : sy.beta;
+                const double2 acc = cadd(cmul(sy.alpha, mp), cmul(bi, sp));
                 q[i] = acc;
                 const double2 t = dot_term(p[i], acc, cj);
                 w0 += t.x;
@@ -268,6 +274,8 @@ __global__ void mass_spmv_kernel(int n, const int *__restrict__ ptr, const int *
 struct OsrcComb {
     int np;
     double2 ik, iik;  // i k and 1/(i k)
+    const double2 *ik_obj;  // disjoint objects: i k of each object (else ik)
+    const int *vcomp;
     double2 cu;       // C0 + sum_j A_j / B_j
     double2 g0;
     double2 a[16];    // A_j / B_j
@@ -285,8 +293,10 @@ __global__ void osrc_combine_kernel(int n, OsrcComb c, const double2 *__restrict
     for (int j = 0; j < c.np; ++j) a = csub(a, cmul(c.a[j], sol[(size_t)(1 + j) * n + i]));
     double2 b = cmul(c.g0, sol[(size_t)(c.np + 1) * n + i]);
     for (int j = 0; j < c.np; ++j) b = cadd(b, cmul(c.g[j], sol[(size_t)(c.np + 2 + j) * n + i]));
-    z[i] = cmul(c.ik, a);
-    z[n + i] = cmul(c.iik, b);
+    const double2 ik = c.ik_obj ? c.ik_obj[c.vcomp[i]] : c.ik;
+    const double2 iik = c.ik_obj ? cdiv(cd(1.0, 0.0), ik) : c.iik;
+    z[i] = cmul(ik, a);
+    z[n + i] = cmul(iik, b);
 }
 
 // Largest cluster the kernel may use: 16 CTAs (a non-portable size that the
@@ -459,11 +469,14 @@ int osrc_precond_fused_async(osrc_problem *pb, const double2 *y, double2 *z, cud
         return mass_solve_async(pb, w, z, false, st);
     }
     const double2 ke2 = cmul(pb->k_eps, pb->k_eps);
-    const double2 inv_ke2 = cdiv(cd(1.0, 0.0), ke2);
+    // disjoint objects: 1/k_eps^2 of each row's object via KrySys::bscale
+    const double2 inv_ke2 = pb->multi ? cd(1.0, 0.0) : cdiv(cd(1.0, 0.0), ke2);
+    const double2 *bscale = pb->multi ? pb->d_obj_ike.p + pb->mesh->ncomp : nullptr;
     double2 *sol = pb->d_kry_rhs.p + 2 * (size_t)n;
     const double2 *y1 = y, *y2 = y + n;
     KryBatch b{};
     b.nsys = 2 * np + 2;
+    b.vcomp = pb->mesh->d_vcomp.p;
     {   // M u1 = y1 (Hermitian CG)
         KrySys &s = b.s[0];
         s.alpha = cd(1.0, 0.0);
@@ -476,6 +489,7 @@ int osrc_precond_fused_async(osrc_problem *pb, const double2 *y, double2 *z, cud
         KrySys &s = b.s[1 + j];
         s.alpha = cd(1.0, 0.0);
         s.beta = cscale(cmul(pb->B[j], inv_ke2), -1.0);
+        s.bscale = bscale;
         s.f = y1;
         s.x = sol + (size_t)(1 + j) * n;
         s.conj = 0;
@@ -484,6 +498,7 @@ int osrc_precond_fused_async(osrc_problem *pb, const double2 *y, double2 *z, cud
         KrySys &s = b.s[np + 1];
         s.alpha = cd(1.0, 0.0);
         s.beta = cscale(inv_ke2, -1.0);
+        s.bscale = bscale;
         s.f = y2;
         s.x = sol + (size_t)(np + 1) * n;
         s.conj = 0;
@@ -492,6 +507,7 @@ int osrc_precond_fused_async(osrc_problem *pb, const double2 *y, double2 *z, cud
         KrySys &s = b.s[np + 2 + j];
         s.alpha = cd(1.0, 0.0);
         s.beta = cscale(cmul(pb->B[j], inv_ke2), -1.0);
+        s.bscale = bscale;
         s.f = y2;
         s.x = sol + (size_t)(np + 2 + j) * n;
         s.conj = 0;
@@ -501,6 +517,8 @@ int osrc_precond_fused_async(osrc_problem *pb, const double2 *y, double2 *z, cud
     c.np = np;
     c.ik = cd(0.0, pb->k_osrc);
     c.iik = cd(0.0, -1.0 / pb->k_osrc);
+    c.ik_obj = pb->multi ? pb->d_obj_ike.p : nullptr;
+    c.vcomp = pb->mesh->d_vcomp.p;
     double2 cu = pb->C0;
     for (int j = 0; j < np; ++j) {
         c.a[j] = cdiv(pb->A[j], pb->B[j]);

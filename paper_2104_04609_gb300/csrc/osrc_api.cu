@@ -203,9 +203,43 @@ extern "C" int osrc_mesh_create(osrc_ctx *ctx, const double *verts, int32_t nv,
             }
         }
     m->mean_edge = cnt ? sum / cnt : 0.0;
+    // objects: union-find over vertices joined by triangle edges, numbered in
+    // the order of each object's first triangle
+    {
+        std::vector<int> par(nv);
+        for (int i = 0; i < nv; ++i) par[i] = i;
+        auto root = [&](int a) {
+            while (par[a] != a) a = par[a] = par[par[a]];
+            return a;
+        };
+        for (int t = 0; t < nt; ++t)
+            for (int k = 1; k < 3; ++k) {
+                const int a = root(tris[3 * t]), b = root(tris[3 * t + k]);
+                if (a != b) par[std::max(a, b)] = std::min(a, b);
+            }
+        std::vector<int> id(nv, -1);
+        m->tcomp.assign(nt, 0);
+        int nc = 0;
+        for (int t = 0; t < nt; ++t) {
+            const int r = root(tris[3 * t]);
+            if (id[r] < 0) id[r] = nc++;
+            m->tcomp[t] = id[r];
+        }
+        m->ncomp = nc;
+        m->vcomp.assign(nv, 0);
+        for (int v = 0; v < nv; ++v) m->vcomp[v] = id[root(v)];
+        m->comp_tbeg.assign(nc + 1, 0);
+        for (int t = 0; t < nt; ++t) m->comp_tbeg[m->tcomp[t] + 1]++;
+        for (int c = 0; c < nc; ++c) m->comp_tbeg[c + 1] += m->comp_tbeg[c];
+        m->tri_order.assign(nt, 0);
+        std::vector<int> fill(m->comp_tbeg.begin(), m->comp_tbeg.end() - 1);
+        for (int t = 0; t < nt; ++t) m->tri_order[fill[m->tcomp[t]]++] = t;
+    }
     int s;
     if ((s = m->d_verts.alloc(ctx, 3 * (size_t)nv)) || (s = m->d_tris.alloc(ctx, 3 * (size_t)nt)) ||
-        (s = m->d_vt_ptr.alloc(ctx, nv + 1)) || (s = m->d_vt_idx.alloc(ctx, 3 * (size_t)nt))) {
+        (s = m->d_vt_ptr.alloc(ctx, nv + 1)) || (s = m->d_vt_idx.alloc(ctx, 3 * (size_t)nt)) ||
+        (s = m->d_tcomp.alloc(ctx, nt)) || (s = m->d_vcomp.alloc(ctx, nv)) ||
+        (s = m->d_tri_order.alloc(ctx, nt))) {
         delete m;
         return s;
     }
@@ -213,6 +247,9 @@ extern "C" int osrc_mesh_create(osrc_ctx *ctx, const double *verts, int32_t nv,
     if (e == cudaSuccess) e = cudaMemcpy(m->d_tris.p, tris, 3 * (size_t)nt * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->d_vt_ptr.p, m->vt_ptr.data(), (nv + 1) * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->d_vt_idx.p, m->vt_idx.data(), 3 * (size_t)nt * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_tcomp.p, m->tcomp.data(), nt * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_vcomp.p, m->vcomp.data(), nv * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_tri_order.p, m->tri_order.data(), nt * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         osrc_set_error(std::string("mesh upload: ") + cudaGetErrorString(e));
         delete m;
@@ -224,6 +261,7 @@ extern "C" int osrc_mesh_create(osrc_ctx *ctx, const double *verts, int32_t nv,
 
 extern "C" void osrc_mesh_destroy(osrc_mesh *m) { delete m; }
 extern "C" double osrc_mesh_mean_edge(const osrc_mesh *m) { return m ? m->mean_edge : 0.0; }
+extern "C" int osrc_mesh_objects(const osrc_mesh *m) { return m ? m->ncomp : 0; }
 
 // ---------------------------------------------------------------------------
 // problem set-up: topology on the host, numerics on the device
@@ -292,9 +330,35 @@ void pade_coefficients(int np, double theta, std::complex<double> &C0,
 
 }  // namespace
 
+static int problem_create(osrc_mesh *mesh, const osrc_params *prm, const double *k_int_obj,
+                          const double *rho_obj, osrc_problem **out, void *stream);
+
 extern "C" int osrc_problem_create(osrc_mesh *mesh, const osrc_params *prm, osrc_problem **out,
                                    void *stream) {
     if (!mesh || !prm || !out) return OSRC_INVALID_ARG;
+    std::vector<double> k(mesh->ncomp, prm->k_int), r(mesh->ncomp, prm->rho_ratio);
+    return problem_create(mesh, prm, k.data(), r.data(), out, stream);
+}
+
+extern "C" int osrc_problem_create_objects(osrc_mesh *mesh, const osrc_params *prm, int nobj,
+                                           const double *k_int, const double *rho_ratio, osrc_problem **out,
+                                           void *stream) {
+    if (!mesh || !prm || !out || !k_int || !rho_ratio) return OSRC_INVALID_ARG;
+    if (nobj != mesh->ncomp) {
+        osrc_set_error("osrc_problem_create_objects: nobj differs from the mesh's number of objects");
+        return OSRC_INVALID_ARG;
+    }
+    for (int m = 0; m < nobj; ++m)
+        if (!(k_int[m] > 0.0) || !std::isfinite(k_int[m]) || !(rho_ratio[m] > 0.0) || !std::isfinite(rho_ratio[m]))
+            return OSRC_INVALID_ARG;
+    osrc_params p = *prm;
+    p.k_int = k_int[0];
+    p.rho_ratio = rho_ratio[0];
+    return problem_create(mesh, &p, k_int, rho_ratio, out, stream);
+}
+
+static int problem_create(osrc_mesh *mesh, const osrc_params *prm, const double *k_int_obj,
+                          const double *rho_obj, osrc_problem **out, void *stream) {
     *out = nullptr;
     const osrc_params &p = *prm;
     if (!(p.k_ext > 0.0) || !(p.k_int > 0.0) || !std::isfinite(p.k_ext) || !std::isfinite(p.k_int) ||
@@ -319,6 +383,38 @@ extern "C" int osrc_problem_create(osrc_mesh *mesh, const osrc_params *prm, osrc
     const int nv = pb->nv, nt = pb->nt;
     const int *tris = mesh->tris.data();
     do {
+        // ---- per-object materials (one object: the single-material path) -------
+        {
+            const double R = p.damping_R > 0.0 ? p.damping_R : mesh->mean_edge;
+            pb->multi = mesh->ncomp > 1;
+            pb->obj.resize(mesh->ncomp);
+            std::vector<FarObj> fo(mesh->ncomp);
+            std::vector<double2> ike(2 * (size_t)mesh->ncomp);
+            for (int m = 0; m < mesh->ncomp; ++m) {
+                ObjMat &o = pb->obj[m];
+                o.k1 = k_int_obj[m];
+                o.rho = rho_obj[m];
+                o.k_osrc = p.osrc_side == 1 ? o.k1 : p.k_ext;
+                const std::complex<double> ke =
+                    o.k_osrc * (1.0 + std::complex<double>(0.0, 0.4) * std::pow(o.k_osrc * R, -2.0 / 3.0));
+                o.k_eps = cd(ke.real(), ke.imag());
+                const std::complex<double> inv = 1.0 / (ke * ke);
+                ike[m] = cd(0.0, o.k_osrc);                         // i k_osrc
+                ike[mesh->ncomp + m] = cd(inv.real(), inv.imag());  // 1 / k_eps^2
+                const double q = o.k1 * 0.15915494309189533577;
+                fo[m] = FarObj{(float)o.k1, (float)-o.k1, (float)o.rho, (float)(1.0 / o.rho),
+                               (float)(o.k1 * o.k1 / o.rho), (float)q, (float)(q - (double)(float)q), 0.f};
+            }
+            if ((s = pb->d_obj.alloc(ctx, mesh->ncomp)) || (s = pb->d_fobj.alloc(ctx, mesh->ncomp)) ||
+                (s = pb->d_obj_ike.alloc(ctx, 2 * (size_t)mesh->ncomp)))
+                break;
+            if (cudaMemcpy(pb->d_obj.p, pb->obj.data(), mesh->ncomp * sizeof(ObjMat), cudaMemcpyHostToDevice) ||
+                cudaMemcpy(pb->d_fobj.p, fo.data(), mesh->ncomp * sizeof(FarObj), cudaMemcpyHostToDevice) ||
+                cudaMemcpy(pb->d_obj_ike.p, ike.data(), ike.size() * sizeof(double2), cudaMemcpyHostToDevice)) {
+                s = OSRC_CUDA_ERROR;
+                break;
+            }
+        }
         if ((s = far_setup_geometry(pb, st))) break;
         // ---- touching triangle pairs ----------------------------------------
         std::vector<NearPair> pairs;
@@ -788,6 +884,11 @@ int problem_clone(osrc_problem *m, osrc_problem **out) {
     c->A = m->A;
     c->B = m->B;
     c->g = m->g;
+    c->multi = m->multi;
+    c->obj = m->obj;
+    c->d_obj.borrow(m->d_obj);
+    c->d_fobj.borrow(m->d_fobj);
+    c->d_obj_ike.borrow(m->d_obj_ike);
     c->d_pt.borrow(m->d_pt);
     c->d_poff.borrow(m->d_poff);
     c->d_cen.borrow(m->d_cen);

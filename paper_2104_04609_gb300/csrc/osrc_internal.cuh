@@ -100,8 +100,28 @@ struct osrc_mesh {
     std::vector<int> tris;           // nt x 3
     std::vector<int> vt_ptr, vt_idx; // vertex -> (3*triangle + local) incidence
     double mean_edge = 0.0;
+    // objects: connected components (triangles sharing vertices), numbered in
+    // the order of their first triangle
+    int ncomp = 1;
+    std::vector<int> tcomp, vcomp;   // per triangle / per vertex object
+    std::vector<int> tri_order;      // triangles sorted by object (stable)
+    std::vector<int> comp_tbeg;      // [ncomp + 1] ranges of tri_order
     DBuf<double> d_verts;
     DBuf<int> d_tris, d_vt_ptr, d_vt_idx;
+    DBuf<int> d_tcomp, d_vcomp, d_tri_order;
+};
+
+// Material of one object (disjoint objects, Sec. 2.2): interior wavenumber,
+// density ratio rho_m / rho_0, OSRC wavenumber and its damped version.
+struct ObjMat {
+    double k1, rho, k_osrc, pad;
+    double2 k_eps;
+};
+
+// FP32 constants of one object for the far kernel (duplicated-pair form is
+// built per thread): k1, -k1, rho, 1/rho, k1^2/rho, k1/(2 pi) as float-float.
+struct FarObj {
+    float k1, nk1, rho, irho, dk1, k1h, k1l, pad;
 };
 
 // Touching triangle pair for the Sauter-Schwab kernel.
@@ -167,9 +187,16 @@ struct osrc_problem {
     DBuf<double> d_scalars;   // reduction scratch
     DBuf<double2> d_w, d_y, d_x1, d_b1, d_cvec;  // 2nv vectors
     double *h_res = nullptr;  // pinned host block: doubles [0, 16), then ints (inner status)
+    // ---- disjoint objects with their own materials --------------------------------
+    bool multi = false;          // more than one object: interior terms within objects only
+    std::vector<ObjMat> obj;     // [ncomp]
+    DBuf<ObjMat> d_obj;
+    DBuf<FarObj> d_fobj;
+    DBuf<double2> d_obj_ike;     // [2][ncomp]: i k_osrc, then 1 / k_eps^2 per object (OSRC)
     // ---- field evaluation off the surface (k_field.cu) -------------------------
     DBuf<double4> d_fsrc;     // [6nt][3] rule points, normals, densities
     DBuf<int> d_freg;         // region scratch when the caller passes none
+    DBuf<int> d_fobeg;        // [objects + 1] source-point ranges of the objects
     // ---- far-kernel event timing -------------------------------------------------
     bool prof_on = false, prof_pending = false;
     cudaEvent_t prof_ev[2] = {nullptr, nullptr};
