@@ -66,6 +66,8 @@ def parse():
                     help="right-hand sides of the same workload solved matrix-free for comparison")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the far-field apply on the 80000-vertex bumpy ellipsoid")
+    ap.add_argument("--no-objects", action="store_true",
+                    help="skip the four-sphere multiple-scattering solve")
     ap.add_argument("--precond-sweep", action="store_true",
                     help="instead of the benchmark: GMRES iterations vs frequency on the "
                          "10242-vertex sphere for the OSRC, mass-only and Calderon preconditioners")
@@ -327,6 +329,8 @@ def run_ours(args, D):
         out["dense_batched"] = run_dense(args.dense_rhs, args.dense_matfree_rhs, D.local)
     if not args.no_large and D.rank == 0:
         out["large"] = run_large(D.local)
+    if not args.no_objects and D.rank == 0:
+        out["four_spheres"] = run_four_spheres(D.local)
     if args.serve_requests > 0 and D.rank == 0:
         out["serving"] = run_serving(args.serve_requests, D.local)
         out["serving_batched"] = run_serving(args.serve_requests, D.local, batched=True)
@@ -606,6 +610,58 @@ def run_large(device):
         }
     finally:
         S.close()
+
+
+# --------------------------------------------------------------------------
+# four spheres (Sec. 3.5): radius 1 (5 mm), centres (+-3, +-1.5, 0), two
+# fat-like and two bone-like interiors, water outside, 0.5 and 1 MHz
+# --------------------------------------------------------------------------
+C_WATER, C_FAT, C_BONE = 1500.0, 1450.0, 3600.0
+RHO_FAT, RHO_BONE = 0.95, 1.9
+
+
+def four_spheres(level=4):
+    import numpy as np
+
+    from paper_2104_04609_gb300.inputs import icosphere
+
+    v, t = icosphere(level)
+    centres = [(-3.0, -1.5, 0.0), (-3.0, 1.5, 0.0), (3.0, -1.5, 0.0), (3.0, 1.5, 0.0)]
+    V = np.vstack([v + np.array(c) for c in centres])
+    T = np.vstack([t + i * len(v) for i in range(4)])
+    return V, T
+
+
+def run_four_spheres(device):
+    """Multiple scattering at four disjoint spheres (level-4 icospheres, 10248
+    vertices in all): the spheres at x < 0 fat-like (c 1450 m/s, rho ratio
+    0.95), at x > 0 bone-like (c 3600 m/s, rho ratio 1.9), k_int = k_ext c_water
+    / c_object; plane wave along +x; GMRES to 1e-5."""
+    import torch
+
+    from paper_2104_04609_gb300 import binding as B
+
+    V, T = four_spheres()
+    res = []
+    for f_mhz in (0.5, 1.0):
+        k0 = 2.0 * math.pi * f_mhz * 1e6 / C_WATER * 5e-3  # radius 5 mm = 1
+        kin = [k0 * C_WATER / C_FAT] * 2 + [k0 * C_WATER / C_BONE] * 2
+        rho = [RHO_FAT] * 2 + [RHO_BONE] * 2
+        S = B.Solver(V, T, k0, None, None, device=device, objects=(kin, rho))
+        try:
+            b = S.rhs_planewave([[1.0, 0.0, 0.0]])
+            S.solve(b, tol=TOL, maxit=1000)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x, info = S.solve(b, tol=TOL, maxit=1000)
+            torch.cuda.synchronize()
+            res.append({"frequency_mhz": f_mhz, "k_ext": k0, "iterations": info.iterations,
+                        "solve_s": time.perf_counter() - t0, "true_residual": info.true_residual})
+        finally:
+            S.close()
+    return {"workload": "four spheres (radius 1 = 5 mm) at (+-3, +-1.5, 0), level-4 icospheres, "
+                        "10248 vertices; two fat-like, two bone-like; plane wave +x; tol 1e-5",
+            "runs": res}
 
 
 # --------------------------------------------------------------------------
