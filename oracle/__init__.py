@@ -170,11 +170,19 @@ def assemble_rows(verts, tris, k, rows, nss=6, part=3):
     return m[:, 0], m[:, 1], m[:, 2], m[:, 3]
 
 
-def pmchwt_matrix(verts, tris, k_ext, k_int, rho_ratio, nss=6, part=3):
+def pmchwt_matrix(verts, tris, k_ext, k_int, rho_ratio, nss=6, part=3, formulation="pmchwt"):
     """Permuted PMCHWT matrix of Sec. 2.7 acting on [psi; phi]:
-        [[V0 + rho V1, -K0 - K1], [T0 + T1, D0 + D1 / rho]],  rho = rho_int/rho_ext."""
+        [[V0 + rho V1, -K0 - K1], [T0 + T1, D0 + D1 / rho]],  rho = rho_int/rho_ext.
+    formulation "muller": the difference of the exterior and interior
+    Calderon equations plus the identity (Sec. 2.2, Mueller), in the same
+    ordering:  [[V0 - rho V1, -K0 + K1 + M], [T0 - T1 + M, D0 - D1 / rho]]
+    (M the P1 mass matrix; part 2 carries it, as the touching pairs do)."""
     V0, K0, T0, D0 = assemble(verts, tris, k_ext, nss, part)
     V1, K1, T1, D1 = assemble(verts, tris, k_int, nss, part)
+    if formulation == "muller":
+        Md = mass_stiffness(verts, tris)[0].toarray() if part & 2 else 0.0
+        return np.block([[V0 - rho_ratio * V1, -K0 + K1 + Md],
+                         [T0 - T1 + Md, D0 - D1 / rho_ratio]])
     return np.block([[V0 + rho_ratio * V1, -K0 - K1],
                      [T0 + T1, D0 + D1 / rho_ratio]])
 
@@ -202,7 +210,7 @@ def components(tris):
     return vcomp[t[:, 0]], vcomp
 
 
-def pmchwt_matrix_objects(verts, tris, k_ext, k_int, rho_ratio, nss=6, part=3):
+def pmchwt_matrix_objects(verts, tris, k_ext, k_int, rho_ratio, nss=6, part=3, formulation="pmchwt"):
     """Permuted PMCHWT matrix of disjoint objects (Sec. 2.2, multiple
     scattering): object m has its own k_int[m] and rho_ratio[m]; the interior
     operators act within each object only (diagonal blocks A_0,mm + A^_m),
@@ -210,14 +218,18 @@ def pmchwt_matrix_objects(verts, tris, k_ext, k_int, rho_ratio, nss=6, part=3):
         [[V0 + sum_m rho_m V_m|mm, -K0 - sum_m K_m|mm],
          [T0 + sum_m T_m|mm,        D0 + sum_m D_m|mm / rho_m]]."""
     _, vc = components(tris)
+    sg = -1.0 if formulation == "muller" else 1.0
     V, K, T, D = (a.copy() for a in assemble(verts, tris, k_ext, nss, part))
     for m in range(vc.max() + 1):
         sel = np.outer(vc == m, vc == m)
         Vm, Km, Tm, Dm = assemble(verts, tris, k_int[m], nss, part)
-        V = V + rho_ratio[m] * np.where(sel, Vm, 0)
-        K = K + np.where(sel, Km, 0)
-        T = T + np.where(sel, Tm, 0)
-        D = D + np.where(sel, Dm, 0) / rho_ratio[m]
+        V = V + sg * rho_ratio[m] * np.where(sel, Vm, 0)
+        K = K + sg * np.where(sel, Km, 0)
+        T = T + sg * np.where(sel, Tm, 0)
+        D = D + sg * np.where(sel, Dm, 0) / rho_ratio[m]
+    if formulation == "muller" and part & 2:
+        Md = mass_stiffness(verts, tris)[0].toarray()
+        return np.block([[V, -K + Md], [T + Md, D]])
     return np.block([[V, -K], [T, D]])
 
 
@@ -502,7 +514,7 @@ class Problem:
 
     def __init__(self, verts, tris, k_ext, k_int, rho_ratio, n_pade=4,
                  theta=math.pi / 3, damping_R=None, osrc_side=1, nss=6, precond="osrc",
-                 objects=None):
+                 objects=None, formulation="pmchwt"):
         """objects = (k_int list, rho_ratio list): one material per connected
         component (disjoint objects); k_int and rho_ratio are then unused."""
         self.verts = np.asarray(verts, dtype=np.float64)
@@ -515,12 +527,14 @@ class Problem:
         if objects is None:
             self.k_osrc = k_int if osrc_side == 1 else k_ext
             self.k_eps = damped_wavenumber(self.k_osrc, self.R)
-            self.B = pmchwt_matrix(self.verts, self.tris, k_ext, k_int, rho_ratio, nss)
+            self.B = pmchwt_matrix(self.verts, self.tris, k_ext, k_int, rho_ratio, nss,
+                                   formulation=formulation)
         else:
             _, self.vcomp = components(self.tris)
             kl = list(objects[0])
             self.k_osrc_obj = [kl[m] if osrc_side == 1 else k_ext for m in range(len(kl))]
-            self.B = pmchwt_matrix_objects(self.verts, self.tris, k_ext, kl, list(objects[1]), nss)
+            self.B = pmchwt_matrix_objects(self.verts, self.tris, k_ext, kl, list(objects[1]), nss,
+                                           formulation=formulation)
         self.M, self.S = mass_stiffness(self.verts, self.tris)
         self._solver = _ShiftedSolver(self.M, self.S)
         self.precond_kind = precond
