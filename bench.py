@@ -947,7 +947,8 @@ def large_sweep(nv, device=0, maxit=600):
 def precond_sweep(device=0, maxit=800):
     """Iteration counts of the paper's comparison (Sec. 3.3): unit sphere
     (level-5 icosphere, 10242 vertices), k_int = 1.3 k_ext, rho 1.5, plane wave,
-    tol 1e-5, for OSRC, mass-only and Calderon preconditioning."""
+    tol 1e-5, for PMCHWT with OSRC, mass-only and Calderon preconditioning and
+    the Mueller formulation with mass preconditioning."""
     import torch
 
     import __graft_entry__
@@ -957,11 +958,12 @@ def precond_sweep(device=0, maxit=800):
     from paper_2104_04609_gb300.inputs import icosphere
 
     v, t = icosphere(5)
-    kinds = (("osrc", B.OSRC_PRECOND_OSRC), ("mass", B.OSRC_PRECOND_MASS),
-             ("calderon", B.OSRC_PRECOND_CALDERON))
+    kinds = (("osrc", B.OSRC_PRECOND_OSRC, B.OSRC_PMCHWT), ("mass", B.OSRC_PRECOND_MASS, B.OSRC_PMCHWT),
+             ("calderon", B.OSRC_PRECOND_CALDERON, B.OSRC_PMCHWT),
+             ("muller", B.OSRC_PRECOND_MASS, B.OSRC_MULLER))
     for k0 in (5.0, 10.0, 20.0):
-        for name, code in kinds:
-            S = B.Solver(v, t, k0, 1.3 * k0, 1.5, device=device, precond=code)
+        for name, code, form in kinds:
+            S = B.Solver(v, t, k0, 1.3 * k0, 1.5, device=device, precond=code, formulation=form)
             try:
                 b = S.rhs_planewave([[0.0, 0.0, 1.0]])
                 torch.cuda.synchronize()

@@ -81,7 +81,18 @@ typedef struct osrc_params {
     double inner_tol;    /* relative residual of the inner mass / shifted solves (<= 1e-8) */
     int inner_maxit;     /* iteration cap of the inner solves */
     int precond;         /* preconditioner P of the GMRES solve: OSRC_PRECOND_* */
+    int formulation;     /* OSRC_PMCHWT (default) or OSRC_MULLER */
 } osrc_params;
+
+/* Boundary integral formulation (Sec. 2.2), both in the permuted ordering
+ * [psi; phi] with the same right-hand side:
+ *   OSRC_PMCHWT: [[V0 + rho V1, -K0 - K1], [T0 + T1, D0 + D1/rho]] (sum of the
+ *                exterior and interior Calderon equations, first kind);
+ *   OSRC_MULLER: [[V0 - rho V1, -K0 + K1 + M], [T0 - T1 + M, D0 - D1/rho]]
+ *                (their difference plus the identity, M the P1 mass matrix;
+ *                second kind without density contrast).
+ * With several objects the interior terms are those of each object. */
+enum { OSRC_PMCHWT = 0, OSRC_MULLER = 1 };
 
 /* Preconditioners of the matrix-free and FP64 dense GMRES solves; GMRES runs
  * on P B x = P b with, for a weak-form vector y,
@@ -96,7 +107,7 @@ enum { OSRC_PRECOND_OSRC = 0, OSRC_PRECOND_MASS = 1, OSRC_PRECOND_CALDERON = 2 }
 
 /* Fills p with the paper's defaults: n_pade 4, theta pi/3, interior OSRC
  * wavenumber, R = mean edge length, n_ss 4, FP32 matrix-free, inner_tol 1e-10,
- * OSRC preconditioner. */
+ * OSRC preconditioner, PMCHWT formulation. */
 void osrc_params_default(osrc_params *p);
 
 /* Result record of osrc_gmres_solve (per right-hand side: the last one). */

@@ -34,6 +34,8 @@ OSRC_PART_FAR = 1
 OSRC_PART_NEAR = 2
 OSRC_PART_ALL = 3
 OSRC_HOST_BUFFERS = 1
+OSRC_PMCHWT = 0
+OSRC_MULLER = 1
 OSRC_PRECOND_OSRC = 0
 OSRC_PRECOND_MASS = 1
 OSRC_PRECOND_CALDERON = 2
@@ -56,6 +58,7 @@ class osrc_params(ctypes.Structure):
         ("osrc_side", ctypes.c_int), ("n_ss", ctypes.c_int),
         ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double),
         ("inner_maxit", ctypes.c_int), ("precond", ctypes.c_int),
+        ("formulation", ctypes.c_int),
     ]
 
 

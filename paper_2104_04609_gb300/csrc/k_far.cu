@@ -367,8 +367,9 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
 // run per 64-triangle tile, then tile sums are added to running sums.
 // CENTRED: pt holds offsets from the test-triangle centroid and cen the
 // float-float centroids (see far_pair2).
-// MULTI: disjoint objects (Sec. 2.2); the interior constants are the test
-// triangle's object's, and interior terms vanish for sources on other objects.
+// MULTI: disjoint objects (Sec. 2.2) or the Mueller formulation; the interior
+// constants are the test triangle's object's, interior terms vanish for
+// sources on other objects and change sign for Mueller.
 template <bool CENTRED, bool MULTI>
 __global__ void __launch_bounds__(FAR_THREADS, 4)
 far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
@@ -401,6 +402,7 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
     FarConst2 c = c0;
     float4 kff = kff0;
     int ct = 0;
+    float sgn = 1.f;  // sign of the interior terms (-1: Mueller)
     if (MULTI) {
         ct = tcomp[tau];
         const FarObj o = fobj[ct];
@@ -411,6 +413,7 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
         c.dk1 = dup2(o.dk1);
         kff.z = o.k1h;
         kff.w = o.k1l;
+        sgn = o.sgn;
     }
     float4 cth = make_float4(0.f, 0.f, 0.f, 0.f), ctl = cth;
     if (CENTRED) {
@@ -461,7 +464,7 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
             }
             const float nxnyn = n4.x * mns.x + n4.y * mns.y + n4.z * mns.z;  // -n_x.n_y
             A.t1r = A.t1i = A.ur = A.ui = A.t3r = A.t3i = make_float2(0.f, 0.f);
-            const f2 m1 = dup2(MULTI && shComp[s] != ct ? 0.f : 1.f);
+            const f2 m1 = dup2(MULTI ? (shComp[s] != ct ? 0.f : sgn) : 1.f);
 #pragma unroll
             for (int q = 0; q < 6; ++q)
                 far_pair2<CENTRED, MULTI>(X, Y, Z, &shP[30 * s + 5 * q], shP5[6 * s + q], mnx, mny, mnz,
@@ -652,7 +655,7 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
         const int *tc = m->d_tcomp.p;
         const FarObj *fo = pb->d_fobj.p;
         float *prt = pb->d_part.p;
-        if (pb->far_reduce && pb->multi)
+        if (pb->far_reduce && pb->far_obj)
             far_kernel<true, true><<<grid, FAR_THREADS, 0, st>>>(pts, pb->d_cen.p, pb->d_tn.p, pb->d_tv.p, pb->d_sP.p,
                                                                  pb->d_sP5.p, pb->d_sC.p, nt, npts, tps, c, kff, tc,
                                                                  fo, prt);
@@ -660,7 +663,7 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
             far_kernel<true, false><<<grid, FAR_THREADS, 0, st>>>(pts, pb->d_cen.p, pb->d_tn.p, pb->d_tv.p, pb->d_sP.p,
                                                                   pb->d_sP5.p, pb->d_sC.p, nt, npts, tps, c, kff, tc,
                                                                   fo, prt);
-        else if (pb->multi)
+        else if (pb->far_obj)
             far_kernel<false, true><<<grid, FAR_THREADS, 0, st>>>(pts, pb->d_cen.p, pb->d_tn.p, pb->d_tv.p, pb->d_sP.p,
                                                                   pb->d_sP5.p, pb->d_sC.p, nt, npts, tps, c, kff, tc,
                                                                   fo, prt);

@@ -82,6 +82,7 @@ struct NearConst {
     int nss;
     const ObjMat *obj;  // disjoint objects: material per object (else k1, rho)
     const int *tcomp;   // object of each triangle
+    double sgn;         // sign of the interior terms: +1 PMCHWT, -1 Mueller
 };
 
 constexpr int NEAR_WARPS = 4;
@@ -168,6 +169,8 @@ near_ss_kernel(const NearPair *__restrict__ pairs, long long npairs,
         double s0, c0, s1, c1;
         sincos(c.k0 * r, &s0, &c0);
         sincos(k1 * r, &s1, &c1);
+        s1 *= c.sgn;
+        c1 *= c.sgn;
         const double kr0 = c.k0 * r, kr1 = k1 * r;
         const double f = kInv4Pi * ri, f3 = f * ri * ri;
         const double g0r = c0 * f, g0i = s0 * f, g1r = c1 * f, g1i = s1 * f;
@@ -298,7 +301,7 @@ dense_far_kernel(int nv, int nt, const double *__restrict__ verts, const int *__
     const double *gt = tgeo + 16 * (size_t)(live ? t : 0), *gs = tgeo + 16 * (size_t)(live ? s : 0);
     // disjoint objects: the pair's object material; interior terms only
     // within one object
-    double k1 = c.k1, rho = c.rho, on1 = 1.0;
+    double k1 = c.k1, rho = c.rho, on1 = c.sgn;
     if (c.obj && live) {
         const int ct = c.tcomp[t], cs = c.tcomp[s];
         const ObjMat o = c.obj[ct];
@@ -487,7 +490,7 @@ int near_build(osrc_problem *pb, const std::vector<NearPair> &pairs,
     OSRC_CK(cudaMemcpyAsync(d_cidx.p, cidx.data(), cidx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     OSRC_CK(cudaMemcpyAsync(d_gl.p, gl, sizeof(gl), cudaMemcpyHostToDevice, st));
     NearConst c{pb->p.k_ext, pb->p.k_int, pb->p.rho_ratio, pb->p.n_ss, pb->multi ? pb->d_obj.p : nullptr,
-                 pb->mesh->d_tcomp.p};
+                 pb->mesh->d_tcomp.p, pb->p.formulation == OSRC_MULLER ? -1.0 : 1.0};
     const long long blocks = (np + NEAR_WARPS - 1) / NEAR_WARPS;
     if (blocks > 0) {
         near_ss_kernel<<<(unsigned)blocks, 32 * NEAR_WARPS, 0, st>>>(
@@ -513,7 +516,7 @@ int dense_assemble(osrc_problem *pb, cudaStream_t st) {
     OSRC_TRY(pb->d_dense.alloc(m->ctx, n2 * n2));
     OSRC_CK(cudaMemsetAsync(pb->d_dense.p, 0, n2 * n2 * sizeof(double2), st));
     NearConst c{pb->p.k_ext, pb->p.k_int, pb->p.rho_ratio, pb->p.n_ss, pb->multi ? pb->d_obj.p : nullptr,
-                 pb->mesh->d_tcomp.p};
+                 pb->mesh->d_tcomp.p, pb->p.formulation == OSRC_MULLER ? -1.0 : 1.0};
     const int folded = (nt + 1) / 2;
     if (folded > 65535) {
         osrc_set_error("dense assembly: too many triangles for the dense path");
@@ -534,6 +537,38 @@ int dense_assemble(osrc_problem *pb, cudaStream_t st) {
 int dense_apply(osrc_problem *pb, const double2 *x, double2 *y, cudaStream_t st) {
     const int n = 2 * pb->nv;
     dense_gemv_kernel<<<(n + 7) / 8, 256, 0, st>>>(n, pb->d_dense.p, x, y);
+    pb->launches++;
+    OSRC_CK(cudaGetLastError());
+    return OSRC_OK;
+}
+
+// Mueller formulation: the identity blocks, + M_ij added to the (1,2) and
+// (2,1) entries of the touching-pair CSR (vertices sharing a triangle are
+// touching, so every mass entry has a place there).  One thread per row.
+__global__ void near_add_mass_kernel(int nv, const int *__restrict__ mptr, const int *__restrict__ mcol,
+                                     const double *__restrict__ M, const int *__restrict__ nptr,
+                                     const int *__restrict__ ncol, double2 *__restrict__ val) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    for (int e = mptr[i]; e < mptr[i + 1]; ++e) {
+        const int j = mcol[e];
+        int lo = nptr[i], hi = nptr[i + 1] - 1;
+        while (lo < hi) {  // first position with ncol >= j (rows are sorted)
+            const int mid = (lo + hi) >> 1;
+            if (ncol[mid] < j) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo < nptr[i + 1] && ncol[lo] == j) {
+            val[4 * (size_t)lo + 1].x += M[e];
+            val[4 * (size_t)lo + 2].x += M[e];
+        }
+    }
+}
+
+int near_add_mass(osrc_problem *pb, cudaStream_t st) {
+    const int nv = pb->nv;
+    near_add_mass_kernel<<<(nv + 127) / 128, 128, 0, st>>>(nv, pb->d_ms_ptr.p, pb->d_ms_col.p, pb->d_M.p,
+                                                           pb->d_nr_ptr.p, pb->d_nr_col.p, pb->d_nr_val.p);
     pb->launches++;
     OSRC_CK(cudaGetLastError());
     return OSRC_OK;

@@ -71,6 +71,7 @@ extern "C" void osrc_params_default(osrc_params *p) {
     p->inner_tol = 1e-10;
     p->inner_maxit = 2000;
     p->precond = OSRC_PRECOND_OSRC;
+    p->formulation = OSRC_PMCHWT;
 }
 
 // ---------------------------------------------------------------------------
@@ -366,6 +367,7 @@ static int problem_create(osrc_mesh *mesh, const osrc_params *prm, const double 
         p.n_ss < 2 || p.n_ss > 12 || !(p.inner_tol > 0.0) || p.inner_tol > 1e-4 ||
         p.inner_maxit < 1 || (p.precision != OSRC_FP32_MATFREE && p.precision != OSRC_FP64_DENSE) ||
         p.precond < OSRC_PRECOND_OSRC || p.precond > OSRC_PRECOND_CALDERON ||
+        (p.formulation != OSRC_PMCHWT && p.formulation != OSRC_MULLER) ||
         (p.osrc_side != 0 && p.osrc_side != 1) || !std::isfinite(p.theta)) {
         osrc_set_error("invalid problem parameters");
         return OSRC_INVALID_ARG;
@@ -387,6 +389,8 @@ static int problem_create(osrc_mesh *mesh, const osrc_params *prm, const double 
         {
             const double R = p.damping_R > 0.0 ? p.damping_R : mesh->mean_edge;
             pb->multi = mesh->ncomp > 1;
+            pb->far_obj = pb->multi || p.formulation == OSRC_MULLER;
+            const float sgn = p.formulation == OSRC_MULLER ? -1.f : 1.f;
             pb->obj.resize(mesh->ncomp);
             std::vector<FarObj> fo(mesh->ncomp);
             std::vector<double2> ike(2 * (size_t)mesh->ncomp);
@@ -403,7 +407,7 @@ static int problem_create(osrc_mesh *mesh, const osrc_params *prm, const double 
                 ike[mesh->ncomp + m] = cd(inv.real(), inv.imag());  // 1 / k_eps^2
                 const double q = o.k1 * 0.15915494309189533577;
                 fo[m] = FarObj{(float)o.k1, (float)-o.k1, (float)o.rho, (float)(1.0 / o.rho),
-                               (float)(o.k1 * o.k1 / o.rho), (float)q, (float)(q - (double)(float)q), 0.f};
+                               (float)(o.k1 * o.k1 / o.rho), (float)q, (float)(q - (double)(float)q), sgn};
             }
             if ((s = pb->d_obj.alloc(ctx, mesh->ncomp)) || (s = pb->d_fobj.alloc(ctx, mesh->ncomp)) ||
                 (s = pb->d_obj_ike.alloc(ctx, 2 * (size_t)mesh->ncomp)))
@@ -501,6 +505,7 @@ static int problem_create(osrc_mesh *mesh, const osrc_params *prm, const double 
             break;
         }
         if ((s = ms_build(pb, cptr, clist, st))) break;
+        if (p.formulation == OSRC_MULLER && (s = near_add_mass(pb, st))) break;
         // ---- OSRC constants (Sec. 2.6) ------------------------------------------
         pb->k_osrc = p.osrc_side == 1 ? p.k_int : p.k_ext;
         const double R = p.damping_R > 0.0 ? p.damping_R : mesh->mean_edge;
@@ -885,6 +890,7 @@ int problem_clone(osrc_problem *m, osrc_problem **out) {
     c->B = m->B;
     c->g = m->g;
     c->multi = m->multi;
+    c->far_obj = m->far_obj;
     c->obj = m->obj;
     c->d_obj.borrow(m->d_obj);
     c->d_fobj.borrow(m->d_fobj);

@@ -121,7 +121,7 @@ struct ObjMat {
 // FP32 constants of one object for the far kernel (duplicated-pair form is
 // built per thread): k1, -k1, rho, 1/rho, k1^2/rho, k1/(2 pi) as float-float.
 struct FarObj {
-    float k1, nk1, rho, irho, dk1, k1h, k1l, pad;
+    float k1, nk1, rho, irho, dk1, k1h, k1l, sgn;  // sgn: +1 PMCHWT, -1 Mueller
 };
 
 // Touching triangle pair for the Sauter-Schwab kernel.
@@ -189,6 +189,7 @@ struct osrc_problem {
     double *h_res = nullptr;  // pinned host block: doubles [0, 16), then ints (inner status)
     // ---- disjoint objects with their own materials --------------------------------
     bool multi = false;          // more than one object: interior terms within objects only
+    bool far_obj = false;        // far kernel with per-object constants (objects or Mueller)
     std::vector<ObjMat> obj;     // [ncomp]
     DBuf<ObjMat> d_obj;
     DBuf<FarObj> d_fobj;
@@ -220,6 +221,7 @@ int near_build(osrc_problem *pb, const std::vector<NearPair> &pairs,
 
 // dense FP64 (k_near.cu)
 int dense_assemble(osrc_problem *pb, cudaStream_t st);
+int near_add_mass(osrc_problem *pb, cudaStream_t st);  // Mueller: + M in blocks (1,2), (2,1)
 int dense_apply(osrc_problem *pb, const double2 *x, double2 *y, cudaStream_t st);
 
 // sparse M, S and the inner solvers (k_sparse.cu)
