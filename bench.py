@@ -47,6 +47,11 @@ FLOPS_PER_PAIR_NOMINAL = 176
 # unrestarted GMRES needs the same count within +-2 at smaller sizes): used
 # to turn the oracle's sampled matvec rate into solves/s
 REF_ITERATIONS = 47
+# DRAM bytes (read + write) of one far_kernel<0, 0> launch at this workload,
+# from one ncu capture of this command (dram__bytes_read.sum 15,106,816 +
+# dram__bytes_write.sum 3,072, the ncu summary of the far kernel kept with the
+# profiles); to be retaken whenever the far kernel changes
+FAR_TRAFFIC_BYTES = 15109888
 
 
 def parse():
@@ -68,6 +73,12 @@ def parse():
                     help="skip the far-field apply on the 80000-vertex bumpy ellipsoid")
     ap.add_argument("--no-objects", action="store_true",
                     help="skip the four-sphere multiple-scattering solve")
+    ap.add_argument("--profile-case", choices=["far-small", "dense-short", "dense-small"],
+                    help="instead of the benchmark: run one small case for profiler captures "
+                         "(far-small: far-field applies on a 2562-vertex sphere, plain then "
+                         "large-ka; dense-short: ellipsoid8000, 128 right-hand sides, one "
+                         "refinement of 120 inner iterations; dense-small: the same on a "
+                         "3000-vertex ellipsoid, 24 inner iterations)")
     ap.add_argument("--precond-sweep", action="store_true",
                     help="instead of the benchmark: GMRES iterations vs frequency on the "
                          "10242-vertex sphere for the OSRC, mass-only and Calderon preconditioners")
@@ -307,7 +318,7 @@ def run_ours(args, D):
         "roofline": {
             "bound": "alu", "kernel": "far_kernel",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None,
+            "traffic": FAR_TRAFFIC_BYTES, "traffic_unit": "bytes per launch (ncu)",
             "flops_per_unit": FLOPS_PER_PAIR, "units_per_launch": far_pairs,
             "unit_def": "far point pair (test point, source point of triangles sharing no "
                         "vertex), both wavenumbers",
@@ -979,8 +990,51 @@ def precond_sweep(device=0, maxit=800):
                 S.close()
 
 
+def profile_case(name, device=0):
+    """Small fixed workloads for ncu captures (see --profile-case)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2104_04609_gb300 import binding as B
+    from paper_2104_04609_gb300.inputs import ellipsoid, icosphere, plane_wave_dirs, workload
+
+    if name == "far-small":
+        v, t = icosphere(4)
+        for k0, k1 in ((20.0, 26.0), (40.0, 100.0)):
+            S = B.Solver(v, t, k0, k1, 1.5, device=device)
+            x = S.rhs_planewave([[0.0, 0.0, 1.0]])
+            for _ in range(3):
+                S.apply(x)
+            torch.cuda.synchronize()
+            S.close()
+        return
+    if name == "dense-short":
+        W = workload(DENSE_WORKLOAD)
+        v, t, k0, k1, rho, dirs, maxit = W["verts"], W["tris"], W["k_ext"], W["k_int"], W["rho_ratio"], \
+            W["dirs"][:128], 120
+    else:
+        v, t = ellipsoid(3000)
+        k0, k1, rho, dirs, maxit = 15.0, 36.0, 1.9, plane_wave_dirs(128, seed=1), 24
+    S = B.Solver(v, t, k0, k1, rho, device=device, precision=B.OSRC_FP64_DENSE)
+    try:
+        b = S.rhs_planewave(dirs)
+        x = torch.zeros_like(b)
+        B.osrc_dense_precond_build(S.pb, tol=1e-3, maxit=500)
+        info = B.osrc_dense_batched_solve(S.pb, b, x, tol=1e-6, max_refine=1, inner_tol=1e-3,
+                                          inner_maxit=maxit, raise_on_nonconvergence=False)
+        torch.cuda.synchronize()
+        print(json.dumps(info), flush=True)
+    finally:
+        S.close()
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     if args.large_sweep > 0:
         large_sweep(args.large_sweep)
         return
