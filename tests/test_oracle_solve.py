@@ -38,7 +38,7 @@ def mie_field(k0, k1, rho, a, pts):
     P = np.atleast_2d(pts)
     r = np.linalg.norm(P, axis=1)
     cth = np.where(r > 0, P[:, 2] / np.where(r > 0, r, 1.0), 1.0)
-    L = int(max(k0, k1) * max(a, r.max()) + 4 * (k1 * a) ** (1 / 3) + 20)
+    L = int(max(abs(k0), abs(k1)) * max(a, r.max()) + 4 * (abs(k1) * a) ** (1 / 3) + 20)
     u = np.zeros(P.shape[0], dtype=complex)
     out = r > a
     for l in range(L):
