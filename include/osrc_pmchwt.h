@@ -82,6 +82,9 @@ typedef struct osrc_params {
     int inner_maxit;     /* iteration cap of the inner solves */
     int precond;         /* preconditioner P of the GMRES solve: OSRC_PRECOND_* */
     int formulation;     /* OSRC_PMCHWT (default) or OSRC_MULLER */
+    double k_int_im;     /* attenuation: imaginary part of the interior wavenumber
+                            (>= 0; Sec. 3.1, k_m = 2 pi f / c_m + i alpha_m f^b_m),
+                            added to every object's; the exterior stays lossless */
 } osrc_params;
 
 /* Boundary integral formulation (Sec. 2.2), both in the permuted ordering

@@ -58,7 +58,7 @@ class osrc_params(ctypes.Structure):
         ("osrc_side", ctypes.c_int), ("n_ss", ctypes.c_int),
         ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double),
         ("inner_maxit", ctypes.c_int), ("precond", ctypes.c_int),
-        ("formulation", ctypes.c_int),
+        ("formulation", ctypes.c_int), ("k_int_im", ctypes.c_double),
     ]
 
 

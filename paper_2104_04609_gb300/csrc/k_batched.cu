@@ -810,7 +810,7 @@ int batched_prepare(osrc_problem *pb, int R, int maxit_inner, cudaStream_t st) {
             for (int m = 0; m < nc; ++m) {
                 const ObjMat &om = pb->obj[m];
                 const double2 ke2 = cmul(om.k_eps, om.k_eps), inv = cdiv(cd(1.0, 0.0), ke2);
-                o[m] = make_float2(0.f, (float)om.k_osrc);
+                o[m] = make_float2((float)-om.k_osrc_i, (float)om.k_osrc);
                 o[nc + m] = make_float2((float)inv.x, (float)inv.y);
             }
             OSRC_TRY(bs->obj32.alloc(ctx, o.size()));
@@ -918,8 +918,11 @@ static int batched_precond(osrc_problem *pb, const float2 *y, float2 *z, float t
                                bs->kits.p));
     OsrcComb32 c{};
     c.np = np;
-    c.ik = make_float2(0.f, (float)pb->k_osrc);
-    c.iik = make_float2(0.f, (float)(-1.0 / pb->k_osrc));
+    {
+        const double2 ik = cd(-pb->k_osrc_i, pb->k_osrc), iik = cdiv(cd(1.0, 0.0), ik);
+        c.ik = make_float2((float)ik.x, (float)ik.y);
+        c.iik = make_float2((float)iik.x, (float)iik.y);
+    }
     double2 cu = pb->C0;
     for (int j = 0; j < np; ++j) {
         const double2 a = cdiv(pb->A[j], pb->B[j]);

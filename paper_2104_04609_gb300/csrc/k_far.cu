@@ -270,10 +270,12 @@ __device__ __forceinline__ CenterPair center_pair(const float4 &cth, const float
 // from the triangle centroids, x - y = D + delta, and the phase is
 // k r = k r_c + k (2 D.delta + delta.delta) / (r + r_c) with k r_c reduced in
 // float-float arithmetic once per triangle pair.
+// MULTI: m1 multiplies the interior terms (0: source on another object, -1:
+// Mueller); k1i / dk1i: imaginary parts of k1 and k1^2 / rho (attenuation).
 template <bool CENTRED, bool MULTI>
 __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, const f2 &P5, f2 mnx,
                                           f2 mny, f2 mnz, f2 wq2, const FarConst2 &c,
-                                          const CenterPair &cp, f2 m1, PairAcc &A) {
+                                          const CenterPair &cp, f2 m1, f2 k1i, f2 dk1i, PairAcc &A) {
     const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3], P4 = P[4];
     f2 dx, dy, dz, ddx, ddy, ddz;
     if (CENTRED) {
@@ -323,9 +325,12 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
         __sincosf(kr1.x, &s1.x, &c1.x);
         __sincosf(kr1.y, &s1.y, &c1.y);
     }
-    if (MULTI) {  // source on another object: exterior wavenumber only
-        c1 = mul2(c1, m1);
-        s1 = mul2(s1, m1);
+    f2 br = make_float2(0.f, 0.f);
+    if (MULTI) {  // e^{i k1 r} with k1 = k1r + i k1i: damping e^{-k1i r}, and m1
+        br = mul2(r, k1i);
+        const f2 damp = mul2(m1, make_float2(__expf(-br.x), __expf(-br.y)));
+        c1 = mul2(c1, damp);
+        s1 = mul2(s1, damp);
     }
     const f2 psr = hi2(P1), psi = lo2(P2), mpsr = hi2(P2), mpsi = lo2(P3);
     const f2 phr = hi2(P3), phi = lo2(P4), mphr = hi2(P4), mphi = P5;
@@ -336,8 +341,13 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
     A.u1r = fma2(gpr, psr, fma2(gpi, mpsi, A.u1r));
     A.u1i = fma2(gpr, psi, fma2(gpi, psr, A.u1i));
     // D normal term (k0^2 G0 + k1^2/rho G1) phi
-    const f2 gkr = mul2(fma2(c.dk1, c1, mul2(c.dk0, c0)), ri);
-    const f2 gki = mul2(fma2(c.dk1, s1, mul2(c.dk0, s0)), ri);
+    f2 gkr0 = fma2(c.dk1, c1, mul2(c.dk0, c0)), gki0 = fma2(c.dk1, s1, mul2(c.dk0, s0));
+    if (MULTI) {  // complex k1^2 / rho
+        gkr0 = fma2(mul2(dk1i, s1), dup2(-1.f), gkr0);
+        gki0 = fma2(dk1i, c1, gki0);
+    }
+    const f2 gkr = mul2(gkr0, ri);
+    const f2 gki = mul2(gki0, ri);
     A.ur = fma2(gkr, phr, fma2(gki, mphi, A.ur));
     A.ui = fma2(gkr, phi, fma2(gki, phr, A.ui));
     // D curl term: sum_q w_q (G0 + G1/rho)
@@ -346,8 +356,14 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
     A.t3i = fma2(fma2(c.irho, s1, s0), wr, A.t3i);
     // -(H0 + H1), H = e^{ikr} (i k r - 1) / r^3:
     //   re = (c0 + c1 + kr0 s0 + kr1 s1) / r^3,  im = (s0 + s1 - kr0 c0 - kr1 c1) / r^3
-    const f2 hp = mul2(fma2(kr1, s1, fma2(kr0, s0, add2(c0, c1))), ri3);
-    const f2 hq = mul2(fma2(nkr1, c1, fma2(nkr0, c0, add2(s0, s1))), ri3);
+    f2 hp0 = fma2(kr1, s1, fma2(kr0, s0, add2(c0, c1)));
+    f2 hq0 = fma2(nkr1, c1, fma2(nkr0, c0, add2(s0, s1)));
+    if (MULTI) {  // (i k1 r - 1) with Im k1: + k1i r (c1, s1)
+        hp0 = fma2(br, c1, hp0);
+        hq0 = fma2(br, s1, hq0);
+    }
+    const f2 hp = mul2(hp0, ri3);
+    const f2 hq = mul2(hq0, ri3);
     A.t1r = fma2(hp, phr, fma2(hq, mphi, A.t1r));  // T1n = -sum Hs phi
     A.t1i = fma2(hp, phi, fma2(hq, phr, A.t1i));
     // T block: (H0 + H1)(x - y).n_x psi = (-(H0 + H1)) (y - x).n_x psi
@@ -403,6 +419,7 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
     float4 kff = kff0;
     int ct = 0;
     float sgn = 1.f;  // sign of the interior terms (-1: Mueller)
+    f2 k1i = make_float2(0.f, 0.f), dk1i = k1i;
     if (MULTI) {
         ct = tcomp[tau];
         const FarObj o = fobj[ct];
@@ -414,6 +431,8 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
         kff.z = o.k1h;
         kff.w = o.k1l;
         sgn = o.sgn;
+        k1i = dup2(o.k1i);
+        dk1i = dup2(o.dk1i);
     }
     float4 cth = make_float4(0.f, 0.f, 0.f, 0.f), ctl = cth;
     if (CENTRED) {
@@ -468,7 +487,7 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
 #pragma unroll
             for (int q = 0; q < 6; ++q)
                 far_pair2<CENTRED, MULTI>(X, Y, Z, &shP[30 * s + 5 * q], shP5[6 * s + q], mnx, mny, mnz,
-                                          q < 3 ? W1 : W2, c, cp, m1, A);
+                                          q < 3 ? W1 : W2, c, cp, m1, k1i, dk1i, A);
             // u1 += (x - y).n_y T1 = (-(x - y).n_y)(-T1);  u2 += (-n_x.n_y) U
             A.u1r = fma2(xnyn, A.t1r, A.u1r);
             A.u1i = fma2(xnyn, A.t1i, A.u1i);

@@ -107,6 +107,7 @@ field_kernel(int npts, const double *__restrict__ pts, int ns, const int *__rest
     const int ins = valid ? region[i] : 0;
     // outside: every source point, k0; inside object m: its own points, k_m
     const double k = ins ? obj[ins - 1].k1 : c.k0;
+    const double ki = ins ? obj[ins - 1].k1i : 0.0;  // attenuation inside
     const int lo = ins ? obeg[ins - 1] : 0, hi = ins ? obeg[ins] : ns;
     double2 S = cd(0, 0), D = cd(0, 0);
     for (int base = 0; base < ns; base += FT) {
@@ -125,11 +126,11 @@ field_kernel(int npts, const double *__restrict__ pts, int ns, const int *__rest
             const double r = (d0 * d0 + d1 * d1 + d2 * d2) * ri;
             double sn_, cs_;
             sincos(k * r, &sn_, &cs_);
-            const double f = a.w * kFInv4Pi * ri;
+            const double f = a.w * kFInv4Pi * ri * (ki != 0.0 ? exp(-ki * r) : 1.0);
             const double2 g = cd(cs_ * f, sn_ * f);                        // w G
             S = cadd(S, cmul(g, cd(dv.x, dv.y)));                          // w G psi_q
             const double dn = (d0 * n.x + d1 * n.y + d2 * n.z) * ri * ri;  // (y - x).n / r^2
-            const double2 h = cscale(cmul(g, cd(-1.0, k * r)), dn);        // w dG/dn_y
+            const double2 h = cscale(cmul(g, cd(-1.0 - ki * r, k * r)), dn);  // w dG/dn_y
             D = cadd(D, cmul(h, cd(dv.z, dv.w)));
         }
         __syncthreads();

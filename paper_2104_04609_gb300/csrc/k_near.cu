@@ -83,6 +83,7 @@ struct NearConst {
     const ObjMat *obj;  // disjoint objects: material per object (else k1, rho)
     const int *tcomp;   // object of each triangle
     double sgn;         // sign of the interior terms: +1 PMCHWT, -1 Mueller
+    double k1i;         // attenuation: Im k1 (objects: their own, from obj)
 };
 
 constexpr int NEAR_WARPS = 4;
@@ -111,11 +112,12 @@ near_ss_kernel(const NearPair *__restrict__ pairs, long long npairs,
     const long long pi = (long long)blockIdx.x * NEAR_WARPS + (threadIdx.x >> 5);
     if (pi >= npairs) return;
     const NearPair pr = pairs[pi];
-    double k1 = c.k1, rho = c.rho;  // touching triangles lie on one object
+    double k1 = c.k1, rho = c.rho, k1i = c.k1i;  // touching triangles lie on one object
     if (c.obj) {
         const ObjMat o = c.obj[c.tcomp[pr.t]];
         k1 = o.k1;
         rho = o.rho;
+        k1i = o.k1i;
     }
     int pt[3], ps[3];
     for (int a = 0; a < 3; ++a) {
@@ -169,17 +171,19 @@ near_ss_kernel(const NearPair *__restrict__ pairs, long long npairs,
         double s0, c0, s1, c1;
         sincos(c.k0 * r, &s0, &c0);
         sincos(k1 * r, &s1, &c1);
-        s1 *= c.sgn;
-        c1 *= c.sgn;
+        // k1 = k1 + i k1i: e^{i k1 r} damped by e^{-k1i r}; (i k1 r - 1) gains -k1i r
+        const double br = k1i * r, damp = c.sgn * (k1i != 0.0 ? exp(-br) : 1.0);
+        s1 *= damp;
+        c1 *= damp;
         const double kr0 = c.k0 * r, kr1 = k1 * r;
         const double f = kInv4Pi * ri, f3 = f * ri * ri;
         const double g0r = c0 * f, g0i = s0 * f, g1r = c1 * f, g1i = s1 * f;
-        const double hsr = (-c0 - kr0 * s0 - c1 - kr1 * s1) * f3;
-        const double hsi = (kr0 * c0 - s0 + kr1 * c1 - s1) * f3;
+        const double hsr = (-c0 - kr0 * s0 - c1 - kr1 * s1 - br * c1) * f3;
+        const double hsi = (kr0 * c0 - s0 + kr1 * c1 - s1 - br * s1) * f3;
         const double gpr = g0r + rho * g1r, gpi = g0i + rho * g1i;
         const double gdr = g0r + g1r / rho, gdi = g0i + g1i / rho;
-        const double dk0 = c.k0 * c.k0, dk1 = k1 * k1 / rho;
-        const double gkr = dk0 * g0r + dk1 * g1r, gki = dk0 * g0i + dk1 * g1i;
+        const double dk0 = c.k0 * c.k0, dk1 = (k1 * k1 - k1i * k1i) / rho, dk1i = 2.0 * k1 * k1i / rho;
+        const double gkr = dk0 * g0r + dk1 * g1r - dk1i * g1i, gki = dk0 * g0i + dk1 * g1i + dk1i * g1r;
         const double dny = -(d0 * ns0 + d1 * ns1 + d2 * ns2);  // (y - x).n_y
         const double dnx = d0 * nt0 + d1 * nt1 + d2 * nt2;     // (x - y).n_x
         dcr += gdr * w;
@@ -301,12 +305,13 @@ dense_far_kernel(int nv, int nt, const double *__restrict__ verts, const int *__
     const double *gt = tgeo + 16 * (size_t)(live ? t : 0), *gs = tgeo + 16 * (size_t)(live ? s : 0);
     // disjoint objects: the pair's object material; interior terms only
     // within one object
-    double k1 = c.k1, rho = c.rho, on1 = c.sgn;
+    double k1 = c.k1, rho = c.rho, on1 = c.sgn, k1i = c.k1i;
     if (c.obj && live) {
         const int ct = c.tcomp[t], cs = c.tcomp[s];
         const ObjMat o = c.obj[ct];
         k1 = o.k1;
         rho = o.rho;
+        k1i = o.k1i;
         if (ct != cs) on1 = 0.0;
     }
     double2 Z[13];
@@ -319,7 +324,7 @@ dense_far_kernel(int nv, int nt, const double *__restrict__ verts, const int *__
             X[k] = dense_bary(p, 0) * verts[3 * vt[0] + k] + dense_bary(p, 1) * verts[3 * vt[1] + k] +
                    dense_bary(p, 2) * verts[3 * vt[2] + k];
         const double scale = gt[0] * gs[0] * dense_w(p);
-        const double dk0 = c.k0 * c.k0, dk1 = k1 * k1 / rho;
+        const double dk0 = c.k0 * c.k0, dk1 = (k1 * k1 - k1i * k1i) / rho, dk1i = 2.0 * k1 * k1i / rho;
         for (int q = 0; q < 6; ++q) {
             const double b0 = dense_bary(q, 0), b1 = dense_bary(q, 1), b2 = dense_bary(q, 2);
             const double d0 = X[0] - (b0 * Vs[0][0] + b1 * Vs[1][0] + b2 * Vs[2][0]);
@@ -330,14 +335,16 @@ dense_far_kernel(int nv, int nt, const double *__restrict__ verts, const int *__
             double s0, c0, s1, c1;
             sincos(c.k0 * r, &s0, &c0);
             sincos(k1 * r, &s1, &c1);
-            s1 *= on1;
-            c1 *= on1;
+            const double br = k1i * r, damp = on1 * (k1i != 0.0 ? exp(-br) : 1.0);
+            s1 *= damp;
+            c1 *= damp;
             const double kr0 = c.k0 * r, kr1 = k1 * r;
             const double fw = kInv4Pi * ri * w, f3 = fw * ri * ri;
             const double2 g0 = cd(c0 * fw, s0 * fw), g1 = cd(c1 * fw, s1 * fw);
-            const double2 hs = cd((-c0 - kr0 * s0 - c1 - kr1 * s1) * f3, (kr0 * c0 - s0 + kr1 * c1 - s1) * f3);
+            const double2 hs = cd((-c0 - kr0 * s0 - c1 - kr1 * s1 - br * c1) * f3,
+                                  (kr0 * c0 - s0 + kr1 * c1 - s1 - br * s1) * f3);
             const double2 gp = cadd(g0, cscale(g1, rho));
-            const double2 gk = cadd(cscale(g0, dk0), cscale(g1, dk1));
+            const double2 gk = cadd(cscale(g0, dk0), cmul(g1, cd(dk1, dk1i)));
             const double2 hk = cscale(hs, d0 * gs[1] + d1 * gs[2] + d2 * gs[3]);  // -hs (y - x).n_y
             const double2 ht = cscale(hs, d0 * gt[1] + d1 * gt[2] + d2 * gt[3]);  //  hs (x - y).n_x
             Z[12] = cadd(Z[12], cadd(g0, cscale(g1, 1.0 / rho)));
@@ -490,7 +497,7 @@ int near_build(osrc_problem *pb, const std::vector<NearPair> &pairs,
     OSRC_CK(cudaMemcpyAsync(d_cidx.p, cidx.data(), cidx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     OSRC_CK(cudaMemcpyAsync(d_gl.p, gl, sizeof(gl), cudaMemcpyHostToDevice, st));
     NearConst c{pb->p.k_ext, pb->p.k_int, pb->p.rho_ratio, pb->p.n_ss, pb->multi ? pb->d_obj.p : nullptr,
-                 pb->mesh->d_tcomp.p, pb->p.formulation == OSRC_MULLER ? -1.0 : 1.0};
+                 pb->mesh->d_tcomp.p, pb->p.formulation == OSRC_MULLER ? -1.0 : 1.0, pb->p.k_int_im};
     const long long blocks = (np + NEAR_WARPS - 1) / NEAR_WARPS;
     if (blocks > 0) {
         near_ss_kernel<<<(unsigned)blocks, 32 * NEAR_WARPS, 0, st>>>(
@@ -516,7 +523,7 @@ int dense_assemble(osrc_problem *pb, cudaStream_t st) {
     OSRC_TRY(pb->d_dense.alloc(m->ctx, n2 * n2));
     OSRC_CK(cudaMemsetAsync(pb->d_dense.p, 0, n2 * n2 * sizeof(double2), st));
     NearConst c{pb->p.k_ext, pb->p.k_int, pb->p.rho_ratio, pb->p.n_ss, pb->multi ? pb->d_obj.p : nullptr,
-                 pb->mesh->d_tcomp.p, pb->p.formulation == OSRC_MULLER ? -1.0 : 1.0};
+                 pb->mesh->d_tcomp.p, pb->p.formulation == OSRC_MULLER ? -1.0 : 1.0, pb->p.k_int_im};
     const int folded = (nt + 1) / 2;
     if (folded > 65535) {
         osrc_set_error("dense assembly: too many triangles for the dense path");

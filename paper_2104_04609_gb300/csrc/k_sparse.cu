@@ -515,8 +515,8 @@ int osrc_precond_fused_async(osrc_problem *pb, const double2 *y, double2 *z, cud
     OSRC_TRY(launch_kry(pb, b, st));
     OsrcComb c{};
     c.np = np;
-    c.ik = cd(0.0, pb->k_osrc);
-    c.iik = cd(0.0, -1.0 / pb->k_osrc);
+    c.ik = cd(-pb->k_osrc_i, pb->k_osrc);  // i k_osrc (complex with attenuation)
+    c.iik = cdiv(cd(1.0, 0.0), c.ik);
     c.ik_obj = pb->multi ? pb->d_obj_ike.p : nullptr;
     c.vcomp = pb->mesh->d_vcomp.p;
     double2 cu = pb->C0;

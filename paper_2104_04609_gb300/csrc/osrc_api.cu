@@ -72,6 +72,7 @@ extern "C" void osrc_params_default(osrc_params *p) {
     p->inner_maxit = 2000;
     p->precond = OSRC_PRECOND_OSRC;
     p->formulation = OSRC_PMCHWT;
+    p->k_int_im = 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -368,6 +369,7 @@ static int problem_create(osrc_mesh *mesh, const osrc_params *prm, const double 
         p.inner_maxit < 1 || (p.precision != OSRC_FP32_MATFREE && p.precision != OSRC_FP64_DENSE) ||
         p.precond < OSRC_PRECOND_OSRC || p.precond > OSRC_PRECOND_CALDERON ||
         (p.formulation != OSRC_PMCHWT && p.formulation != OSRC_MULLER) ||
+        !(p.k_int_im >= 0.0) || !std::isfinite(p.k_int_im) ||
         (p.osrc_side != 0 && p.osrc_side != 1) || !std::isfinite(p.theta)) {
         osrc_set_error("invalid problem parameters");
         return OSRC_INVALID_ARG;
@@ -389,7 +391,7 @@ static int problem_create(osrc_mesh *mesh, const osrc_params *prm, const double 
         {
             const double R = p.damping_R > 0.0 ? p.damping_R : mesh->mean_edge;
             pb->multi = mesh->ncomp > 1;
-            pb->far_obj = pb->multi || p.formulation == OSRC_MULLER;
+            pb->far_obj = pb->multi || p.formulation == OSRC_MULLER || p.k_int_im != 0.0;
             const float sgn = p.formulation == OSRC_MULLER ? -1.f : 1.f;
             pb->obj.resize(mesh->ncomp);
             std::vector<FarObj> fo(mesh->ncomp);
@@ -397,17 +399,22 @@ static int problem_create(osrc_mesh *mesh, const osrc_params *prm, const double 
             for (int m = 0; m < mesh->ncomp; ++m) {
                 ObjMat &o = pb->obj[m];
                 o.k1 = k_int_obj[m];
+                o.k1i = p.k_int_im;
                 o.rho = rho_obj[m];
                 o.k_osrc = p.osrc_side == 1 ? o.k1 : p.k_ext;
+                o.k_osrc_i = p.osrc_side == 1 ? o.k1i : 0.0;
+                const std::complex<double> ko(o.k_osrc, o.k_osrc_i);
                 const std::complex<double> ke =
-                    o.k_osrc * (1.0 + std::complex<double>(0.0, 0.4) * std::pow(o.k_osrc * R, -2.0 / 3.0));
+                    ko * (1.0 + std::complex<double>(0.0, 0.4) * std::pow(ko * R, -2.0 / 3.0));
                 o.k_eps = cd(ke.real(), ke.imag());
                 const std::complex<double> inv = 1.0 / (ke * ke);
-                ike[m] = cd(0.0, o.k_osrc);                         // i k_osrc
+                ike[m] = cd(-o.k_osrc_i, o.k_osrc);                 // i k_osrc
                 ike[mesh->ncomp + m] = cd(inv.real(), inv.imag());  // 1 / k_eps^2
                 const double q = o.k1 * 0.15915494309189533577;
+                const std::complex<double> k1c(o.k1, o.k1i), dk1 = k1c * k1c / o.rho;
                 fo[m] = FarObj{(float)o.k1, (float)-o.k1, (float)o.rho, (float)(1.0 / o.rho),
-                               (float)(o.k1 * o.k1 / o.rho), (float)q, (float)(q - (double)(float)q), sgn};
+                               (float)dk1.real(), (float)q, (float)(q - (double)(float)q), sgn,
+                               (float)o.k1i, (float)dk1.imag()};
             }
             if ((s = pb->d_obj.alloc(ctx, mesh->ncomp)) || (s = pb->d_fobj.alloc(ctx, mesh->ncomp)) ||
                 (s = pb->d_obj_ike.alloc(ctx, 2 * (size_t)mesh->ncomp)))
@@ -508,9 +515,11 @@ static int problem_create(osrc_mesh *mesh, const osrc_params *prm, const double 
         if (p.formulation == OSRC_MULLER && (s = near_add_mass(pb, st))) break;
         // ---- OSRC constants (Sec. 2.6) ------------------------------------------
         pb->k_osrc = p.osrc_side == 1 ? p.k_int : p.k_ext;
+        pb->k_osrc_i = p.osrc_side == 1 ? p.k_int_im : 0.0;
         const double R = p.damping_R > 0.0 ? p.damping_R : mesh->mean_edge;
+        const std::complex<double> kos(pb->k_osrc, pb->k_osrc_i);
         const std::complex<double> ke =
-            pb->k_osrc * (1.0 + std::complex<double>(0.0, 0.4) * std::pow(pb->k_osrc * R, -2.0 / 3.0));
+            kos * (1.0 + std::complex<double>(0.0, 0.4) * std::pow(kos * R, -2.0 / 3.0));
         pb->k_eps = cd(ke.real(), ke.imag());
         std::complex<double> C0;
         std::vector<std::complex<double>> A, B;
@@ -883,6 +892,7 @@ int problem_clone(osrc_problem *m, osrc_problem **out) {
     c->near_nnz = m->near_nnz;
     c->ms_nnz = m->ms_nnz;
     c->k_osrc = m->k_osrc;
+    c->k_osrc_i = m->k_osrc_i;
     c->k_eps = m->k_eps;
     c->C0 = m->C0;
     c->g0 = m->g0;

@@ -114,14 +114,16 @@ struct osrc_mesh {
 // Material of one object (disjoint objects, Sec. 2.2): interior wavenumber,
 // density ratio rho_m / rho_0, OSRC wavenumber and its damped version.
 struct ObjMat {
-    double k1, rho, k_osrc, pad;
+    double k1, rho, k_osrc, k1i;  // k1i: imaginary part of the interior wavenumber
     double2 k_eps;
+    double k_osrc_i, pad;         // imaginary part of the OSRC wavenumber
 };
 
 // FP32 constants of one object for the far kernel (duplicated-pair form is
 // built per thread): k1, -k1, rho, 1/rho, k1^2/rho, k1/(2 pi) as float-float.
 struct FarObj {
     float k1, nk1, rho, irho, dk1, k1h, k1l, sgn;  // sgn: +1 PMCHWT, -1 Mueller
+    float k1i, dk1i;  // attenuation: Im k1 and Im(k1^2 / rho) (dk1 holds the real part)
 };
 
 // Touching triangle pair for the Sauter-Schwab kernel.
@@ -168,7 +170,7 @@ struct osrc_problem {
     // ---- dense FP64 system (OSRC_FP64_DENSE) -------------------------------
     DBuf<double2> d_dense;    // [2nv][2nv] row-major
     // ---- OSRC constants (Sec. 2.6) -------------------------------------------
-    double k_osrc = 0.0;
+    double k_osrc = 0.0, k_osrc_i = 0.0;  // OSRC wavenumber (complex with attenuation)
     double2 k_eps{};
     double2 C0{}, g0{};
     std::vector<double2> A, B, g;
