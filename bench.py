@@ -79,6 +79,9 @@ def parse():
                          "large-ka; dense-short: ellipsoid8000, 128 right-hand sides, one "
                          "refinement of 120 inner iterations; dense-small: the same on a "
                          "3000-vertex ellipsoid, 24 inner iterations)")
+    ap.add_argument("--sponge-sweep", action="store_true",
+                    help="instead of the benchmark: GMRES iterations of the four formulations on "
+                         "the level-2 Menger sponge at 0.5 and 1 MHz")
     ap.add_argument("--precond-sweep", action="store_true",
                     help="instead of the benchmark: GMRES iterations vs frequency on the "
                          "10242-vertex sphere for the OSRC, mass-only and Calderon preconditioners")
@@ -1030,8 +1033,48 @@ def profile_case(name, device=0):
         S.close()
 
 
+def sponge_sweep(device=0, maxit=400):
+    """The non-smooth domain of Sec. 3.4: level-2 Menger sponge, edge 2 (10 mm),
+    bone-like interior (c 3600 m/s, rho ratio 1.9) in water, plane wave +x,
+    tol 1e-5; faces split so that there are about six or more elements per
+    exterior wavelength (sub 3 at 0.5 MHz, 5 at 1 MHz)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2104_04609_gb300 import binding as B
+    from paper_2104_04609_gb300.inputs import menger_sponge
+
+    kinds = (("osrc", B.OSRC_PRECOND_OSRC, B.OSRC_PMCHWT), ("mass", B.OSRC_PRECOND_MASS, B.OSRC_PMCHWT),
+             ("calderon", B.OSRC_PRECOND_CALDERON, B.OSRC_PMCHWT),
+             ("muller", B.OSRC_PRECOND_MASS, B.OSRC_MULLER))
+    for f_mhz, sub in ((0.5, 3), (1.0, 5)):
+        v, t = menger_sponge(2, sub, edge=2.0)
+        k0 = 2.0 * math.pi * f_mhz * 1e6 / C_WATER * 5e-3
+        for name, code, form in kinds:
+            S = B.Solver(v, t, k0, k0 * C_WATER / C_BONE, RHO_BONE, device=device, precond=code,
+                         formulation=form)
+            try:
+                b = S.rhs_planewave([[1.0, 0.0, 0.0]])
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                x, info = S.solve(b, tol=TOL, maxit=maxit, raise_on_nonconvergence=False)
+                torch.cuda.synchronize()
+                print(json.dumps({"mesh": f"level-2 Menger sponge, {S.nv} vertices",
+                                  "frequency_mhz": f_mhz, "k_ext": k0, "formulation": name,
+                                  "iterations": info.iterations, "converged": bool(info.converged),
+                                  "true_residual": info.true_residual,
+                                  "solve_s": time.perf_counter() - t0}), flush=True)
+            finally:
+                S.close()
+
+
 def main():
     args = parse()
+    if args.sponge_sweep:
+        sponge_sweep()
+        return
     if args.profile_case:
         profile_case(args.profile_case)
         return

@@ -163,6 +163,56 @@ def serving_requests(n: int = 1000, rate: float = 50.0, seed: int = 2):
     return out
 
 
+def menger_sponge(level: int = 2, sub: int = 1, edge: float = 2.0):
+    """Surface of a level-``level`` Menger sponge (a cube of side ``edge``,
+    centred at the origin, from which the middle cells are removed
+    recursively: a cell of the 3^level grid is kept when no level has more
+    than one of its three base-3 digits equal to 1).  Every boundary face of
+    a kept cell is split into sub x sub squares on the global lattice and each
+    square into two triangles, counter-clockwise seen from outside."""
+    n = 3 ** level
+    keep = np.ones((n, n, n), dtype=bool)
+    idx = np.arange(n)
+    for d in range(level):
+        dig = (idx // 3 ** d) % 3 == 1
+        ones = dig[:, None, None].astype(int) + dig[None, :, None] + dig[None, None, :]
+        keep &= ones <= 1
+    N = n * sub
+    vid = {}
+    verts, tris = [], []
+
+    def vertex(p):
+        if p not in vid:
+            vid[p] = len(verts)
+            verts.append(p)
+        return vid[p]
+
+    for a in range(3):
+        b, c = (a + 1) % 3, (a + 2) % 3
+        for cell in zip(*np.nonzero(keep)):
+            for side in (0, 1):
+                nb = list(cell)
+                nb[a] += 1 if side else -1
+                if 0 <= nb[a] < n and keep[tuple(nb)]:
+                    continue
+                base = [int(cell[0]) * sub, int(cell[1]) * sub, int(cell[2]) * sub]
+                base[a] += sub if side else 0
+                for u in range(sub):
+                    for w in range(sub):
+                        def corner(du, dw):
+                            q = list(base)
+                            q[b] += u + du
+                            q[c] += w + dw
+                            return vertex(tuple(q))
+                        p00, p10, p11, p01 = corner(0, 0), corner(1, 0), corner(1, 1), corner(0, 1)
+                        if side:  # outward normal +e_a: (e_b, e_c) right-handed
+                            tris += [(p00, p10, p11), (p00, p11, p01)]
+                        else:
+                            tris += [(p00, p11, p10), (p00, p01, p11)]
+    V = np.asarray(verts, dtype=np.float64) * (edge / N) - edge / 2.0
+    return V, np.asarray(tris, dtype=np.int32)
+
+
 def workload(name: str):
     """The named synthetic workloads: mesh + physical parameters.
 
