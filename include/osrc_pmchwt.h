@@ -349,8 +349,9 @@ int osrc_field_eval(osrc_problem *pb, const void *x, const double *pts, int npts
  * tol applies to the true residual, 1e-3 inner tolerance, at most 400 inner
  * iterations per refinement, blocks of up to 128), on the cached problem,
  * whose assembled system, BF16 matrices and explicit preconditioner stay
- * resident for later requests on the same mesh and frequency.  The worker
- * runs such a block to completion before it advances the other slots.
+ * resident for later requests on the same mesh and frequency.  Such a block
+ * runs on a host thread of its own with its slot's stream, so it overlaps
+ * with the other slots' work; one block per resident problem at a time.
  * Results equal a direct osrc_dense_batched_solve of the same block within
  * the solve's tolerance, not bit for bit: the FP64 assembly accumulates with
  * atomics, so each assembly differs in the last bits. */

@@ -35,18 +35,23 @@ extern "C" const char *osrc_status_string(int s) {
 
 int ctx_alloc(osrc_ctx *ctx, void **p, size_t bytes) {
     *p = nullptr;
-    if (ctx->budget && ctx->used + bytes > ctx->budget) {
-        osrc_set_error("device memory budget exceeded");
-        return OSRC_OUT_OF_MEMORY;
-    }
+    // reserve against the budget first (atomically: allocations may come from
+    // several host threads), give the reservation back if cudaMalloc fails
+    size_t cur = ctx->used.load();
+    do {
+        if (ctx->budget && cur + bytes > ctx->budget) {
+            osrc_set_error("device memory budget exceeded");
+            return OSRC_OUT_OF_MEMORY;
+        }
+    } while (!ctx->used.compare_exchange_weak(cur, cur + bytes));
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         *p = nullptr;
+        ctx->used -= bytes;
         osrc_set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
         return OSRC_OUT_OF_MEMORY;
     }
-    ctx->used += bytes;
     return OSRC_OK;
 }
 
@@ -99,7 +104,7 @@ extern "C" int osrc_create(osrc_ctx **out, int device, size_t budget) {
 }
 
 extern "C" void osrc_destroy(osrc_ctx *ctx) { delete ctx; }
-extern "C" size_t osrc_mem_used(const osrc_ctx *ctx) { return ctx ? ctx->used : 0; }
+extern "C" size_t osrc_mem_used(const osrc_ctx *ctx) { return ctx ? ctx->used.load() : 0; }
 
 // ---------------------------------------------------------------------------
 // mesh

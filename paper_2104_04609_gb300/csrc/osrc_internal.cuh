@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <atomic>
 #include <vector>
 
 #include "../../include/osrc_pmchwt.h"
@@ -53,8 +54,8 @@ __host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
 // ---------------------------------------------------------------------------
 struct osrc_ctx {
     int device = 0;
-    size_t budget = 0;  // 0 = unlimited
-    size_t used = 0;
+    size_t budget = 0;               // 0 = unlimited
+    std::atomic<size_t> used{0};     // allocations may come from several host threads
 };
 
 int ctx_alloc(osrc_ctx *ctx, void **p, size_t bytes);

@@ -68,6 +68,7 @@ struct CacheEntry {
     int refs = 0;
     uint64_t last_use = 0;
     bool precond_built = false;  // explicit preconditioner matrix of the batched solve
+    bool batched_busy = false;   // a batched job is using this problem's batched state
 };
 
 struct Slot {
@@ -80,7 +81,17 @@ struct Slot {
     int rhs = -1;
     DBuf<double2> d_b, d_x;
     bool busy = false;
+    // a batched job (all right-hand sides of one request) runs on its own host
+    // thread with this slot's stream; bdone is set under the server mutex
+    bool batched = false;
+    std::thread bth;
+    CacheEntry *bentry = nullptr;
+    bool bdone = false;
+    int bstatus = OSRC_OK;
+    osrc_solve_info binfo{};
 };
+
+constexpr int ADMIT_WAIT = -1;  // the head of the queue must wait (its problem is busy)
 
 uint64_t fnv1a(const void *data, size_t n, uint64_t h) {
     const unsigned char *p = (const unsigned char *)data;
@@ -125,8 +136,10 @@ struct osrc_server {
 
     void run();
     int admit_one(Slot &slot);
-    int run_batched(Slot &slot, Request *r);
-    int acquire_entry(Request *r, CacheEntry **out);
+    int start_batched(Slot &slot, Request *r);
+    void batched_body(Slot &slot, Request *r, CacheEntry *entry);
+    void finish_batched(Slot &slot);
+    int acquire_entry(Request *r, CacheEntry **out, cudaStream_t st);
     void release_slot_workspace(Slot &slot);
     bool evict_one();
     void finish_job(Slot &slot, int status);
@@ -168,7 +181,7 @@ void osrc_server::release_slot_workspace(Slot &slot) {
     slot.d_x.release();
 }
 
-int osrc_server::acquire_entry(Request *r, CacheEntry **out) {
+int osrc_server::acquire_entry(Request *r, CacheEntry **out, cudaStream_t st) {
     auto it = cache.find(r->key);
     if (it != cache.end()) {
         stats.cache_hits++;
@@ -181,7 +194,7 @@ int osrc_server::acquire_entry(Request *r, CacheEntry **out) {
     CacheEntry e;
     int s = osrc_mesh_create(ctx, r->verts.data(), r->nv, r->tris.data(), r->nt, &e.mesh);
     if (s != OSRC_OK) return s;
-    s = osrc_problem_create(e.mesh, &r->params, &e.pb, slots[0].st);
+    s = osrc_problem_create(e.mesh, &r->params, &e.pb, st);
     if (s != OSRC_OK) {
         osrc_mesh_destroy(e.mesh);
         return s;
@@ -204,14 +217,14 @@ int osrc_server::admit_one(Slot &slot) {
         if (pending.empty()) return OSRC_TIMEOUT;  // nothing to do
         r = pending.front();
     }
-    if (r->params.precision == OSRC_FP64_DENSE) return run_batched(slot, r);
+    if (r->params.precision == OSRC_FP64_DENSE) return start_batched(slot, r);
     // workspace: reuse the slot's clone if it serves the same problem
     CacheEntry *entry = nullptr;
     if (slot.entry && slot.entry_key == r->key) {
         entry = slot.entry;
     } else {
         release_slot_workspace(slot);
-        int s = acquire_entry(r, &entry);
+        int s = acquire_entry(r, &entry, slot.st);
         if (s != OSRC_OK) return s;
         const size_t need = estimate_work_bytes(r->nv, r->nt, r->params, r->maxit);
         while (ctx->budget && ctx->used + need > ctx->budget) {
@@ -259,14 +272,18 @@ int osrc_server::admit_one(Slot &slot) {
     return OSRC_OK;
 }
 
-// Solves every right-hand side of request r as blocks of up to BATCH_MAX on
-// the cached problem (the batched mixed-precision solve), to completion.
-// Returns OSRC_OUT_OF_MEMORY (request left queued) if the block's memory
-// cannot be found yet; otherwise the request is finished here.
-int osrc_server::run_batched(Slot &slot, Request *r) {
+// Starts a batched job: every right-hand side of request r, as blocks of up
+// to BATCH_MAX, by the batched mixed-precision solve on the cached problem.
+// The GPU work runs on a host thread of its own (the worker keeps advancing
+// the other slots); one batched job per resident problem at a time.  Returns
+// OSRC_OUT_OF_MEMORY or ADMIT_WAIT (request left queued) if it cannot start
+// yet.
+int osrc_server::start_batched(Slot &slot, Request *r) {
     release_slot_workspace(slot);  // the block runs on the resident problem, not on a clone
+    auto it = cache.find(r->key);
+    if (it != cache.end() && it->second.batched_busy) return ADMIT_WAIT;
     CacheEntry *entry = nullptr;
-    int s = acquire_entry(r, &entry);
+    int s = acquire_entry(r, &entry, slot.st);
     if (s != OSRC_OK) return s;
     entry->refs++;
     const int blk = std::min(r->nrhs, BATCH_MAX);
@@ -285,10 +302,25 @@ int osrc_server::run_batched(Slot &slot, Request *r) {
         pending.pop_front();
     }
     entry->last_use = ++tick;
+    entry->batched_busy = true;
     stats.jobs_started++;
     stats.batched_jobs++;
+    slot.req = r;
+    slot.busy = true;
+    slot.batched = true;
+    slot.bentry = entry;
+    slot.bdone = false;
+    slot.bth = std::thread([this, &slot, r, entry] { batched_body(slot, r, entry); });
+    return OSRC_OK;
+}
+
+// The GPU work of a batched job (its own host thread; touches only the job's
+// slot buffers, stream and problem, and the request's result).
+void osrc_server::batched_body(Slot &slot, Request *r, CacheEntry *entry) {
+    cudaSetDevice(ctx->device);
+    const int blk = std::min(r->nrhs, BATCH_MAX);
     const int n2 = 2 * r->nv;
-    int status = OSRC_OK;
+    int status = OSRC_OK, s;
     osrc_solve_info agg{};
     agg.converged = 1;
     if ((s = slot.d_b.alloc(ctx, (size_t)blk * n2)) || (s = slot.d_x.alloc(ctx, (size_t)blk * n2))) status = s;
@@ -320,27 +352,48 @@ int osrc_server::run_batched(Slot &slot, Request *r) {
         agg.total_iterations += bi.inner_iterations;
         agg.true_residual = fmax(agg.true_residual, bi.residual);
     }
+    std::lock_guard<std::mutex> lock(mu);
+    slot.bstatus = status;
+    slot.binfo = agg;
+    slot.bdone = true;
+}
+
+// Worker side of a finished batched job: joins its thread, releases its
+// buffers and finishes the request.
+void osrc_server::finish_batched(Slot &slot) {
+    if (slot.bth.joinable()) slot.bth.join();
     slot.d_b.release();
     slot.d_x.release();
+    CacheEntry *entry = slot.bentry;
     entry->refs--;
+    entry->batched_busy = false;
     if (ctx->used > stats.mem_peak) stats.mem_peak = ctx->used;
-    std::lock_guard<std::mutex> lock(mu);
-    r->info.iterations = agg.iterations;
-    r->info.total_iterations = agg.total_iterations;
-    r->info.true_residual = agg.true_residual;
-    r->info.precond_residual = agg.true_residual;
-    r->info.converged = agg.converged;
-    if (status == OSRC_OK && !agg.converged) status = OSRC_NOT_CONVERGED;
-    r->status = status;
-    r->rhs_done = r->nrhs;
-    r->inflight--;
-    r->finished = true;
-    r->t_done = Clock::now();
-    r->info.ms_total = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
-    stats.completed++;
-    if (status != OSRC_OK) stats.failed++;
-    cv.notify_all();
-    return OSRC_OK;
+    Request *r = slot.req;
+    int status = slot.bstatus;
+    const osrc_solve_info &agg = slot.binfo;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        r->info.iterations = agg.iterations;
+        r->info.total_iterations = agg.total_iterations;
+        r->info.true_residual = agg.true_residual;
+        r->info.precond_residual = agg.true_residual;
+        r->info.converged = agg.converged;
+        if (status == OSRC_OK && !agg.converged) status = OSRC_NOT_CONVERGED;
+        r->status = status;
+        r->rhs_done = r->nrhs;
+        r->inflight--;
+        r->finished = true;
+        r->t_done = Clock::now();
+        r->info.ms_total = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+        stats.completed++;
+        if (status != OSRC_OK) stats.failed++;
+        cv.notify_all();
+    }
+    slot.req = nullptr;
+    slot.bentry = nullptr;
+    slot.batched = false;
+    slot.bdone = false;
+    slot.busy = false;
 }
 
 void osrc_server::finish_job(Slot &slot, int status) {
@@ -397,7 +450,7 @@ void osrc_server::run() {
                 ++busy;
                 continue;
             }
-            if (a == OSRC_TIMEOUT) break;  // queue empty
+            if (a == OSRC_TIMEOUT || a == ADMIT_WAIT) break;  // queue empty, or its head must wait
             if (a == OSRC_OUT_OF_MEMORY && busy > 0) break;  // wait for memory
             if (a == OSRC_OUT_OF_MEMORY) {
                 // nothing runs: free everything idle and try once more
@@ -427,6 +480,18 @@ void osrc_server::run() {
         }
         if (busy > stats.active_peak) stats.active_peak = busy;
         for (Slot &s : slots) {
+            if (s.busy && s.batched) {
+                bool done;
+                {
+                    std::lock_guard<std::mutex> lock(mu);
+                    done = s.bdone;
+                }
+                if (done) {
+                    finish_batched(s);
+                    progress = true;
+                }
+                continue;
+            }
             if (!s.busy || !s.run.ready()) continue;
             const int st = s.run.advance();
             progress = true;
@@ -547,6 +612,8 @@ extern "C" void osrc_server_destroy(osrc_server *sv) {
     if (!sv) return;
     sv->stop.store(true);
     if (sv->worker.joinable()) sv->worker.join();
+    for (Slot &s : sv->slots)  // batched jobs still running finish first
+        if (s.bth.joinable()) s.bth.join();
     cudaSetDevice(sv->ctx->device);
     for (Slot &s : sv->slots) {
         if (s.st) cudaStreamSynchronize(s.st);

@@ -160,3 +160,37 @@ def test_server_batches_dense_requests(B):
         assert np.abs(xa - ref).max() <= 1e-8 * np.abs(ref).max()
     finally:
         S.close()
+
+
+def test_server_batched_requests_overlap(B):
+    """Batched requests on different meshes run concurrently (each on its own
+    host thread and stream); every result equals the same request served
+    alone, within the dense path's solution tolerance."""
+    meshes = [fibonacci_hull(n) for n in (150, 200, 250)]
+    dirs = np.array([[0.0, 0.0, 1.0], [0.6, 0.0, 0.8]])
+
+    def serve(jobs, max_active):
+        ctx = B.osrc_create(0, 0)
+        sv = B.osrc_server_create(ctx, max_active)
+        try:
+            ids = []
+            for v, t in jobs:
+                p = _params(B, 2.0, 3.0, 1.5)
+                p.precision = B.OSRC_FP64_DENSE
+                ids.append(B.osrc_server_submit(sv, v, t, p, dirs, tol=1e-10, maxit=300))
+            out = []
+            for rid, (v, t) in zip(ids, jobs):
+                assert B.osrc_server_wait(sv, rid, 300.0) == B.OSRC_OK
+                done, st, lat, info = B.osrc_server_poll(sv, rid)
+                assert done and st == B.OSRC_OK
+                out.append(B.osrc_server_result(sv, rid, len(dirs), v.shape[0])[1])
+            return out, B.osrc_server_get_stats(sv)
+        finally:
+            B.osrc_server_destroy(sv)
+            B.osrc_destroy(ctx)
+
+    alone = [serve([m], 1)[0][0] for m in meshes]
+    mixed, stats = serve(meshes, 3)
+    assert stats["batched_jobs"] == 3 and stats["active_peak"] >= 2
+    for a, x in zip(alone, mixed):
+        assert np.abs(x - a).max() <= 1e-8 * np.abs(a).max()
