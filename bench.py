@@ -289,7 +289,7 @@ def run_ours(args, D):
     sol_diff = float(np.linalg.norm(hxn.ravel() - x.cpu().numpy().ravel()) /
                      np.linalg.norm(x.cpu().numpy().ravel()))
 
-    field = run_field(S, x, W, B) if D.rank == 0 else None
+    field = run_field(S, x, W, B) if D.world == 1 else None
     far_pairs = B.osrc_far_pairs(S.pb)
     far_avg_ms = far_ms / max(far_n, 1)
     achieved = FLOPS_PER_PAIR * far_pairs / (far_avg_ms * 1e-3) / 1e12
@@ -337,15 +337,18 @@ def run_ours(args, D):
     if peaks is not None:
         out["measured_peaks_file"] = True
     S.close()
-    if D.rank == 0:
+    # single-GPU legs: only when one GPU runs the bench (a multi-GPU run
+    # measures the replicated headline solve and holds the other GPUs for it only)
+    single = D.world == 1
+    if single:
         out["small_dense"] = run_small_dense(D.local)
-    if args.dense_rhs > 0 and D.rank == 0:
+    if args.dense_rhs > 0 and single:
         out["dense_batched"] = run_dense(args.dense_rhs, args.dense_matfree_rhs, D.local)
-    if not args.no_large and D.rank == 0:
+    if not args.no_large and single:
         out["large"] = run_large(D.local)
-    if not args.no_objects and D.rank == 0:
+    if not args.no_objects and single:
         out["four_spheres"] = run_four_spheres(D.local)
-    if args.serve_requests > 0 and D.rank == 0:
+    if args.serve_requests > 0 and single:
         out["serving"] = run_serving(args.serve_requests, D.local)
         out["serving_batched"] = run_serving(args.serve_requests, D.local, batched=True)
     return out, (infos[-1]["iterations"] if infos else REF_ITERATIONS)

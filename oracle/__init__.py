@@ -27,7 +27,7 @@ Functions and the passages they follow:
                       the same for disjoint objects with their own materials
                       (Sec. 2.2, multiple scattering)
 
-Readings where the paper is silent or ambiguous (each is listed in the design doc):
+Readings where the paper is silent or ambiguous:
 quadrature orders (6-point rule for separated pairs, Sauter-Schwab with n
 Gauss points per dimension for touching ones); the Pade coefficients and the
 NtD form; the damping length R; the strong form of the preconditioned system.

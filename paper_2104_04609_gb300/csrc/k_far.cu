@@ -272,7 +272,7 @@ __device__ __forceinline__ CenterPair center_pair(const float4 &cth, const float
 // float-float arithmetic once per triangle pair.
 // MULTI: m1 multiplies the interior terms (0: source on another object, -1:
 // Mueller); k1i / dk1i: imaginary parts of k1 and k1^2 / rho (attenuation).
-template <bool CENTRED, bool MULTI>
+template <bool CENTRED, bool MULTI, bool ABSORB>
 __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, const f2 &P5, f2 mnx,
                                           f2 mny, f2 mnz, f2 wq2, const FarConst2 &c,
                                           const CenterPair &cp, f2 m1, f2 k1i, f2 dk1i, PairAcc &A) {
@@ -326,9 +326,13 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
         __sincosf(kr1.y, &s1.y, &c1.y);
     }
     f2 br = make_float2(0.f, 0.f);
+    constexpr bool absorb = MULTI && ABSORB;
     if (MULTI) {  // e^{i k1 r} with k1 = k1r + i k1i: damping e^{-k1i r}, and m1
-        br = mul2(r, k1i);
-        const f2 damp = mul2(m1, make_float2(__expf(-br.x), __expf(-br.y)));
+        f2 damp = m1;
+        if (absorb) {
+            br = mul2(r, k1i);
+            damp = mul2(m1, make_float2(__expf(-br.x), __expf(-br.y)));
+        }
         c1 = mul2(c1, damp);
         s1 = mul2(s1, damp);
     }
@@ -342,7 +346,7 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
     A.u1i = fma2(gpr, psi, fma2(gpi, psr, A.u1i));
     // D normal term (k0^2 G0 + k1^2/rho G1) phi
     f2 gkr0 = fma2(c.dk1, c1, mul2(c.dk0, c0)), gki0 = fma2(c.dk1, s1, mul2(c.dk0, s0));
-    if (MULTI) {  // complex k1^2 / rho
+    if (absorb) {  // complex k1^2 / rho
         gkr0 = fma2(mul2(dk1i, s1), dup2(-1.f), gkr0);
         gki0 = fma2(dk1i, c1, gki0);
     }
@@ -358,7 +362,7 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
     //   re = (c0 + c1 + kr0 s0 + kr1 s1) / r^3,  im = (s0 + s1 - kr0 c0 - kr1 c1) / r^3
     f2 hp0 = fma2(kr1, s1, fma2(kr0, s0, add2(c0, c1)));
     f2 hq0 = fma2(nkr1, c1, fma2(nkr0, c0, add2(s0, s1)));
-    if (MULTI) {  // (i k1 r - 1) with Im k1: + k1i r (c1, s1)
+    if (absorb) {  // (i k1 r - 1) with Im k1: + k1i r (c1, s1)
         hp0 = fma2(br, c1, hp0);
         hq0 = fma2(br, s1, hq0);
     }
@@ -385,8 +389,9 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
 // float-float centroids (see far_pair2).
 // MULTI: disjoint objects (Sec. 2.2) or the Mueller formulation; the interior
 // constants are the test triangle's object's, interior terms vanish for
-// sources on other objects and change sign for Mueller.
-template <bool CENTRED, bool MULTI>
+// sources on other objects and change sign for Mueller.  ABSORB (with MULTI):
+// complex interior wavenumbers (attenuation).
+template <bool CENTRED, bool MULTI, bool ABSORB>
 __global__ void __launch_bounds__(FAR_THREADS, 4)
 far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
            const float4 *__restrict__ tn, const int4 *__restrict__ tv,
@@ -486,7 +491,7 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
             const f2 m1 = dup2(MULTI ? (shComp[s] != ct ? 0.f : sgn) : 1.f);
 #pragma unroll
             for (int q = 0; q < 6; ++q)
-                far_pair2<CENTRED, MULTI>(X, Y, Z, &shP[30 * s + 5 * q], shP5[6 * s + q], mnx, mny, mnz,
+                far_pair2<CENTRED, MULTI, ABSORB>(X, Y, Z, &shP[30 * s + 5 * q], shP5[6 * s + q], mnx, mny, mnz,
                                           q < 3 ? W1 : W2, c, cp, m1, k1i, dk1i, A);
             // u1 += (x - y).n_y T1 = (-(x - y).n_y)(-T1);  u2 += (-n_x.n_y) U
             A.u1r = fma2(xnyn, A.t1r, A.u1r);
@@ -609,9 +614,9 @@ int far_setup_geometry(osrc_problem *pb, cudaStream_t st) {
     int dev = m->ctx->device, sms = 0, per_sm = 0;
     OSRC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (pb->far_reduce)
-        OSRC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far_kernel<true, false>, FAR_THREADS, 0));
+        OSRC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far_kernel<true, false, false>, FAR_THREADS, 0));
     else
-        OSRC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far_kernel<false, false>, FAR_THREADS, 0));
+        OSRC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, far_kernel<false, false, false>, FAR_THREADS, 0));
     if (per_sm < 1) per_sm = 1;
     const int bx = (pb->npts / 2 + FAR_THREADS - 1) / FAR_THREADS;
     const int slots = sms * per_sm;
@@ -674,22 +679,17 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
         const int *tc = m->d_tcomp.p;
         const FarObj *fo = pb->d_fobj.p;
         float *prt = pb->d_part.p;
-        if (pb->far_reduce && pb->far_obj)
-            far_kernel<true, true><<<grid, FAR_THREADS, 0, st>>>(pts, pb->d_cen.p, pb->d_tn.p, pb->d_tv.p, pb->d_sP.p,
-                                                                 pb->d_sP5.p, pb->d_sC.p, nt, npts, tps, c, kff, tc,
-                                                                 fo, prt);
-        else if (pb->far_reduce)
-            far_kernel<true, false><<<grid, FAR_THREADS, 0, st>>>(pts, pb->d_cen.p, pb->d_tn.p, pb->d_tv.p, pb->d_sP.p,
-                                                                  pb->d_sP5.p, pb->d_sC.p, nt, npts, tps, c, kff, tc,
-                                                                  fo, prt);
-        else if (pb->far_obj)
-            far_kernel<false, true><<<grid, FAR_THREADS, 0, st>>>(pts, pb->d_cen.p, pb->d_tn.p, pb->d_tv.p, pb->d_sP.p,
-                                                                  pb->d_sP5.p, pb->d_sC.p, nt, npts, tps, c, kff, tc,
-                                                                  fo, prt);
-        else
-            far_kernel<false, false><<<grid, FAR_THREADS, 0, st>>>(pts, pb->d_cen.p, pb->d_tn.p, pb->d_tv.p,
-                                                                   pb->d_sP.p, pb->d_sP5.p, pb->d_sC.p, nt, npts, tps,
-                                                                   c, kff, tc, fo, prt);
+        const bool ab = pb->absorb;
+#define OSRC_FAR_LAUNCH(C, M, A)                                                                               \
+    far_kernel<C, M, A><<<grid, FAR_THREADS, 0, st>>>(pts, pb->d_cen.p, pb->d_tn.p, pb->d_tv.p, pb->d_sP.p,      \
+                                                      pb->d_sP5.p, pb->d_sC.p, nt, npts, tps, c, kff, tc, fo, prt)
+        if (pb->far_reduce && pb->far_obj && ab) OSRC_FAR_LAUNCH(true, true, true);
+        else if (pb->far_reduce && pb->far_obj) OSRC_FAR_LAUNCH(true, true, false);
+        else if (pb->far_reduce) OSRC_FAR_LAUNCH(true, false, false);
+        else if (pb->far_obj && ab) OSRC_FAR_LAUNCH(false, true, true);
+        else if (pb->far_obj) OSRC_FAR_LAUNCH(false, true, false);
+        else OSRC_FAR_LAUNCH(false, false, false);
+#undef OSRC_FAR_LAUNCH
         pb->launches++;
         if (pb->prof_on) {
             OSRC_CK(cudaEventRecord(pb->prof_ev[1], st));

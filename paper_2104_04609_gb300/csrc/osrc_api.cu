@@ -396,7 +396,8 @@ static int problem_create(osrc_mesh *mesh, const osrc_params *prm, const double 
         {
             const double R = p.damping_R > 0.0 ? p.damping_R : mesh->mean_edge;
             pb->multi = mesh->ncomp > 1;
-            pb->far_obj = pb->multi || p.formulation == OSRC_MULLER || p.k_int_im != 0.0;
+            pb->absorb = p.k_int_im != 0.0;
+            pb->far_obj = pb->multi || p.formulation == OSRC_MULLER || pb->absorb;
             const float sgn = p.formulation == OSRC_MULLER ? -1.f : 1.f;
             pb->obj.resize(mesh->ncomp);
             std::vector<FarObj> fo(mesh->ncomp);
@@ -906,6 +907,7 @@ int problem_clone(osrc_problem *m, osrc_problem **out) {
     c->g = m->g;
     c->multi = m->multi;
     c->far_obj = m->far_obj;
+    c->absorb = m->absorb;
     c->obj = m->obj;
     c->d_obj.borrow(m->d_obj);
     c->d_fobj.borrow(m->d_fobj);

@@ -193,6 +193,7 @@ struct osrc_problem {
     // ---- disjoint objects with their own materials --------------------------------
     bool multi = false;          // more than one object: interior terms within objects only
     bool far_obj = false;        // far kernel with per-object constants (objects or Mueller)
+    bool absorb = false;         // some object has a complex interior wavenumber
     std::vector<ObjMat> obj;     // [ncomp]
     DBuf<ObjMat> d_obj;
     DBuf<FarObj> d_fobj;
