@@ -296,12 +296,9 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
     const f2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
     const f2 r = mul2(r2, ri);
     const f2 ri2 = mul2(ri, ri);
-    const f2 ri3 = mul2(ri2, ri);
     f2 dnxn = mul2(dx, mnx);  // (y - x).n_x
     dnxn = fma2(dy, mny, dnxn);
     dnxn = fma2(dz, mnz, dnxn);
-    const f2 kr0 = mul2(r, c.k0), kr1 = mul2(r, c.k1);
-    const f2 nkr0 = mul2(r, c.nk0), nkr1 = mul2(r, c.nk1);
     f2 s0, c0, s1, c1;
     if (CENTRED) {
         f2 num = mul2(ddx, ddx);
@@ -320,6 +317,7 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
         __sincosf(ph1.x, &s1.x, &c1.x);
         __sincosf(ph1.y, &s1.y, &c1.y);
     } else {
+        const f2 kr0 = mul2(r, c.k0), kr1 = mul2(r, c.k1);
         __sincosf(kr0.x, &s0.x, &c0.x);
         __sincosf(kr0.y, &s0.y, &c0.y);
         __sincosf(kr1.x, &s1.x, &c1.x);
@@ -340,34 +338,33 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
     const f2 phr = hi2(P3), phi = lo2(P4), mphr = hi2(P4), mphi = P5;
     (void)mpsr;
     (void)mphr;
+    // cos and sin scaled by 1/r once: G = (c + i s)/r for every kernel below
+    const f2 c0r = mul2(c0, ri), s0r = mul2(s0, ri), c1r = mul2(c1, ri), s1r = mul2(s1, ri);
     // V block (G0 + rho G1) psi, without 1/(4 pi)
-    const f2 gpr = mul2(fma2(c.rho, c1, c0), ri), gpi = mul2(fma2(c.rho, s1, s0), ri);
+    const f2 gpr = fma2(c.rho, c1r, c0r), gpi = fma2(c.rho, s1r, s0r);
     A.u1r = fma2(gpr, psr, fma2(gpi, mpsi, A.u1r));
     A.u1i = fma2(gpr, psi, fma2(gpi, psr, A.u1i));
     // D normal term (k0^2 G0 + k1^2/rho G1) phi
-    f2 gkr0 = fma2(c.dk1, c1, mul2(c.dk0, c0)), gki0 = fma2(c.dk1, s1, mul2(c.dk0, s0));
+    f2 gkr = fma2(c.dk1, c1r, mul2(c.dk0, c0r)), gki = fma2(c.dk1, s1r, mul2(c.dk0, s0r));
     if (absorb) {  // complex k1^2 / rho
-        gkr0 = fma2(mul2(dk1i, s1), dup2(-1.f), gkr0);
-        gki0 = fma2(dk1i, c1, gki0);
+        gkr = fma2(mul2(dk1i, s1r), dup2(-1.f), gkr);
+        gki = fma2(dk1i, c1r, gki);
     }
-    const f2 gkr = mul2(gkr0, ri);
-    const f2 gki = mul2(gki0, ri);
     A.ur = fma2(gkr, phr, fma2(gki, mphi, A.ur));
     A.ui = fma2(gkr, phi, fma2(gki, phr, A.ui));
     // D curl term: sum_q w_q (G0 + G1/rho)
-    const f2 wr = mul2(wq2, ri);
-    A.t3r = fma2(fma2(c.irho, c1, c0), wr, A.t3r);
-    A.t3i = fma2(fma2(c.irho, s1, s0), wr, A.t3i);
-    // -(H0 + H1), H = e^{ikr} (i k r - 1) / r^3:
-    //   re = (c0 + c1 + kr0 s0 + kr1 s1) / r^3,  im = (s0 + s1 - kr0 c0 - kr1 c1) / r^3
-    f2 hp0 = fma2(kr1, s1, fma2(kr0, s0, add2(c0, c1)));
-    f2 hq0 = fma2(nkr1, c1, fma2(nkr0, c0, add2(s0, s1)));
-    if (absorb) {  // (i k1 r - 1) with Im k1: + k1i r (c1, s1)
-        hp0 = fma2(br, c1, hp0);
-        hq0 = fma2(br, s1, hq0);
+    A.t3r = fma2(fma2(c.irho, c1r, c0r), wq2, A.t3r);
+    A.t3i = fma2(fma2(c.irho, s1r, s0r), wq2, A.t3i);
+    // -(H0 + H1), H = e^{ikr} (i k r - 1) / r^3, written with the scaled c, s:
+    //   re = (c0/r + c1/r + k0 s0 + k1 s1) / r^2,  im = (s0/r + s1/r - k0 c0 - k1 c1) / r^2
+    f2 hp0 = fma2(c.k1, s1, fma2(c.k0, s0, add2(c0r, c1r)));
+    f2 hq0 = fma2(c.nk1, c1, fma2(c.nk0, c0, add2(s0r, s1r)));
+    if (absorb) {  // (i k1 r - 1) with Im k1: + k1i r (c1, s1) / r
+        hp0 = fma2(k1i, c1, hp0);
+        hq0 = fma2(k1i, s1, hq0);
     }
-    const f2 hp = mul2(hp0, ri3);
-    const f2 hq = mul2(hq0, ri3);
+    const f2 hp = mul2(hp0, ri2);
+    const f2 hq = mul2(hq0, ri2);
     A.t1r = fma2(hp, phr, fma2(hq, mphi, A.t1r));  // T1n = -sum Hs phi
     A.t1i = fma2(hp, phi, fma2(hq, phr, A.t1i));
     // T block: (H0 + H1)(x - y).n_x psi = (-(H0 + H1)) (y - x).n_x psi
