@@ -35,12 +35,12 @@ METRIC = "OSRC-PMCHWT solves/s to 1e-5 residual"
 UNIT = "solves/s"
 TOL = 1e-5
 # FP32 flops (FMA = 2) of one far-field point pair, both wavenumbers, as the
-# factored evaluation of the far kernel performs it: 32 FMA, 16 MUL, 5 ADD
+# factored evaluation of the far kernel performs it: 32 FMA, 14 MUL, 5 ADD
 # (distance, 1/r and 1/r^2, (y - x).n_x, k r for both k, cos and sin of both
-# phases scaled by 1/r, then the V, D-normal, D-curl, H and T/K
-# accumulations); 5 MUFU operations (1 rsqrt, 2 sin, 2 cos) and their
-# argument scaling come on top and are not counted.
-FLOPS_PER_PAIR = 85
+# phases scaled by 1/r, then the V, D-normal (scale k0^2 taken out per source
+# triangle), D-curl, H and T/K accumulations); 5 MUFU operations (1 rsqrt,
+# 2 sin, 2 cos) and their argument scaling come on top and are not counted.
+FLOPS_PER_PAIR = 83
 # nominal count for a per-operator evaluation (V, K, T, D separately per
 # wavenumber), reported beside the main figure
 FLOPS_PER_PAIR_NOMINAL = 176
@@ -50,9 +50,9 @@ FLOPS_PER_PAIR_NOMINAL = 176
 REF_ITERATIONS = 47
 # DRAM bytes (read + write) of one far_kernel<0, 0, 0> launch at this
 # workload, from one ncu capture of this command (dram__bytes_read.sum
-# 15,454,464 + dram__bytes_write.sum 256, the ncu summary of the far kernel
+# 15,393,536 + dram__bytes_write.sum 2,816, the ncu summary of the far kernel
 # kept with the profiles); to be retaken whenever the far kernel changes
-FAR_TRAFFIC_BYTES = 15454720
+FAR_TRAFFIC_BYTES = 15396352
 
 
 def parse():
@@ -549,11 +549,11 @@ def run_field(S, x, W, B):
 # --------------------------------------------------------------------------
 SMALL_WORKLOAD = "sphere642"
 LARGE_WORKLOAD = "bumpy80000"
-# FP32 flops per far point pair of the large-ka (centred) variant: the 85 of the
+# FP32 flops per far point pair of the large-ka (centred) variant: the 83 of the
 # plain kernel less its 2 MUL for k r, plus 21 for the phase from the centroid
 # distance (3 ADD for the offsets, r^2 - r_c^2 in 2 x (1 MUL + 2 FMA) + 1 FMA,
 # 1 ADD and 1 MUL for r - r_c, one FMA per wavenumber for the phase)
-FLOPS_PER_PAIR_CENTRED = 104
+FLOPS_PER_PAIR_CENTRED = 102
 
 
 def run_small_dense(device):

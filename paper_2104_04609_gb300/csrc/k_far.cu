@@ -172,7 +172,10 @@ __device__ __forceinline__ f2 hi2(const float4 &v) { return make_float2(v.z, v.w
 __device__ __forceinline__ f2 neg2(f2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ f2 dup2(float a) { return make_float2(a, a); }
 
-// Constants as (value, value) pairs for the packed instructions.
+// Constants as (value, value) pairs for the packed instructions.  The D
+// normal term k0^2 G0 + (k1^2/rho) G1 is evaluated as dks (G0 + dk1 G1):
+// dk0 holds the scale dks (applied once per source triangle) and dk1 the
+// ratio (k1^2/rho) / dks.
 struct FarConst2 {
     f2 k0, k1, nk0, nk1, rho, irho, dk0, dk1;
 };
@@ -344,9 +347,10 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
     const f2 gpr = fma2(c.rho, c1r, c0r), gpi = fma2(c.rho, s1r, s0r);
     A.u1r = fma2(gpr, psr, fma2(gpi, mpsi, A.u1r));
     A.u1i = fma2(gpr, psi, fma2(gpi, psr, A.u1i));
-    // D normal term (k0^2 G0 + k1^2/rho G1) phi
-    f2 gkr = fma2(c.dk1, c1r, mul2(c.dk0, c0r)), gki = fma2(c.dk1, s1r, mul2(c.dk0, s0r));
-    if (absorb) {  // complex k1^2 / rho
+    // D normal term (k0^2 G0 + k1^2/rho G1) phi, as (G0 + dk1 G1) phi; the
+    // scale dks is applied per source triangle
+    f2 gkr = fma2(c.dk1, c1r, c0r), gki = fma2(c.dk1, s1r, s0r);
+    if (absorb) {  // complex k1^2 / (rho dks)
         gkr = fma2(mul2(dk1i, s1r), dup2(-1.f), gkr);
         gki = fma2(dk1i, c1r, gki);
     }
@@ -381,7 +385,8 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
 //   u2 = sum [ (H0 + H1)(x - y).n_x psi_q - (n_x.n_y)(k0^2 G0 + k1^2/rho G1) phi_q ]
 //   A  = sum_s (sum_q w_q (G0 + G1/rho)) c_s
 // with G, H here without the factor 1/(4 pi) (applied in the gather).  Sums
-// run per 64-triangle tile, then tile sums are added to running sums.
+// run per 64-triangle tile, then tile sums are added to running sums kept in
+// part.
 // CENTRED: pt holds offsets from the test-triangle centroid and cen the
 // float-float centroids (see far_pair2).
 // MULTI: disjoint objects (Sec. 2.2) or the Mueller formulation; the interior
@@ -442,10 +447,6 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
         ctl = cen[2 * tau + 1];
     }
 
-    f2 run[10];
-#pragma unroll
-    for (int i = 0; i < 10; ++i) run[i] = make_float2(0.f, 0.f);
-
     for (int t0 = s_begin; t0 < s_end; t0 += FAR_TS) {
         const int cnt = min(FAR_TS, s_end - t0);
         __syncthreads();
@@ -493,7 +494,7 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
             // u1 += (x - y).n_y T1 = (-(x - y).n_y)(-T1);  u2 += (-n_x.n_y) U
             A.u1r = fma2(xnyn, A.t1r, A.u1r);
             A.u1i = fma2(xnyn, A.t1i, A.u1i);
-            const f2 nn = dup2(nxnyn);
+            const f2 nn = dup2(nxnyn * c.dk0.x);
             A.u2r = fma2(nn, A.ur, A.u2r);
             A.u2i = fma2(nn, A.ui, A.u2i);
             const float4 C0 = shC[5 * s], C1 = shC[5 * s + 1], C2 = shC[5 * s + 2];
@@ -505,18 +506,23 @@ far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
             A.azr = fma2(A.t3r, lo2(C3), fma2(A.t3i, lo2(C4), A.azr));
             A.azi = fma2(A.t3r, hi2(C3), fma2(A.t3i, lo2(C3), A.azi));
         }
-        run[0] = add2(run[0], A.u1r); run[1] = add2(run[1], A.u1i);
-        run[2] = add2(run[2], A.u2r); run[3] = add2(run[3], A.u2i);
-        run[4] = add2(run[4], A.axr); run[5] = add2(run[5], A.axi);
-        run[6] = add2(run[6], A.ayr); run[7] = add2(run[7], A.ayi);
-        run[8] = add2(run[8], A.azr); run[9] = add2(run[9], A.azi);
-    }
-    if (active) {
+        // running sums live in the output: the first tile stores, later
+        // tiles add (the thread's own entries; registers stay free for the
+        // pair loop)
+        if (active) {
+            const f2 v[10] = {A.u1r, A.u1i, A.u2r, A.u2i, A.axr, A.axi, A.ayr, A.ayi, A.azr, A.azi};
+            f2 *pp = reinterpret_cast<f2 *>(part);
 #pragma unroll
-        for (int i = 0; i < 10; ++i) {
-            part[((size_t)split * 10 + i) * npts + p0] = run[i].x;
-            part[((size_t)split * 10 + i) * npts + p0 + 1] = run[i].y;
+            for (int i = 0; i < 10; ++i) {
+                const size_t o = (((size_t)split * 10 + i) * npts + p0) / 2;
+                pp[o] = t0 == s_begin ? v[i] : add2(pp[o], v[i]);
+            }
         }
+    }
+    if (active && s_begin >= s_end) {  // empty split: zero sums
+        f2 *pp = reinterpret_cast<f2 *>(part);
+#pragma unroll
+        for (int i = 0; i < 10; ++i) pp[(((size_t)split * 10 + i) * npts + p0) / 2] = make_float2(0.f, 0.f);
     }
 }
 
@@ -659,8 +665,8 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
         c.nk1 = d2(-k1);
         c.rho = d2(rho);
         c.irho = d2(1.0 / rho);
-        c.dk0 = d2(k0 * k0);
-        c.dk1 = d2(k1 * k1 / rho);
+        c.dk0 = d2(pb->far_dks);
+        c.dk1 = d2(k1 * k1 / rho / pb->far_dks);
         // k / (2 pi) as float pairs (hi, lo) for the float-float phases
         const double q0 = k0 * inv2pi, q1 = k1 * inv2pi;
         const float q0h = (float)q0, q1h = (float)q1;

@@ -402,6 +402,12 @@ static int problem_create(osrc_mesh *mesh, const osrc_params *prm, const double 
             pb->obj.resize(mesh->ncomp);
             std::vector<FarObj> fo(mesh->ncomp);
             std::vector<double2> ike(2 * (size_t)mesh->ncomp);
+            double dk1_max = 0.0;
+            for (int m = 0; m < mesh->ncomp; ++m) {
+                const std::complex<double> k1c(k_int_obj[m], p.k_int_im);
+                dk1_max = std::fmax(dk1_max, std::abs(k1c * k1c / rho_obj[m]));
+            }
+            pb->far_dks = far_dnormal_scale(p.k_ext, dk1_max);
             for (int m = 0; m < mesh->ncomp; ++m) {
                 ObjMat &o = pb->obj[m];
                 o.k1 = k_int_obj[m];
@@ -419,8 +425,8 @@ static int problem_create(osrc_mesh *mesh, const osrc_params *prm, const double 
                 const double q = o.k1 * 0.15915494309189533577;
                 const std::complex<double> k1c(o.k1, o.k1i), dk1 = k1c * k1c / o.rho;
                 fo[m] = FarObj{(float)o.k1, (float)-o.k1, (float)o.rho, (float)(1.0 / o.rho),
-                               (float)dk1.real(), (float)q, (float)(q - (double)(float)q), sgn,
-                               (float)o.k1i, (float)dk1.imag()};
+                               (float)(dk1.real() / pb->far_dks), (float)q, (float)(q - (double)(float)q),
+                               sgn, (float)o.k1i, (float)(dk1.imag() / pb->far_dks)};
             }
             if ((s = pb->d_obj.alloc(ctx, mesh->ncomp)) || (s = pb->d_fobj.alloc(ctx, mesh->ncomp)) ||
                 (s = pb->d_obj_ike.alloc(ctx, 2 * (size_t)mesh->ncomp)))
@@ -907,6 +913,7 @@ int problem_clone(osrc_problem *m, osrc_problem **out) {
     c->g = m->g;
     c->multi = m->multi;
     c->far_obj = m->far_obj;
+    c->far_dks = m->far_dks;
     c->absorb = m->absorb;
     c->obj = m->obj;
     c->d_obj.borrow(m->d_obj);

@@ -7,6 +7,7 @@
 
 #include <string>
 #include <atomic>
+#include <cmath>
 #include <vector>
 
 #include "../../include/osrc_pmchwt.h"
@@ -124,8 +125,16 @@ struct ObjMat {
 // built per thread): k1, -k1, rho, 1/rho, k1^2/rho, k1/(2 pi) as float-float.
 struct FarObj {
     float k1, nk1, rho, irho, dk1, k1h, k1l, sgn;  // sgn: +1 PMCHWT, -1 Mueller
-    float k1i, dk1i;  // attenuation: Im k1 and Im(k1^2 / rho) (dk1 holds the real part)
+    float k1i, dk1i;  // attenuation: Im k1; dk1, dk1i: Re and Im of (k1^2 / rho) / far_dks
 };
+
+// Scale dks of the far kernel's D normal term k0^2 G0 + (k1^2/rho) G1 =
+// dks (G0 + (k1^2/rho)/dks G1): k0^2, raised to 1e-20 max|k1^2/rho| so that
+// the ratio stays below 1e20 (a G0 coefficient changed by less than 1e-20 of
+// the G1 coefficient is below FP32 resolution).
+inline double far_dnormal_scale(double k0, double dk1_abs_max) {
+    return std::fmax(k0 * k0, 1e-20 * dk1_abs_max);
+}
 
 // Touching triangle pair for the Sauter-Schwab kernel.
 struct NearPair {
@@ -192,6 +201,7 @@ struct osrc_problem {
     double *h_res = nullptr;  // pinned host block: doubles [0, 16), then ints (inner status)
     // ---- disjoint objects with their own materials --------------------------------
     bool multi = false;          // more than one object: interior terms within objects only
+    double far_dks = 1.0;        // scale of the far kernel's D normal term (far_dnormal_scale)
     bool far_obj = false;        // far kernel with per-object constants (objects or Mueller)
     bool absorb = false;         // some object has a complex interior wavenumber
     std::vector<ObjMat> obj;     // [ncomp]

@@ -285,6 +285,22 @@ def test_low_frequency(B, small):
         S.close()
 
 
+@pytest.mark.parametrize("k0,k1", [(1e-12, 3.0), (3.0, 1e-12)])
+def test_extreme_wavenumber_ratio(B, small, k0, k1):
+    """One wavenumber 1e-12 against 3: the far kernel writes its D normal term
+    k0^2 G0 + (k1^2/rho) G1 as s (G0 + ratio G1) with s >= 1e-20 (k1^2/rho),
+    so neither the scale underflows nor the ratio overflows in FP32."""
+    v, t, _ = small
+    S = B.Solver(v, t, k0, k1, RHO)
+    try:
+        far = O.pmchwt_matrix(v, t, k0, k1, RHO, nss=S.params.n_ss, part=1)
+        x = _rand(2 * v.shape[0], 23)
+        y = _apply(B, S, x, part=B.OSRC_PART_FAR)
+        assert _rel(y, far @ x) < 1e-5
+    finally:
+        S.close()
+
+
 def test_invalid_arguments_rejected(B, small):
     v, t, S = small
     x = torch.zeros((1, 2 * v.shape[0]), dtype=torch.complex128, device="cuda")
