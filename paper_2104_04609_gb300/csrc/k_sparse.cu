@@ -16,8 +16,12 @@
 // Jacobi-preconditioned and stop at |r| <= tol |f|.  All loops are bounded by
 // the iteration cap; every CTA of a cluster takes the same branch because
 // the decisions are made from cluster-reduced values summed in rank order.
+// Two kernels share this layout: kmix_kernel (FP32 inner solves refined in
+// FP64, used whenever a CTA's rows and FP32 entries fit) and kry_kernel
+// (all FP64: larger meshes, in-place systems, the allocation-free entry).
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "osrc_internal.cuh"
@@ -255,6 +259,277 @@ kry_kernel(KryBatch batch, int n, const int *__restrict__ ptr, const int *__rest
     }
 }
 
+// ---- mixed-precision refinement ---------------------------------------------
+// The same systems (alpha M + beta S) w = f, solved by iterative refinement
+// in the same cluster layout: an FP32 Jacobi-CG/COCG solve of A d = r, with
+// the FP32 copy of A built once per launch in shared memory and r scaled to
+// unit norm, reduces the residual by KMIX_INNER_TOL; then the FP64 solution
+// is updated, x += d, and the FP64 residual r = f - A x decides: stop when
+// |r| <= tol |f| (the criterion of kry_kernel, here on the true residual),
+// else refine again.  Most arithmetic runs on the FP32 pipe, which on this
+// part issues 64 times the FP64 rate; a refinement costs one FP64 product.
+// Refinement converges while cond(D^-1 A) * 2^-24 stays well below one (the
+// OSRC and mass systems sit near cond 10..100); a refinement that fails to
+// halve the residual norm ends the solve as not converged.
+constexpr int KMIX_THREADS = 512;          // at most, per CTA (two CTAs per SM)
+constexpr int KMIX_ROWS_PER_THREAD = 2;    // rows a thread owns, at most
+constexpr float KMIX_INNER_TOL = 1e-5f;    // residual reduction of one FP32 solve
+constexpr int KMIX_MAX_REFINE = 40;
+constexpr size_t KMIX_SMEM_MAX = 200 * 1024;
+
+// Cluster-wide sums of NV values, identical in every thread of every CTA of
+// the cluster: butterflies within each warp, the warp sums added by a
+// butterfly in warp 0, then the CTA sums of all ranks (lane r reads rank r's
+// slot through distributed shared memory) added by a butterfly in warp 0.
+// IEEE addition is commutative, so every lane of a butterfly ends with the
+// same bits, and every CTA adds the same rank-ordered values.  A slot may be
+// written again once every CTA has passed one more cluster barrier.
+template <typename T, int NV>
+__device__ __forceinline__ void kmix_csum(cg::cluster_group &cl, T (&v)[NV], T *wred, T *slot, T *out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) wred[NV * wid + k] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+        T w[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) w[k] = lane < nw ? wred[NV * lane + k] : T(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) w[k] += __shfl_xor_sync(0xffffffffu, w[k], o);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) slot[k] = w[k];
+    }
+    cl.sync();
+    if (wid == 0) {
+        const unsigned cs = cl.num_blocks();
+        T w[NV];
+        if ((unsigned)lane < cs) {
+            const T *rem = cl.map_shared_rank(slot, lane);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) w[k] = rem[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) w[k] = T(0);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) w[k] += __shfl_xor_sync(0xffffffffu, w[k], o);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) out[k] = w[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = out[k];
+}
+
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 f2dot(float2 a, float2 b, int conj) {
+    return conj ? make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x) : f2mul(a, b);
+}
+__device__ __forceinline__ float2 f2div(float2 a, float2 b) {
+    const float den = b.x * b.x + b.y * b.y;
+    return make_float2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+
+// One cluster per system, rows [r0, r1) per CTA, row r0 + tid + k blockDim.x
+// for k < RPT per thread.  Dynamic shared memory: the CTA's CSR entries of
+// A in FP32 (float2) followed by their columns.  work32: n float2 per
+// system, the published FP32 search direction.  sy.x holds the published
+// FP64 solution.  Status and residual as kry_kernel; the iteration count is
+// the number of FP32 iterations over all refinements.
+template <int RPT>
+__global__ void __launch_bounds__(KMIX_THREADS, 2)
+kmix_kernel(KryBatch batch, int n, const int *__restrict__ ptr, const int *__restrict__ col,
+            const double *__restrict__ M, const double *__restrict__ S, float2 *__restrict__ work32,
+            double tol, int maxit, int *__restrict__ stat, double *__restrict__ res_out) {
+    extern __shared__ __align__(16) unsigned char kmix_dyn[];
+    __shared__ float wredf[3 * 32];
+    __shared__ double wredd[32];
+    __shared__ float slotP[2], slotR[3], slotI[3], outf[3];
+    __shared__ double slotD[1], slotB[1], outd[1];
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned cs = cl.num_blocks();
+    const unsigned rank = cl.block_rank();
+    const int sid = blockIdx.x / cs;
+    const KrySys sy = batch.s[sid];
+    const int rows = (n + cs - 1) / cs;
+    const int r0 = min(n, (int)rank * rows), r1 = min(n, r0 + rows);
+    const int ebase = r0 < n ? ptr[r0] : 0;
+    const int ne = r0 < r1 ? ptr[r1] - ebase : 0;
+    float2 *As = reinterpret_cast<float2 *>(kmix_dyn);
+    int *Cs = reinterpret_cast<int *>(kmix_dyn + sizeof(float2) * (size_t)((ne + 1) & ~1));
+    float2 *pg = work32 + (size_t)sid * n;
+    double2 *xg = sy.x;
+    const int cj = sy.conj;
+
+    // per row: the FP64 residual and the FP32 state (the FP64 solution
+    // lives in sy.x, the right-hand side is read again when needed)
+    int row[RPT];
+    bool ok[RPT];
+    double2 r64[RPT];
+    float2 dinv[RPT], d[RPT], r[RPT], z[RPT], p[RPT], q[RPT];
+    double bb = 0.0;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        row[k] = r0 + threadIdx.x + k * blockDim.x;
+        ok[k] = row[k] < r1;
+        r64[k] = cd(0.0, 0.0);
+        dinv[k] = make_float2(0.f, 0.f);
+        if (ok[k]) {
+            const int i = row[k];
+            const double2 bi = sy.bscale ? cmul(sy.beta, sy.bscale[batch.vcomp[i]]) : sy.beta;
+            double2 dg = cd(0.0, 0.0);
+            for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+                const double2 a = cadd(cscale(sy.alpha, M[e]), cscale(bi, S[e]));
+                As[e - ebase] = make_float2((float)a.x, (float)a.y);
+                Cs[e - ebase] = col[e];
+                if (col[e] == i) dg = a;
+            }
+            const double2 di = cdiv(cd(1.0, 0.0), dg);
+            dinv[k] = make_float2((float)di.x, (float)di.y);
+            r64[k] = sy.f[i];
+            bb += cabs2(r64[k]);
+            xg[i] = cd(0.0, 0.0);
+        }
+    }
+    {
+        double v[1] = {bb};
+        kmix_csum<double, 1>(cl, v, wredd, slotB, outd);  // its barrier also orders the shared-memory fill
+        bb = v[0];
+    }
+    double rr = bb;
+    int its = 0, status = 0;  // 0 converged, 1 not converged, 2 breakdown
+    if (bb > 0.0) {
+        status = 1;
+        for (int ref = 0; ref < KMIX_MAX_REFINE && its < maxit; ++ref) {
+            // FP32 solve of A d = r / |r|
+            const double sc = 1.0 / sqrt(rr);
+            float v3[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                r[k] = make_float2((float)(r64[k].x * sc), (float)(r64[k].y * sc));
+                z[k] = f2mul(dinv[k], r[k]);
+                p[k] = z[k];
+                d[k] = make_float2(0.f, 0.f);
+                if (ok[k]) {
+                    pg[row[k]] = p[k];
+                    const float2 t = f2dot(r[k], z[k], cj);
+                    v3[0] += t.x;
+                    v3[1] += t.y;
+                    v3[2] += r[k].x * r[k].x + r[k].y * r[k].y;
+                }
+            }
+            kmix_csum<float, 3>(cl, v3, wredf, slotI, outf);  // also publishes p
+            float2 rho = make_float2(v3[0], v3[1]);
+            const float rr0 = v3[2];
+            bool brk = false;
+            while (its < maxit) {
+                float v2[2] = {0.f, 0.f};
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) {
+                    float2 acc = make_float2(0.f, 0.f);
+                    if (ok[k]) {
+                        const int eb = ptr[row[k]] - ebase, ee = ptr[row[k] + 1] - ebase;
+#pragma unroll 4
+                        for (int e = eb; e < ee; ++e) {
+                            const float2 a = As[e], pj = __ldcg(&pg[Cs[e]]);
+                            acc.x = fmaf(a.x, pj.x, fmaf(-a.y, pj.y, acc.x));
+                            acc.y = fmaf(a.x, pj.y, fmaf(a.y, pj.x, acc.y));
+                        }
+                        const float2 t = f2dot(p[k], acc, cj);
+                        v2[0] += t.x;
+                        v2[1] += t.y;
+                    }
+                    q[k] = acc;
+                }
+                kmix_csum<float, 2>(cl, v2, wredf, slotP, outf);
+                const float2 pq = make_float2(v2[0], v2[1]);
+                if (!(pq.x * pq.x + pq.y * pq.y > 0.f)) { brk = true; break; }
+                const float2 al = f2div(rho, pq);
+                float w3[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) {
+                    d[k] = make_float2(fmaf(al.x, p[k].x, fmaf(-al.y, p[k].y, d[k].x)),
+                                       fmaf(al.x, p[k].y, fmaf(al.y, p[k].x, d[k].y)));
+                    r[k] = make_float2(fmaf(-al.x, q[k].x, fmaf(al.y, q[k].y, r[k].x)),
+                                       fmaf(-al.x, q[k].y, fmaf(-al.y, q[k].x, r[k].y)));
+                    z[k] = f2mul(dinv[k], r[k]);
+                    if (ok[k]) {
+                        const float2 t = f2dot(r[k], z[k], cj);
+                        w3[0] += t.x;
+                        w3[1] += t.y;
+                        w3[2] += r[k].x * r[k].x + r[k].y * r[k].y;
+                    }
+                }
+                kmix_csum<float, 3>(cl, w3, wredf, slotR, outf);
+                ++its;
+                if (w3[2] <= KMIX_INNER_TOL * KMIX_INNER_TOL * rr0) break;
+                if (!(rho.x * rho.x + rho.y * rho.y > 0.f)) { brk = true; break; }
+                const float2 rz = make_float2(w3[0], w3[1]);
+                const float2 be = f2div(rz, rho);
+                rho = rz;
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) {
+                    p[k] = make_float2(fmaf(be.x, p[k].x, fmaf(-be.y, p[k].y, z[k].x)),
+                                       fmaf(be.x, p[k].y, fmaf(be.y, p[k].x, z[k].y)));
+                    if (ok[k]) pg[row[k]] = p[k];
+                }
+                cl.sync();  // p published
+            }
+            if (brk) { status = 2; break; }
+            // FP64 update and residual
+            const double back = sqrt(rr);
+#pragma unroll
+            for (int k = 0; k < RPT; ++k)
+                if (ok[k]) xg[row[k]] = cadd(xg[row[k]], cd((double)d[k].x * back, (double)d[k].y * back));
+            cl.sync();  // x published
+            double rn = 0.0;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                if (!ok[k]) continue;
+                const int i = row[k];
+                double2 mx = cd(0.0, 0.0), sx = cd(0.0, 0.0);
+                for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+                    const double2 xj = __ldcg(&xg[col[e]]);
+                    const double me = M[e], se = S[e];
+                    mx.x += me * xj.x;
+                    mx.y += me * xj.y;
+                    sx.x += se * xj.x;
+                    sx.y += se * xj.y;
+                }
+                const double2 bi = sy.bscale ? cmul(sy.beta, sy.bscale[batch.vcomp[i]]) : sy.beta;
+                r64[k] = csub(sy.f[i], cadd(cmul(sy.alpha, mx), cmul(bi, sx)));
+                rn += cabs2(r64[k]);
+            }
+            double v[1] = {rn};
+            kmix_csum<double, 1>(cl, v, wredd, slotD, outd);
+            const double rprev = rr;
+            rr = v[0];
+            if (rr <= tol * tol * bb) { status = 0; break; }
+            if (!(rr <= 0.25 * rprev)) break;  // refinement stagnates (or NaN): not converged
+        }
+    } else {
+        rr = 0.0;
+    }
+    cl.sync();  // keep shared memory alive until every CTA has read it
+    if (rank == 0 && threadIdx.x == 0) {
+        stat[sid] = status == 0 ? its : (status == 1 ? -its : -1000000 - its);
+        res_out[sid] = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    }
+}
+
 // y = M u on both block rows (turns a strong-form vector into the weak one)
 __global__ void mass_spmv_kernel(int n, const int *__restrict__ ptr, const int *__restrict__ col,
                                  const double *__restrict__ M, const double2 *__restrict__ u,
@@ -333,10 +608,105 @@ int cluster_size_for(int n) {
     return cs;
 }
 
+template <int RPT>
+int kmix_attrs() {
+    OSRC_CK(cudaFuncSetAttribute(kmix_kernel<RPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    OSRC_CK(cudaFuncSetAttribute(kmix_kernel<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)KMIX_SMEM_MAX));
+    return OSRC_OK;
+}
+
+// Decides once per problem whether the mixed-precision kernel serves its
+// systems: every CTA's rows within KMIX_THREADS x KMIX_ROWS_PER_THREAD, its
+// FP32 entries within KMIX_SMEM_MAX, and the device able to hold one cluster
+// of that shape.
+int kmix_decide(osrc_problem *pb, int cs) {
+    if (pb->kmix_state >= 0) return OSRC_OK;
+    pb->kmix_state = 0;
+    const int n = pb->nv;
+    if ((int)pb->ms_ptr_h.size() != n + 1) return OSRC_OK;
+    const int rows = (n + cs - 1) / cs;
+    const int rpt = (rows + KMIX_THREADS - 1) / KMIX_THREADS;
+    if (rpt < 1 || rpt > KMIX_ROWS_PER_THREAD) return OSRC_OK;
+    size_t smem = 0;
+    for (int k = 0; k < cs; ++k) {
+        const int r0 = std::min(n, k * rows), r1 = std::min(n, r0 + rows);
+        const size_t ne = (size_t)(pb->ms_ptr_h[r1] - pb->ms_ptr_h[r0]);
+        smem = std::max(smem, sizeof(float2) * ((ne + 1) & ~(size_t)1) + sizeof(int) * ne);
+    }
+    if (smem > KMIX_SMEM_MAX) return OSRC_OK;
+    const int threads = ((rows + rpt - 1) / rpt + 31) / 32 * 32;
+    static std::once_flag once;
+    static int attr_status = OSRC_OK;
+    std::call_once(once, [] {
+        attr_status = kmix_attrs<1>();
+        if (attr_status == OSRC_OK) attr_status = kmix_attrs<2>();
+    });
+    OSRC_TRY(attr_status);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    const cudaError_t e = rpt == 1 ? cudaOccupancyMaxActiveClusters(&nclusters, kmix_kernel<1>, &cfg)
+                                   : cudaOccupancyMaxActiveClusters(&nclusters, kmix_kernel<2>, &cfg);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return OSRC_OK;
+    }
+    if (nclusters < 1) return OSRC_OK;
+    pb->kmix_state = 1;
+    pb->kmix_rpt = rpt;
+    pb->kmix_threads = threads;
+    pb->kmix_smem = smem;
+    return OSRC_OK;
+}
+
+static bool ranges_overlap(const double2 *a, const double2 *b, int n) {
+    return a < b + n && b < a + n;
+}
+
 int launch_kry(osrc_problem *pb, const KryBatch &batch, cudaStream_t st) {
     OSRC_TRY(kry_opt_in());
     const int n = pb->nv;
     const int cs = cluster_size_for(n);
+    OSRC_TRY(kmix_decide(pb, cs));
+    bool mix = pb->kmix_state == 1;
+    for (int k = 0; k < batch.nsys && mix; ++k)  // in-place systems stay on the FP64 kernel
+        if (ranges_overlap(batch.s[k].f, batch.s[k].x, n)) mix = false;
+    if (mix) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(batch.nsys * cs, 1, 1);
+        cfg.blockDim = dim3(pb->kmix_threads, 1, 1);
+        cfg.dynamicSmemBytes = pb->kmix_smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        float2 *w32 = reinterpret_cast<float2 *>(pb->d_kry.p);
+        const int *ptr = pb->d_ms_ptr.p, *col = pb->d_ms_col.p;
+        if (pb->kmix_rpt == 1)
+            OSRC_CK(cudaLaunchKernelEx(&cfg, kmix_kernel<1>, batch, n, ptr, col, (const double *)pb->d_M.p,
+                                       (const double *)pb->d_S.p, w32, pb->p.inner_tol, pb->p.inner_maxit,
+                                       pb->d_kry_stat.p, pb->d_kry_res.p));
+        else
+            OSRC_CK(cudaLaunchKernelEx(&cfg, kmix_kernel<2>, batch, n, ptr, col, (const double *)pb->d_M.p,
+                                       (const double *)pb->d_S.p, w32, pb->p.inner_tol, pb->p.inner_maxit,
+                                       pb->d_kry_stat.p, pb->d_kry_res.p));
+        pb->launches++;
+        return OSRC_OK;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(batch.nsys * cs, 1, 1);
     cfg.blockDim = dim3(KRY_THREADS, 1, 1);

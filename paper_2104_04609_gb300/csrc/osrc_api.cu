@@ -508,6 +508,7 @@ static int problem_create(osrc_mesh *mesh, const osrc_params *prm, const double 
             for (int i = 0; i < nv; ++i) mcol.insert(mcol.end(), rowsets[i].begin(), rowsets[i].end());
         }
         pb->ms_nnz = mptr[nv];
+        pb->ms_ptr_h = mptr;
         cpos.clear();
         cidx.clear();
         for (int t = 0; t < nt; ++t)
@@ -903,6 +904,7 @@ int problem_clone(osrc_problem *m, osrc_problem **out) {
     c->near_pairs = m->near_pairs;
     c->near_nnz = m->near_nnz;
     c->ms_nnz = m->ms_nnz;
+    c->ms_ptr_h = m->ms_ptr_h;
     c->k_osrc = m->k_osrc;
     c->k_osrc_i = m->k_osrc_i;
     c->k_eps = m->k_eps;

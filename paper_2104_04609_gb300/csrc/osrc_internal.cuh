@@ -176,6 +176,7 @@ struct osrc_problem {
     // ---- sparse mass / stiffness (1-ring CSR), FP64 ----------------------
     int ms_nnz = 0;
     DBuf<int> d_ms_ptr, d_ms_col;
+    std::vector<int> ms_ptr_h;  // host copy of the CSR row pointers (shared-memory sizing)
     DBuf<double> d_M, d_S;
     // ---- dense FP64 system (OSRC_FP64_DENSE) -------------------------------
     DBuf<double2> d_dense;    // [2nv][2nv] row-major
@@ -191,6 +192,11 @@ struct osrc_problem {
     DBuf<int> d_kry_stat;     // per-system iteration count / status
     DBuf<double> d_kry_res;   // per-system final relative residual
     int inner_last_max = 0;
+    // mixed-precision inner solver (k_sparse.cu): -1 not yet decided, 0 not
+    // usable for this problem, 1 usable with kmix_rpt rows per thread,
+    // kmix_threads threads and kmix_smem bytes of dynamic shared memory
+    int kmix_state = -1, kmix_rpt = 0, kmix_threads = 0;
+    size_t kmix_smem = 0;
     // ---- GMRES workspace --------------------------------------------------------
     DBuf<double2> d_basis;    // (maxit+1) x 2nv
     int basis_cap = 0;
