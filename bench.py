@@ -74,10 +74,11 @@ def parse():
                     help="skip the far-field apply on the 80000-vertex bumpy ellipsoid")
     ap.add_argument("--no-objects", action="store_true",
                     help="skip the four-sphere multiple-scattering solve")
-    ap.add_argument("--profile-case", choices=["far-small", "dense-short", "dense-small"],
+    ap.add_argument("--profile-case", choices=["far-small", "precond-small", "dense-short", "dense-small"],
                     help="instead of the benchmark: run one small case for profiler captures "
                          "(far-small: far-field applies on a 2562-vertex sphere, plain then "
-                         "large-ka; dense-short: ellipsoid8000, 128 right-hand sides, one "
+                         "large-ka; precond-small: five OSRC preconditioner applies on it; "
+                         "dense-short: ellipsoid8000, 128 right-hand sides, one "
                          "refinement of 120 inner iterations; dense-small: the same on a "
                          "3000-vertex ellipsoid, 24 inner iterations)")
     ap.add_argument("--sponge-sweep", action="store_true",
@@ -1016,6 +1017,16 @@ def profile_case(name, device=0):
                 S.apply(x)
             torch.cuda.synchronize()
             S.close()
+        return
+    if name == "precond-small":
+        # OSRC preconditioner (mass solve + 2 N_Pade + 1 shifted systems) on icosphere(4), five applies
+        v, t = icosphere(4)
+        S = B.Solver(v, t, 20.0, 26.0, 1.5, device=device)
+        x = S.rhs_planewave([[0.0, 0.0, 1.0]])
+        for _ in range(5):
+            S.precond(x)
+        torch.cuda.synchronize()
+        S.close()
         return
     if name == "dense-short":
         W = workload(DENSE_WORKLOAD)
