@@ -74,6 +74,9 @@ def parse():
                     help="skip the far-field apply on the 80000-vertex bumpy ellipsoid")
     ap.add_argument("--no-objects", action="store_true",
                     help="skip the four-sphere multiple-scattering solve")
+    ap.add_argument("--fp32-mix-probe", action="store_true",
+                    help="instead of the benchmark: FP32-pipe throughput of packed FMA alone and of "
+                         "the far kernel's FMA / rsqrt / sincos mix (compiles a small probe)")
     ap.add_argument("--profile-case", choices=["far-small", "precond-small", "dense-short", "dense-small"],
                     help="instead of the benchmark: run one small case for profiler captures "
                          "(far-small: far-field applies on a 2562-vertex sphere, plain then "
@@ -1085,8 +1088,33 @@ def sponge_sweep(device=0, maxit=400):
                 S.close()
 
 
+def fp32_mix_probe():
+    """Compiles and runs paper_2104_04609_gb300/probes/fp32_mix.cu: FP32-pipe
+    throughput for packed FMA alone, scalar FMA alone, and the far kernel's
+    mix (54 packed FMA + 2 rsqrt + 4 sincos per iteration), with the SM clock
+    sampled while it runs."""
+    here = os.path.join(ROOT, "paper_2104_04609_gb300")
+    exe = os.path.join(here, "_build", "probe_fp32_mix")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
+                    os.path.join(here, "probes", "fp32_mix.cu"), "-o", exe], check=True)
+    clk = ClockSampler([0])
+    clk.start()
+    r = subprocess.run([exe, "2070"], capture_output=True, text=True, check=True)
+    c = clk.stop()
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    mhz = c.get("sm_mhz") or 2070.0
+    out["clock_mhz_assumed"] = mhz
+    out["mix_cycles_per_warp_iteration"] *= mhz / 2070.0
+    out["clocks"] = c
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.fp32_mix_probe:
+        fp32_mix_probe()
+        return
     if args.sponge_sweep:
         sponge_sweep()
         return
