@@ -387,7 +387,7 @@ def run_dense(nrhs, n_matfree, device):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     S = B.Solver(W["verts"], W["tris"], W["k_ext"], W["k_int"], W["rho_ratio"], device=device,
-                 precision=B.OSRC_FP64_DENSE)
+                 precision=B.OSRC_FP64_DENSE, dense_assembly=B.OSRC_ASSEMBLE_FF)
     torch.cuda.synchronize()
     t_assembly = time.perf_counter() - t0
     out = {}
@@ -446,7 +446,8 @@ def run_dense(nrhs, n_matfree, device):
             "workload": f"{DENSE_WORKLOAD}: ellipsoid (1, 0.7, 0.5), {S.nv} vertices, k_ext "
                         f"{W['k_ext']:g}, k_int {W['k_int']:g}, rho ratio {W['rho_ratio']:g}, "
                         f"{nrhs} plane waves (seed 1)",
-            "path": "FP64 dense assembly; explicit BF16 P M^-1 matrix; inner GMRES (FP32, CGS) on "
+            "path": "dense assembly in float-float (FP64 storage); explicit BF16 P M^-1 matrix; "
+                    "inner GMRES (FP32, CGS) on "
                     "BF16 tcgen05 far field + exact near field; float-float outer residual",
             "tol": DENSE_TOL, "right_hand_sides": nrhs,
             "solves_per_s": nrhs / t_solve,
@@ -738,6 +739,7 @@ def run_serving(n_req, device, batched=False):
             p = B.osrc_params_default(k_ext=w["k_ext"], k_int=w["k_int"], rho_ratio=w["rho"])
             if batched and len(w["dirs"]) >= 2:
                 p.precision = B.OSRC_FP64_DENSE
+                p.dense_assembly = B.OSRC_ASSEMBLE_FF
             ids.append(B.osrc_server_submit(sv, w["verts"], w["tris"], p, w["dirs"], tol=TOL,
                                             maxit=1000))
         lat, its, ok = [], 0, 0

@@ -28,6 +28,8 @@ OSRC_UNSUPPORTED = 7
 
 OSRC_FP32_MATFREE = 0
 OSRC_FP64_DENSE = 1
+OSRC_ASSEMBLE_FP64 = 0
+OSRC_ASSEMBLE_FF = 1
 OSRC_WEAK = 0
 OSRC_STRONG = 1
 OSRC_PART_FAR = 1
@@ -59,6 +61,7 @@ class osrc_params(ctypes.Structure):
         ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double),
         ("inner_maxit", ctypes.c_int), ("precond", ctypes.c_int),
         ("formulation", ctypes.c_int), ("k_int_im", ctypes.c_double),
+        ("dense_assembly", ctypes.c_int),
     ]
 
 

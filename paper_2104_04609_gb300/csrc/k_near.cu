@@ -13,6 +13,7 @@
 // whose Jacobians (xi^3 eta2, xi^3 eta1^2 [eta2], xi^3 eta1^2 eta2) cancel the
 // 1/r and 1/r^2 singularities, leaving integrands that tensor Gauss-Legendre
 // rules integrate with exponential convergence.
+#include "ffmath.cuh"
 #include "osrc_internal.cuh"
 
 namespace {
@@ -394,6 +395,167 @@ dense_far_kernel(int nv, int nt, const double *__restrict__ verts, const int *__
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same dense far-pair assembly in float-float arithmetic (ffmath.cuh,
+// about 48 significant bits) on the FP32 pipes, which on this part issue
+// 64 times the FP64 rate.  Same pairs, threads, contraction and FP64
+// atomics as dense_far_kernel; the geometry comes from a per-triangle
+// float-float table (area, normal, surface curls, the six rule points) and
+// the phases k r from float-float sine / cosine.  Lossless materials only.
+// ---------------------------------------------------------------------------
+constexpr int DFF_GEOM = 31;  // float-float values per triangle in the table
+
+struct FFMat {
+    ff k1, rho, irho, dk1;  // interior wavenumber, rho, 1/rho, k1^2 / rho
+};
+
+struct DenseFFConst {
+    ff k0, dk0, inv4pi;
+    FFMat m;             // the material (one object)
+    const FFMat *obj;    // disjoint objects: material per object (else m)
+    const int *tcomp;    // object of each triangle
+    float sgn;           // sign of the interior terms: +1 PMCHWT, -1 Mueller
+};
+
+// Per triangle: [0] area, [1..3] unit normal, [4..12] the surface curls of
+// the three hat functions, [13..30] the six rule points (x, y, z each).
+__global__ void dense_geom_ff_kernel(int nt, const double *__restrict__ verts, const int *__restrict__ tris,
+                                     const double *__restrict__ tgeo, ff *__restrict__ G) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    ff *o = G + DFF_GEOM * (size_t)t;
+    for (int i = 0; i < 13; ++i) o[i] = ff_make(tgeo[16 * (size_t)t + i]);
+    for (int p = 0; p < 6; ++p)
+        for (int k = 0; k < 3; ++k) {
+            const double x = dense_bary(p, 0) * verts[3 * tris[3 * t] + k] +
+                             dense_bary(p, 1) * verts[3 * tris[3 * t + 1] + k] +
+                             dense_bary(p, 2) * verts[3 * tris[3 * t + 2] + k];
+            o[13 + 3 * p + k] = ff_make(x);
+        }
+}
+
+__device__ __forceinline__ cff cff_add(cff a, cff b) { return cff{ff_add(a.re, b.re), ff_add(a.im, b.im)}; }
+__device__ __forceinline__ cff cff_scale(cff a, ff s) { return cff{ff_mul(a.re, s), ff_mul(a.im, s)}; }
+__device__ __forceinline__ cff cff_axpy(ff s, cff a, cff y) {  // y + s a
+    return cff{ff_fma(s, a.re, y.re), ff_fma(s, a.im, y.im)};
+}
+
+__global__ void __launch_bounds__(DA_PAIRS * 6)
+dense_far_ff_kernel(int nv, int nt, const int *__restrict__ tris, const ff *__restrict__ G, DenseFFConst c,
+                    double2 *__restrict__ A) {
+    __shared__ cff zs[DA_PAIRS][6][13];  // per pair, per test point: V[3], K[3], T[3], D[3], dc
+    const int lp = threadIdx.x / 6, p = threadIdx.x % 6;
+    const int f = blockIdx.y;
+    const long long j = (long long)blockIdx.x * DA_PAIRS + lp;
+    int t = -1, s = -1;
+    if (j < nt - 1 - f) {
+        t = f;
+        s = f + 1 + (int)j;
+    } else if (nt - 1 - f != f && j < nt - 1) {
+        t = nt - 1 - f;
+        s = t + 1 + (int)(j - (nt - 1 - f));
+    }
+    bool live = t >= 0 && s < nt;
+    int vt[3] = {0, 0, 0}, vs[3] = {0, 0, 0};
+    if (live) {
+        for (int a = 0; a < 3; ++a) {
+            vt[a] = tris[3 * t + a];
+            vs[a] = tris[3 * s + a];
+        }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                if (vt[a] == vs[b]) live = false;  // touching: near field
+    }
+    const ff *gt = G + DFF_GEOM * (size_t)(live ? t : 0), *gs = G + DFF_GEOM * (size_t)(live ? s : 0);
+    // rule constants: weights and the two barycentric values of each orbit
+    const ff w1 = ff_make(kDw1), w2 = ff_make(kDw2);
+    const ff a1 = ff_make(kDa1), a2 = ff_make(kDa2);
+    const ff b1 = ff_make(1.0 - 2.0 * kDa1), b2 = ff_make(1.0 - 2.0 * kDa2);
+    FFMat m = c.m;
+    float on1 = c.sgn;
+    if (c.obj && live) {
+        const int ct = c.tcomp[t], cs = c.tcomp[s];
+        m = c.obj[ct];
+        if (ct != cs) on1 = 0.f;
+    }
+    cff Z[13];
+    for (int i = 0; i < 13; ++i) Z[i] = cff{ff{0.f, 0.f}, ff{0.f, 0.f}};
+    if (live) {
+        const ff X[3] = {gt[13 + 3 * p], gt[14 + 3 * p], gt[15 + 3 * p]};
+        const ff scale = ff_mul(ff_mul(gt[0], gs[0]), p < 3 ? w1 : w2);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const ff d[3] = {ff_sub(X[0], gs[13 + 3 * q]), ff_sub(X[1], gs[14 + 3 * q]),
+                             ff_sub(X[2], gs[15 + 3 * q])};
+            const ff r = ff_sqrt(ff_dot3(d, d));
+            const ff ri = ff_rcp(r);
+            const ff kr0 = ff_mul(c.k0, r), kr1 = ff_mul(m.k1, r);
+            ff s0, c0, s1, c1;
+            ff_sincos(kr0, s0, c0);
+            ff_sincos(kr1, s1, c1);
+            s1 = ff{s1.hi * on1, s1.lo * on1};
+            c1 = ff{c1.hi * on1, c1.lo * on1};
+            const ff fw = ff_mul(ff_mul(c.inv4pi, ri), ff_mul(q < 3 ? w1 : w2, scale));
+            const ff f3 = ff_mul(ff_mul(fw, ri), ri);
+            const cff g0{ff_mul(c0, fw), ff_mul(s0, fw)}, g1{ff_mul(c1, fw), ff_mul(s1, fw)};
+            // H = e^{ikr}(ikr - 1)/r^3 summed over both wavenumbers, negated
+            const ff hre = ff_neg(ff_add(ff_add(c0, ff_mul(kr0, s0)), ff_add(c1, ff_mul(kr1, s1))));
+            const ff him = ff_sub(ff_add(ff_mul(kr0, c0), ff_mul(kr1, c1)), ff_add(s0, s1));
+            const cff hs{ff_mul(hre, f3), ff_mul(him, f3)};
+            const cff gp = cff_axpy(m.rho, g1, g0);
+            const cff gk = cff_axpy(m.dk1, g1, cff_scale(g0, c.dk0));
+            const cff hk = cff_scale(hs, ff_dot3(d, gs + 1));  // -hs (y - x).n_y
+            const cff ht = cff_scale(hs, ff_dot3(d, gt + 1));  //  hs (x - y).n_x
+            Z[12] = cff_add(Z[12], cff_axpy(m.irho, g1, g0));
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const ff bq = (b == q % 3) ? (q < 3 ? b1 : b2) : (q < 3 ? a1 : a2);
+                Z[b] = cff_axpy(bq, gp, Z[b]);
+                Z[3 + b] = cff_axpy(bq, hk, Z[3 + b]);
+                Z[6 + b] = cff_axpy(bq, ht, Z[6 + b]);
+                Z[9 + b] = cff_axpy(bq, gk, Z[9 + b]);
+            }
+        }
+    }
+    for (int i = 0; i < 13; ++i) zs[lp][p][i] = Z[i];
+    __syncthreads();
+    if (!live) return;
+    const ff nn = ff_dot3(gt + 1, gs + 1);
+    cff dc = zs[lp][0][12];
+    for (int pp = 1; pp < 6; ++pp) dc = cff_add(dc, zs[lp][pp][12]);
+    const size_t n2 = 2 * (size_t)nv;
+    for (int e = p; e < 9; e += 6) {
+        const int a = e / 3, b = e % 3;
+        const cff z0{ff{0.f, 0.f}, ff{0.f, 0.f}};
+        cff v = z0, k = z0, tt = z0, d = z0;
+        for (int pp = 0; pp < 6; ++pp) {
+            const ff ba = (a == pp % 3) ? (pp < 3 ? b1 : b2) : (pp < 3 ? a1 : a2);
+            v = cff_axpy(ba, zs[lp][pp][b], v);
+            k = cff_axpy(ba, zs[lp][pp][3 + b], k);
+            tt = cff_axpy(ba, zs[lp][pp][6 + b], tt);
+            d = cff_axpy(ba, zs[lp][pp][9 + b], d);
+        }
+        const ff cc = ff_dot3(gt + 4 + 3 * a, gs + 4 + 3 * b);
+        const cff dd{ff_sub(ff_mul(dc.re, cc), ff_mul(d.re, nn)), ff_sub(ff_mul(dc.im, cc), ff_mul(d.im, nn))};
+        const double vx = ff_to_double(v.re), vy = ff_to_double(v.im);
+        const double kx = ff_to_double(k.re), ky = ff_to_double(k.im);
+        const double tx = ff_to_double(tt.re), ty = ff_to_double(tt.im);
+        const double dx = ff_to_double(dd.re), dy = ff_to_double(dd.im);
+        const size_t ra = vt[a], rb = vs[b];
+        double *o;
+        // forward (test t, source s)
+        o = (double *)&A[ra * n2 + rb];                     atomicAdd(o, vx);  atomicAdd(o + 1, vy);
+        o = (double *)&A[ra * n2 + nv + rb];                atomicAdd(o, kx);  atomicAdd(o + 1, ky);
+        o = (double *)&A[(nv + ra) * n2 + rb];              atomicAdd(o, tx);  atomicAdd(o + 1, ty);
+        o = (double *)&A[(nv + ra) * n2 + nv + rb];         atomicAdd(o, dx);  atomicAdd(o + 1, dy);
+        // reversed (test s, source t)
+        o = (double *)&A[rb * n2 + ra];                     atomicAdd(o, vx);  atomicAdd(o + 1, vy);
+        o = (double *)&A[rb * n2 + nv + ra];                atomicAdd(o, -tx); atomicAdd(o + 1, -ty);
+        o = (double *)&A[(nv + rb) * n2 + ra];              atomicAdd(o, -kx); atomicAdd(o + 1, -ky);
+        o = (double *)&A[(nv + rb) * n2 + nv + ra];         atomicAdd(o, dx);  atomicAdd(o + 1, dy);
+    }
+}
+
 // Adds the near CSR blocks into the dense matrix (one thread per vertex row).
 __global__ void dense_add_near_kernel(int nv, const int *__restrict__ ptr, const int *__restrict__ col,
                                       const double2 *__restrict__ val, double2 *__restrict__ A) {
@@ -530,14 +692,43 @@ int dense_assemble(osrc_problem *pb, cudaStream_t st) {
         return OSRC_UNSUPPORTED;
     }
     dim3 grid((unsigned)((nt - 1 + DA_PAIRS - 1) / DA_PAIRS), (unsigned)folded);
-    if (nt > 1)
+    // float-float assembly on request, for lossless materials
+    const bool use_ff = pb->p.dense_assembly == OSRC_ASSEMBLE_FF && !pb->absorb;
+    DBuf<ff> geo;
+    DBuf<FFMat> fobj;
+    if (nt > 1 && use_ff) {
+        OSRC_TRY(geo.alloc(m->ctx, DFF_GEOM * (size_t)nt));
+        dense_geom_ff_kernel<<<(nt + 127) / 128, 128, 0, st>>>(nt, m->d_verts.p, m->d_tris.p, pb->d_tgeo.p,
+                                                               geo.p);
+        pb->launches++;
+        auto mat = [](double k1, double rho) {
+            return FFMat{ff_make(k1), ff_make(rho), ff_make(1.0 / rho), ff_make(k1 * k1 / rho)};
+        };
+        DenseFFConst fc{};
+        fc.k0 = ff_make(pb->p.k_ext);
+        fc.dk0 = ff_make(pb->p.k_ext * pb->p.k_ext);
+        fc.inv4pi = ff_make(kInv4Pi);
+        fc.m = mat(pb->p.k_int, pb->p.rho_ratio);
+        fc.sgn = pb->p.formulation == OSRC_MULLER ? -1.f : 1.f;
+        fc.tcomp = pb->mesh->d_tcomp.p;
+        if (pb->multi) {
+            std::vector<FFMat> h(pb->obj.size());
+            for (size_t i = 0; i < h.size(); ++i) h[i] = mat(pb->obj[i].k1, pb->obj[i].rho);
+            OSRC_TRY(fobj.alloc(m->ctx, h.size()));
+            OSRC_CK(cudaMemcpyAsync(fobj.p, h.data(), h.size() * sizeof(FFMat), cudaMemcpyHostToDevice, st));
+            fc.obj = fobj.p;
+        }
+        dense_far_ff_kernel<<<grid, DA_PAIRS * 6, 0, st>>>(nv, nt, m->d_tris.p, geo.p, fc, pb->d_dense.p);
+    } else if (nt > 1) {
         dense_far_kernel<<<grid, DA_PAIRS * 6, 0, st>>>(nv, nt, m->d_verts.p, m->d_tris.p, pb->d_tgeo.p, c,
                                                          pb->d_dense.p);
+    }
     pb->launches++;
     dense_add_near_kernel<<<(nv + 127) / 128, 128, 0, st>>>(nv, pb->d_nr_ptr.p, pb->d_nr_col.p,
                                                             pb->d_nr_val.p, pb->d_dense.p);
     pb->launches++;
     OSRC_CK(cudaGetLastError());
+    if (use_ff) OSRC_CK(cudaStreamSynchronize(st));  // the float-float tables are released on return
     return OSRC_OK;
 }
 

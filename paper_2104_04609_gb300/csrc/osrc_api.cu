@@ -78,6 +78,7 @@ extern "C" void osrc_params_default(osrc_params *p) {
     p->precond = OSRC_PRECOND_OSRC;
     p->formulation = OSRC_PMCHWT;
     p->k_int_im = 0.0;
+    p->dense_assembly = OSRC_ASSEMBLE_FP64;
 }
 
 // ---------------------------------------------------------------------------
@@ -375,6 +376,7 @@ static int problem_create(osrc_mesh *mesh, const osrc_params *prm, const double 
         p.precond < OSRC_PRECOND_OSRC || p.precond > OSRC_PRECOND_CALDERON ||
         (p.formulation != OSRC_PMCHWT && p.formulation != OSRC_MULLER) ||
         !(p.k_int_im >= 0.0) || !std::isfinite(p.k_int_im) ||
+        (p.dense_assembly != OSRC_ASSEMBLE_FP64 && p.dense_assembly != OSRC_ASSEMBLE_FF) ||
         (p.osrc_side != 0 && p.osrc_side != 1) || !std::isfinite(p.theta)) {
         osrc_set_error("invalid problem parameters");
         return OSRC_INVALID_ARG;

@@ -108,7 +108,8 @@ std::string request_key(const Request &r) {
     h = fnv1a(r.tris.data(), r.tris.size() * sizeof(int), h);
     const osrc_params &p = r.params;
     const double d[] = {p.k_ext, p.k_int, p.rho_ratio, p.theta, p.damping_R, p.inner_tol, p.k_int_im};
-    const int i[] = {p.n_pade, p.osrc_side, p.n_ss, p.precision, p.inner_maxit, p.precond, p.formulation, r.nv, r.nt};
+    const int i[] = {p.n_pade, p.osrc_side, p.n_ss, p.precision, p.inner_maxit, p.precond, p.formulation,
+                     p.dense_assembly, r.nv, r.nt};
     h = fnv1a(d, sizeof(d), h);
     h = fnv1a(i, sizeof(i), h);
     char buf[32];
