@@ -1040,7 +1040,8 @@ def profile_case(name, device=0):
     else:
         v, t = ellipsoid(3000)
         k0, k1, rho, dirs, maxit = 15.0, 36.0, 1.9, plane_wave_dirs(128, seed=1), 24
-    S = B.Solver(v, t, k0, k1, rho, device=device, precision=B.OSRC_FP64_DENSE)
+    S = B.Solver(v, t, k0, k1, rho, device=device, precision=B.OSRC_FP64_DENSE,
+                 dense_assembly=B.OSRC_ASSEMBLE_FF)
     try:
         b = S.rhs_planewave(dirs)
         x = torch.zeros_like(b)

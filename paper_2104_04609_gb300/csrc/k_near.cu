@@ -434,16 +434,11 @@ __global__ void dense_geom_ff_kernel(int nt, const double *__restrict__ verts, c
         }
 }
 
-__device__ __forceinline__ cff cff_add(cff a, cff b) { return cff{ff_add(a.re, b.re), ff_add(a.im, b.im)}; }
-__device__ __forceinline__ cff cff_scale(cff a, ff s) { return cff{ff_mul(a.re, s), ff_mul(a.im, s)}; }
-__device__ __forceinline__ cff cff_axpy(ff s, cff a, cff y) {  // y + s a
-    return cff{ff_fma(s, a.re, y.re), ff_fma(s, a.im, y.im)};
-}
-
 __global__ void __launch_bounds__(DA_PAIRS * 6)
 dense_far_ff_kernel(int nv, int nt, const int *__restrict__ tris, const ff *__restrict__ G, DenseFFConst c,
                     double2 *__restrict__ A) {
-    __shared__ cff zs[DA_PAIRS][6][13];  // per pair, per test point: V[3], K[3], T[3], D[3], dc
+    // complex values as ff2 with (re, im) in the two lanes
+    __shared__ ff2 zs[DA_PAIRS][6][13];  // per pair, per test point: V[3], K[3], T[3], D[3], dc
     const int lp = threadIdx.x / 6, p = threadIdx.x % 6;
     const int f = blockIdx.y;
     const long long j = (long long)blockIdx.x * DA_PAIRS + lp;
@@ -467,10 +462,11 @@ dense_far_ff_kernel(int nv, int nt, const int *__restrict__ tris, const ff *__re
                 if (vt[a] == vs[b]) live = false;  // touching: near field
     }
     const ff *gt = G + DFF_GEOM * (size_t)(live ? t : 0), *gs = G + DFF_GEOM * (size_t)(live ? s : 0);
-    // rule constants: weights and the two barycentric values of each orbit
-    const ff w1 = ff_make(kDw1), w2 = ff_make(kDw2);
-    const ff a1 = ff_make(kDa1), a2 = ff_make(kDa2);
-    const ff b1 = ff_make(1.0 - 2.0 * kDa1), b2 = ff_make(1.0 - 2.0 * kDa2);
+    // rule constants (kDw*, kDa*, 1 - 2 kDa* split into float pairs): weights
+    // and the two barycentric values of each orbit
+    const ff w1{0.22338159382343292f, -4.1454217836189855e-09f}, w2{0.10995174199342728f, 1.6618947329405387e-09f};
+    const ff a1{0.4459484815597534f, 9.356211805311432e-09f}, a2{0.09157621115446091f, 2.355310169122049e-09f};
+    const ff b1{0.10810301452875137f, 3.6393186242378306e-09f}, b2{0.816847562789917f, 1.0190540855603558e-08f};
     FFMat m = c.m;
     float on1 = c.sgn;
     if (c.obj && live) {
@@ -478,42 +474,48 @@ dense_far_ff_kernel(int nv, int nt, const int *__restrict__ tris, const ff *__re
         m = c.obj[ct];
         if (ct != cs) on1 = 0.f;
     }
-    cff Z[13];
-    for (int i = 0; i < 13; ++i) Z[i] = cff{ff{0.f, 0.f}, ff{0.f, 0.f}};
+    const ff2 zero{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    ff2 Z[13];
+    for (int i = 0; i < 13; ++i) Z[i] = zero;
     if (live) {
         const ff X[3] = {gt[13 + 3 * p], gt[14 + 3 * p], gt[15 + 3 * p]};
         const ff scale = ff_mul(ff_mul(gt[0], gs[0]), p < 3 ? w1 : w2);
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
+        const ff2 k01 = ff2_make(c.k0, m.k1);
+#pragma unroll 1
+        for (int q = 0; q < 6; ++q) {  // not unrolled: the body is long enough
             const ff d[3] = {ff_sub(X[0], gs[13 + 3 * q]), ff_sub(X[1], gs[14 + 3 * q]),
                              ff_sub(X[2], gs[15 + 3 * q])};
             const ff r = ff_sqrt(ff_dot3(d, d));
             const ff ri = ff_rcp(r);
-            const ff kr0 = ff_mul(c.k0, r), kr1 = ff_mul(m.k1, r);
-            ff s0, c0, s1, c1;
-            ff_sincos(kr0, s0, c0);
-            ff_sincos(kr1, s1, c1);
-            s1 = ff{s1.hi * on1, s1.lo * on1};
-            c1 = ff{c1.hi * on1, c1.lo * on1};
+            const ff2 kr = ff2_mul(k01, ff2_dup(r));  // (k0 r, k1 r)
+            ff2 sn, cs;                               // (sin k0 r, sin k1 r), (cos ..)
+            ff2_sincos(kr, sn, cs);
+            sn.hi.y *= on1;
+            sn.lo.y *= on1;
+            cs.hi.y *= on1;
+            cs.lo.y *= on1;
             const ff fw = ff_mul(ff_mul(c.inv4pi, ri), ff_mul(q < 3 ? w1 : w2, scale));
             const ff f3 = ff_mul(ff_mul(fw, ri), ri);
-            const cff g0{ff_mul(c0, fw), ff_mul(s0, fw)}, g1{ff_mul(c1, fw), ff_mul(s1, fw)};
-            // H = e^{ikr}(ikr - 1)/r^3 summed over both wavenumbers, negated
-            const ff hre = ff_neg(ff_add(ff_add(c0, ff_mul(kr0, s0)), ff_add(c1, ff_mul(kr1, s1))));
-            const ff him = ff_sub(ff_add(ff_mul(kr0, c0), ff_mul(kr1, c1)), ff_add(s0, s1));
-            const cff hs{ff_mul(hre, f3), ff_mul(him, f3)};
-            const cff gp = cff_axpy(m.rho, g1, g0);
-            const cff gk = cff_axpy(m.dk1, g1, cff_scale(g0, c.dk0));
-            const cff hk = cff_scale(hs, ff_dot3(d, gs + 1));  // -hs (y - x).n_y
-            const cff ht = cff_scale(hs, ff_dot3(d, gt + 1));  //  hs (x - y).n_x
-            Z[12] = cff_add(Z[12], cff_axpy(m.irho, g1, g0));
+            const ff2 fw2 = ff2_dup(fw);
+            const ff2 cw = ff2_mul(cs, fw2), sw = ff2_mul(sn, fw2);
+            const ff2 g0 = ff2_make(ff2_x(cw), ff2_x(sw)), g1 = ff2_make(ff2_y(cw), ff2_y(sw));
+            // H = e^{ikr}(ikr - 1)/r^3 summed over both wavenumbers, negated:
+            // re = -(sum c + kr s) f3, im = (sum kr c - s) f3
+            const ff2 ha = ff2_fma(kr, sn, cs), hb = ff2_sub(ff2_mul(kr, cs), sn);
+            const ff2 hs = ff2_mul(ff2_make(ff_neg(ff_add(ff2_x(ha), ff2_y(ha))), ff_add(ff2_x(hb), ff2_y(hb))),
+                                   ff2_dup(f3));
+            const ff2 gp = ff2_fma(ff2_dup(m.rho), g1, g0);
+            const ff2 gk = ff2_fma(ff2_dup(m.dk1), g1, ff2_mul(ff2_dup(c.dk0), g0));
+            const ff2 hk = ff2_mul(hs, ff2_dup(ff_dot3(d, gs + 1)));  // -hs (y - x).n_y
+            const ff2 ht = ff2_mul(hs, ff2_dup(ff_dot3(d, gt + 1)));  //  hs (x - y).n_x
+            Z[12] = ff2_add(Z[12], ff2_fma(ff2_dup(m.irho), g1, g0));
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
-                const ff bq = (b == q % 3) ? (q < 3 ? b1 : b2) : (q < 3 ? a1 : a2);
-                Z[b] = cff_axpy(bq, gp, Z[b]);
-                Z[3 + b] = cff_axpy(bq, hk, Z[3 + b]);
-                Z[6 + b] = cff_axpy(bq, ht, Z[6 + b]);
-                Z[9 + b] = cff_axpy(bq, gk, Z[9 + b]);
+                const ff2 bq = ff2_dup((b == q % 3) ? (q < 3 ? b1 : b2) : (q < 3 ? a1 : a2));
+                Z[b] = ff2_fma(bq, gp, Z[b]);
+                Z[3 + b] = ff2_fma(bq, hk, Z[3 + b]);
+                Z[6 + b] = ff2_fma(bq, ht, Z[6 + b]);
+                Z[9 + b] = ff2_fma(bq, gk, Z[9 + b]);
             }
         }
     }
@@ -521,26 +523,25 @@ dense_far_ff_kernel(int nv, int nt, const int *__restrict__ tris, const ff *__re
     __syncthreads();
     if (!live) return;
     const ff nn = ff_dot3(gt + 1, gs + 1);
-    cff dc = zs[lp][0][12];
-    for (int pp = 1; pp < 6; ++pp) dc = cff_add(dc, zs[lp][pp][12]);
+    ff2 dc = zs[lp][0][12];
+    for (int pp = 1; pp < 6; ++pp) dc = ff2_add(dc, zs[lp][pp][12]);
     const size_t n2 = 2 * (size_t)nv;
     for (int e = p; e < 9; e += 6) {
         const int a = e / 3, b = e % 3;
-        const cff z0{ff{0.f, 0.f}, ff{0.f, 0.f}};
-        cff v = z0, k = z0, tt = z0, d = z0;
+        ff2 v = zero, k = zero, tt = zero, d = zero;
         for (int pp = 0; pp < 6; ++pp) {
-            const ff ba = (a == pp % 3) ? (pp < 3 ? b1 : b2) : (pp < 3 ? a1 : a2);
-            v = cff_axpy(ba, zs[lp][pp][b], v);
-            k = cff_axpy(ba, zs[lp][pp][3 + b], k);
-            tt = cff_axpy(ba, zs[lp][pp][6 + b], tt);
-            d = cff_axpy(ba, zs[lp][pp][9 + b], d);
+            const ff2 ba = ff2_dup((a == pp % 3) ? (pp < 3 ? b1 : b2) : (pp < 3 ? a1 : a2));
+            v = ff2_fma(ba, zs[lp][pp][b], v);
+            k = ff2_fma(ba, zs[lp][pp][3 + b], k);
+            tt = ff2_fma(ba, zs[lp][pp][6 + b], tt);
+            d = ff2_fma(ba, zs[lp][pp][9 + b], d);
         }
         const ff cc = ff_dot3(gt + 4 + 3 * a, gs + 4 + 3 * b);
-        const cff dd{ff_sub(ff_mul(dc.re, cc), ff_mul(d.re, nn)), ff_sub(ff_mul(dc.im, cc), ff_mul(d.im, nn))};
-        const double vx = ff_to_double(v.re), vy = ff_to_double(v.im);
-        const double kx = ff_to_double(k.re), ky = ff_to_double(k.im);
-        const double tx = ff_to_double(tt.re), ty = ff_to_double(tt.im);
-        const double dx = ff_to_double(dd.re), dy = ff_to_double(dd.im);
+        const ff2 dd = ff2_sub(ff2_mul(dc, ff2_dup(cc)), ff2_mul(d, ff2_dup(nn)));
+        const double vx = ff_to_double(ff2_x(v)), vy = ff_to_double(ff2_y(v));
+        const double kx = ff_to_double(ff2_x(k)), ky = ff_to_double(ff2_y(k));
+        const double tx = ff_to_double(ff2_x(tt)), ty = ff_to_double(ff2_y(tt));
+        const double dx = ff_to_double(ff2_x(dd)), dy = ff_to_double(ff2_y(dd));
         const size_t ra = vt[a], rb = vs[b];
         double *o;
         // forward (test t, source s)
