@@ -78,7 +78,10 @@ typedef struct osrc_params {
     int osrc_side;       /* wavenumber of the OSRC operator: 0 exterior, 1 interior */
     int n_ss;            /* Gauss points per dimension of the Sauter-Schwab rules (2..12) */
     int precision;       /* OSRC_FP32_MATFREE or OSRC_FP64_DENSE */
-    double inner_tol;    /* relative residual of the inner mass / shifted solves (<= 1e-8) */
+    double inner_tol;    /* relative residual of the inner mass / shifted solves (<= 1e-8);
+                            checked on the true FP64 residual when the solves run
+                            as FP32 iterations refined in FP64 (meshes whose
+                            per-cluster-CTA slices fit shared memory) */
     int inner_maxit;     /* iteration cap of the inner solves */
     int precond;         /* preconditioner P of the GMRES solve: OSRC_PRECOND_* */
     int formulation;     /* OSRC_PMCHWT (default) or OSRC_MULLER */
@@ -133,7 +136,8 @@ typedef struct osrc_solve_info {
     double ms_matvec;          /* time in B x (far + near), ms, summed */
     double ms_precond;         /* time in M^-1 and OSRC, ms, summed */
     double ms_arnoldi;         /* time in orthogonalisation, ms, summed */
-    int inner_iterations_max;  /* largest inner CG/COCG iteration count seen */
+    int inner_iterations_max;  /* largest inner CG/COCG iteration count seen (FP32
+                                  iterations over all refinements when refined) */
     int total_iterations;      /* GMRES iterations summed over right-hand sides */
 } osrc_solve_info;
 
