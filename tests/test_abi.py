@@ -80,3 +80,33 @@ def test_input_meshes_valid(lib):
     for v, t in (icosphere(3), ellipsoid(500), bumpy_ellipsoid(800)):
         assert B.osrc_mesh_validate(v, t) == B.OSRC_OK
         assert t.shape[0] == 2 * v.shape[0] - 4
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    of the C structure in include/osrc_pmchwt.h (compiled with gcc)."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_2104_04609_gb300 import binding as B
+
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = [B.osrc_params, B.osrc_solve_info, B.osrc_batched_info, B.osrc_request, B.osrc_server_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "osrc_pmchwt.h"', "int main(void) {"]
+    for S in structs:
+        lines.append(f'    printf("{S.__name__} sizeof %zu\\n", sizeof({S.__name__}));')
+        for name, _ in S._fields_:
+            lines.append(f'    printf("{S.__name__} {name} %zu\\n", offsetof({S.__name__}, {name}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for S in structs:
+        assert got[(S.__name__, "sizeof")] == ctypes.sizeof(S), S.__name__
+        for name, _ in S._fields_:
+            assert got[(S.__name__, name)] == getattr(S, name).offset, (S.__name__, name)
