@@ -262,13 +262,12 @@ int umma_gemm_bf16(const void *A, int M, int K, const void *Bm, int N, float *C,
     OSRC_TRY(make_map(&ma, A, M, K, UM_BM));
     OSRC_TRY(make_map(&mb, Bm, N, K, N));
     const size_t smem = umma_smem_bytes(N);
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
-    std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)umma_smem_bytes(256));
-    });
-    OSRC_CK(attr);
+    static PerDeviceOnce once;
+    OSRC_TRY(per_device_once(once, [](int) -> int {
+        OSRC_CK(cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)umma_smem_bytes(256)));
+        return OSRC_OK;
+    }));
     umma_gemm_kernel<<<M / UM_BM, UM_THREADS, smem, st>>>(ma, mb, M, N, K, C, ldc, err);
     OSRC_CK(cudaGetLastError());
     return OSRC_OK;

@@ -574,37 +574,41 @@ __global__ void osrc_combine_kernel(int n, OsrcComb c, const double2 *__restrict
     z[n + i] = cmul(iik, b);
 }
 
-// Largest cluster the kernel may use: 16 CTAs (a non-portable size that the
-// kernel opts into) if the device can schedule it, else 8.
-int g_kry_max_cluster = 8;
+// Largest cluster the kernels may use on each device: 16 CTAs (a
+// non-portable size that the kernel opts into) if the device can schedule
+// it, else 8; 0 until kry_opt_in has run on that device.
+int g_kry_max_cluster[OSRC_MAX_DEVICES] = {};
 
 int kry_opt_in() {
-    static std::once_flag once;
-    static cudaError_t err = cudaSuccess;
-    std::call_once(once, [] {
-        err = cudaFuncSetAttribute(kry_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (err != cudaSuccess) {
+    static PerDeviceOnce once;
+    return per_device_once(once, [](int dev) -> int {
+        g_kry_max_cluster[dev] = 8;
+        if (cudaFuncSetAttribute(kry_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
             (void)cudaGetLastError();
-            err = cudaSuccess;
-            return;
+            return (int)OSRC_OK;
         }
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(16, 1, 1);
         cfg.blockDim = dim3(KRY_THREADS, 1, 1);
         int size = 0;
         if (cudaOccupancyMaxPotentialClusterSize(&size, kry_kernel, &cfg) == cudaSuccess && size >= 16)
-            g_kry_max_cluster = 16;
+            g_kry_max_cluster[dev] = 16;
         (void)cudaGetLastError();
+        return (int)OSRC_OK;
     });
-    OSRC_CK(err);
-    return OSRC_OK;
 }
 
-// CTAs per system: about 640 rows each, at most g_kry_max_cluster.
+// CTAs per system: about 640 rows each, at most the device's largest
+// cluster (call after kry_opt_in).
 int cluster_size_for(int n) {
+    int dev = 0;
+    const int mx = cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < OSRC_MAX_DEVICES &&
+                           g_kry_max_cluster[dev] > 0
+                       ? g_kry_max_cluster[dev]
+                       : 8;
     int cs = (n + 639) / 640;
     if (cs < 1) cs = 1;
-    if (cs > g_kry_max_cluster) cs = g_kry_max_cluster;
+    if (cs > mx) cs = mx;
     return cs;
 }
 
@@ -636,13 +640,16 @@ int kmix_decide(osrc_problem *pb, int cs) {
     }
     if (smem > KMIX_SMEM_MAX) return OSRC_OK;
     const int threads = ((rows + rpt - 1) / rpt + 31) / 32 * 32;
-    static std::once_flag once;
-    static int attr_status = OSRC_OK;
-    std::call_once(once, [] {
-        attr_status = kmix_attrs<1>();
-        if (attr_status == OSRC_OK) attr_status = kmix_attrs<2>();
+    static PerDeviceOnce once;
+    const int attr_status = per_device_once(once, [](int) -> int {
+        int st = kmix_attrs<1>();
+        if (st == OSRC_OK) st = kmix_attrs<2>();
+        return st;
     });
-    OSRC_TRY(attr_status);
+    if (attr_status != OSRC_OK) {  // no opt-in on this device: the FP64 kernel serves
+        (void)cudaGetLastError();
+        return OSRC_OK;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, 1, 1);
     cfg.blockDim = dim3(threads, 1, 1);

@@ -7,6 +7,7 @@
 
 #include <string>
 #include <atomic>
+#include <mutex>
 #include <cmath>
 #include <vector>
 
@@ -53,6 +54,28 @@ __host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
 // ---------------------------------------------------------------------------
 // handles
 // ---------------------------------------------------------------------------
+// One-time set-up per device: kernel attributes (opt-ins, shared-memory
+// limits) and occupancy-derived settings belong to the device that is current
+// when they are made, so each call site keeps one result per device.
+constexpr int OSRC_MAX_DEVICES = 64;
+struct PerDeviceOnce {
+    std::mutex m;
+    bool done[OSRC_MAX_DEVICES] = {};
+    int status[OSRC_MAX_DEVICES] = {};
+};
+template <typename F>
+int per_device_once(PerDeviceOnce &o, F f) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return OSRC_CUDA_ERROR;
+    if (dev < 0 || dev >= OSRC_MAX_DEVICES) return OSRC_UNSUPPORTED;
+    std::lock_guard<std::mutex> g(o.m);
+    if (!o.done[dev]) {
+        o.status[dev] = f(dev);
+        o.done[dev] = true;
+    }
+    return o.status[dev];
+}
+
 struct osrc_ctx {
     int device = 0;
     size_t budget = 0;               // 0 = unlimited
