@@ -6,10 +6,10 @@
 // FP64 accumulation.  Every rounding-sensitive step uses the explicit _rn
 // intrinsics, so the compiler cannot contract or reorder it.
 //
-// ff_sincos: Cody-Waite reduction by pi/2 (pi/2 split into three FP32 parts,
-// Cody & Waite 1980), then the Taylor series of sin and cos on |t| <= pi/4:
-// the leading terms in float-float, the tail (below 3e-8 of the result) in
-// FP32, and the quadrant from n mod 4.
+// ff2_sincos: Cody-Waite reduction by pi/2 (pi/2 split into three FP32
+// parts, Cody & Waite 1980), then the Taylor series of sin and cos on
+// |t| <= pi/4: the leading terms in float-float, the tail (below 3e-8 of the
+// result) in FP32, and the quadrant from n mod 4.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -55,11 +55,6 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
     return ff_fast_two_sum(p.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo)));
 }
 
-__device__ __forceinline__ ff ff_mulf(ff a, float b) {
-    const ff p = ff_two_prod(a.hi, b);
-    return ff_fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
-}
-
 __device__ __forceinline__ ff ff_fma(ff a, ff b, ff c) { return ff_add(ff_mul(a, b), c); }
 
 __device__ __forceinline__ ff ff_sqrt(ff a) {  // a > 0
@@ -78,42 +73,6 @@ __device__ __forceinline__ ff ff_rcp(ff a) {  // a != 0
 
 __device__ __forceinline__ ff ff_dot3(const ff *a, const ff *b) {
     return ff_add(ff_add(ff_mul(a[0], b[0]), ff_mul(a[1], b[1])), ff_mul(a[2], b[2]));
-}
-
-// sin and cos of x >= 0 (|x| < 2^22 pi/2).
-__device__ __forceinline__ void ff_sincos(ff x, ff &s, ff &c) {
-    // pi/2 = P1 + P2 + P3 (each the FP32 rounding of what is left)
-    const float P1 = 1.5707963705062866f, P2 = -4.371138828673793e-08f, P3 = -1.7151245100058819e-15f;
-    const float n = rintf(__fmul_rn(x.hi, 0.6366197466850281f));
-    ff t = ff_sub(x, ff_two_prod(n, P1));
-    t = ff_sub(t, ff_two_prod(n, P2));
-    t = ff_add(t, ff{__fmul_rn(-n, P3), 0.f});
-    const ff u = ff_mul(t, t);
-    const float uh = u.hi;
-    // sin t = t (1 - u/3! + u^2/5! - ... ), u = t^2; terms from u^5 in FP32
-    float ts = __fmaf_rn(uh, 2.8114573589663704e-15f, -7.647163609812713e-13f);
-    ts = __fmaf_rn(uh, ts, 1.6059044372074283e-10f);
-    ts = __fmaf_rn(uh, ts, -2.5052107943679403e-08f);
-    ff ps = ff_fma(ff{ts, 0.f}, u, ff{2.7557318844628753e-06f, 3.793571224297229e-14f});
-    ps = ff_fma(ps, u, ff{-0.00019841270113829523f, 2.725596874933456e-12f});
-    ps = ff_fma(ps, u, ff{0.008333333767950535f, -4.34617203337595e-10f});
-    ps = ff_fma(ps, u, ff{-0.1666666716337204f, 4.967053879312289e-09f});
-    ps = ff_fma(ps, u, ff{1.f, 0.f});
-    const ff st = ff_mul(ps, t);
-    // cos t = 1 - u/2! + u^2/4! - ... ; terms from u^6 in FP32
-    float tc = __fmaf_rn(uh, 4.7794772561329454e-14f, -1.147074536050896e-11f);
-    tc = __fmaf_rn(uh, tc, 2.0876755879584152e-09f);
-    ff pc = ff_fma(ff{tc, 0.f}, u, ff{-2.755731998149713e-07f, 7.575112209051195e-15f});
-    pc = ff_fma(pc, u, ff{2.4801587642286904e-05f, -3.40699609366682e-13f});
-    pc = ff_fma(pc, u, ff{-0.0013888889225199819f, 3.3631094437103215e-11f});
-    pc = ff_fma(pc, u, ff{0.0416666679084301f, -1.2417634698280722e-09f});
-    pc = ff_fma(pc, u, ff{-0.5f, 0.f});
-    const ff ct = ff_fma(pc, u, ff{1.f, 0.f});
-    const int q = ((int)n) & 3;
-    if (q == 0) { s = st; c = ct; }
-    else if (q == 1) { s = ct; c = ff_neg(st); }
-    else if (q == 2) { s = ff_neg(st); c = ff_neg(ct); }
-    else { s = ff_neg(ct); c = st; }
 }
 
 // ---- two float-float numbers packed into FP32x2 lanes -------------------
@@ -165,8 +124,9 @@ __device__ __forceinline__ ff2 ff2_mul(ff2 a, ff2 b) {
 
 __device__ __forceinline__ ff2 ff2_fma(ff2 a, ff2 b, ff2 c) { return ff2_add(ff2_mul(a, b), c); }
 
-// sin and cos of both lanes, x >= 0 (see ff_sincos)
+// sin and cos of both lanes, x >= 0 (|x| < 2^22 pi/2)
 __device__ __forceinline__ void ff2_sincos(ff2 x, ff2 &s, ff2 &c) {
+    // pi/2 = P1 + P2 + P3 (each the FP32 rounding of what is left)
     const float P1 = 1.5707963705062866f, P2 = -4.371138828673793e-08f, P3 = -1.7151245100058819e-15f;
     const float2 xh = __fmul2_rn(x.hi, f2_dup(0.6366197466850281f));
     const float2 n = make_float2(rintf(xh.x), rintf(xh.y));
@@ -176,6 +136,7 @@ __device__ __forceinline__ void ff2_sincos(ff2 x, ff2 &s, ff2 &c) {
     const ff2 u = ff2_mul(t, t);
     const float2 uh = u.hi;
     auto K = [](float h, float l) { return ff2{f2_dup(h), f2_dup(l)}; };
+    // sin t = t (1 - u/3! + u^2/5! - ... ), u = t^2; terms from u^5 in FP32
     float2 ts = __ffma2_rn(uh, f2_dup(2.8114573589663704e-15f), f2_dup(-7.647163609812713e-13f));
     ts = __ffma2_rn(uh, ts, f2_dup(1.6059044372074283e-10f));
     ts = __ffma2_rn(uh, ts, f2_dup(-2.5052107943679403e-08f));
@@ -185,6 +146,7 @@ __device__ __forceinline__ void ff2_sincos(ff2 x, ff2 &s, ff2 &c) {
     ps = ff2_fma(ps, u, K(-0.1666666716337204f, 4.967053879312289e-09f));
     ps = ff2_fma(ps, u, K(1.f, 0.f));
     const ff2 st = ff2_mul(ps, t);
+    // cos t = 1 - u/2! + u^2/4! - ... ; terms from u^6 in FP32
     float2 tc = __ffma2_rn(uh, f2_dup(4.7794772561329454e-14f), f2_dup(-1.147074536050896e-11f));
     tc = __ffma2_rn(uh, tc, f2_dup(2.0876755879584152e-09f));
     ff2 pc = ff2_fma(ff2{tc, f2_dup(0.f)}, u, K(-2.755731998149713e-07f, 7.575112209051195e-15f));
