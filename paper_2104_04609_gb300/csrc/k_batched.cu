@@ -100,15 +100,6 @@ __global__ void pack_b_kernel(int n2, int R, int Kp, const float2 *__restrict__ 
     }
 }
 
-// zero the padding columns of B_cat once
-__global__ void zero_pad_b_kernel(int n2, int NN, int Kp, __nv_bfloat16 *__restrict__ Bcat) {
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int pad = Kp - 2 * n2;
-    if (pad <= 0 || idx >= (size_t)NN * pad) return;
-    const int r = (int)(idx / pad), k = 2 * n2 + (int)(idx % pad);
-    Bcat[(size_t)r * Kp + k] = __float2bfloat16_rn(0.f);
-}
-
 // y[m][r] = (C[m][r], C[m][R + r]) + (near CSR product)[m][r]
 __global__ void unpack_near_kernel(int nv, int R, int ldc, const float *__restrict__ C,
                                    const int *__restrict__ ptr, const int *__restrict__ col,

@@ -169,7 +169,6 @@ __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ f2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ f2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
-__device__ __forceinline__ f2 neg2(f2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ f2 dup2(float a) { return make_float2(a, a); }
 
 // Constants as (value, value) pairs for the packed instructions.  The D
