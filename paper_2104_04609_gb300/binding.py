@@ -241,7 +241,10 @@ def osrc_status_string(status):
 def osrc_params_default(**overrides):
     p = osrc_params()
     lib().osrc_params_default(ctypes.byref(p))
+    names = {f[0] for f in osrc_params._fields_}
     for k, v in overrides.items():
+        if k not in names:  # ctypes would accept any attribute name silently
+            raise TypeError(f"unknown osrc_params field {k!r}")
         setattr(p, k, v)
     return p
 
@@ -556,18 +559,16 @@ class Solver:
         (connected component) of the mesh; k_int and rho_ratio are then unused."""
         import torch
 
+        kk = float(k_int) if objects is None else float(objects[0][0])
+        rr = float(rho_ratio) if objects is None else float(objects[1][0])
+        p = osrc_params_default(k_ext=float(k_ext), k_int=kk, rho_ratio=rr, **params)
+        self.params = p
         self.device = torch.device("cuda", device)
         self.ctx = osrc_create(device, mem_budget_bytes)
         self.mesh = None
         self.pb = None
         try:
             self.mesh = osrc_mesh_create(self.ctx, verts, tris)
-            kk = float(k_int) if objects is None else float(objects[0][0])
-            rr = float(rho_ratio) if objects is None else float(objects[1][0])
-            p = osrc_params_default(k_ext=float(k_ext), k_int=kk, rho_ratio=rr)
-            for k, v in params.items():
-                setattr(p, k, v)
-            self.params = p
             if objects is None:
                 self.pb = osrc_problem_create(self.mesh, p)
             else:

@@ -110,3 +110,19 @@ def test_struct_layouts_match_header(tmp_path):
         assert got[(S.__name__, "sizeof")] == ctypes.sizeof(S), S.__name__
         for name, _ in S._fields_:
             assert got[(S.__name__, name)] == getattr(S, name).offset, (S.__name__, name)
+
+
+def test_unknown_params_rejected(lib):
+    """A misspelt parameter raises instead of becoming a stray Python
+    attribute of the ctypes structure (checked before any device call)."""
+    from paper_2104_04609_gb300 import binding as B
+    from paper_2104_04609_gb300.inputs import icosphere
+
+    p = B.osrc_params_default(dense_assembly=B.OSRC_ASSEMBLE_FF, k_int_im=0.1)
+    assert p.dense_assembly == B.OSRC_ASSEMBLE_FF and p.k_int_im == 0.1
+    with pytest.raises(TypeError):
+        B.osrc_params_default(dense_asembly=1)
+    pytest.importorskip("torch")
+    v, t = icosphere(1)
+    with pytest.raises(TypeError):
+        B.Solver(v, t, 2.0, 3.0, 1.5, precision=B.OSRC_FP64_DENSE, dense_asembly=1)
