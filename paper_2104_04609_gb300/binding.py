@@ -224,6 +224,19 @@ def _dev(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _need(t, n, what):
+    """Raises unless the buffer t (torch tensor or numpy array) holds at least
+    n elements: the C ABI takes bare pointers, so a short buffer would be
+    read or written past its end on the device."""
+    have = int(t.numel()) if hasattr(t, "numel") else int(np.size(t))
+    if have < n:
+        raise ValueError(f"{what}: buffer holds {have} elements, {n} needed")
+
+
+def _nv2(pb):
+    return 2 * int(lib().osrc_problem_nv(pb))
+
+
 def _stream(stream=None):
     import torch
 
@@ -319,27 +332,35 @@ def osrc_problem_nv(pb):
 
 def osrc_rhs_planewave(pb, dirs, b, stream=None):
     d, dp = _host_f64(np.atleast_2d(dirs))
+    _need(b, d.shape[0] * _nv2(pb), "osrc_rhs_planewave b")
     _check(lib().osrc_rhs_planewave(pb, dp, d.shape[0], _dev(b), _stream(stream)),
            "osrc_rhs_planewave")
 
 
 def osrc_rhs_pointsource(pb, srcs, b, stream=None):
     d, dp = _host_f64(np.atleast_2d(srcs))
+    _need(b, d.shape[0] * _nv2(pb), "osrc_rhs_pointsource b")
     _check(lib().osrc_rhs_pointsource(pb, dp, d.shape[0], _dev(b), _stream(stream)),
            "osrc_rhs_pointsource")
 
 
 def osrc_pmchwt_apply(pb, x, y, nrhs=1, form=OSRC_WEAK, part=OSRC_PART_ALL, stream=None):
+    _need(x, int(nrhs) * _nv2(pb), "osrc_pmchwt_apply x")
+    _need(y, int(nrhs) * _nv2(pb), "osrc_pmchwt_apply y")
     _check(lib().osrc_pmchwt_apply(pb, _dev(x), _dev(y), int(nrhs), int(form), int(part),
                                    _stream(stream)), "osrc_pmchwt_apply")
 
 
 def osrc_mass_solve(pb, x, y, nrhs=1, stream=None):
+    _need(x, int(nrhs) * _nv2(pb), "osrc_mass_solve x")
+    _need(y, int(nrhs) * _nv2(pb), "osrc_mass_solve y")
     _check(lib().osrc_mass_solve(pb, _dev(x), _dev(y), int(nrhs), _stream(stream)),
            "osrc_mass_solve")
 
 
 def osrc_precond_apply(pb, x, y, nrhs=1, stream=None):
+    _need(x, int(nrhs) * _nv2(pb), "osrc_precond_apply x")
+    _need(y, int(nrhs) * _nv2(pb), "osrc_precond_apply y")
     _check(lib().osrc_precond_apply(pb, _dev(x), _dev(y), int(nrhs), _stream(stream)),
            "osrc_precond_apply")
 
@@ -349,6 +370,8 @@ def osrc_gmres_solve(pb, b, x, nrhs=1, tol=1e-5, maxit=500, host_buffers=False,
     """Returns the osrc_solve_info record.  With host_buffers, b and x are
     numpy complex128 arrays (C-contiguous), else CUDA tensors."""
     info = osrc_solve_info()
+    _need(b, int(nrhs) * _nv2(pb), "osrc_gmres_solve b")
+    _need(x, int(nrhs) * _nv2(pb), "osrc_gmres_solve x")
     if host_buffers:
         if not (isinstance(b, np.ndarray) and isinstance(x, np.ndarray)
                 and b.dtype == np.complex128 and x.dtype == np.complex128
@@ -468,6 +491,8 @@ def osrc_dense_batched_solve(pb, b, x, tol=1e-6, max_refine=8, inner_tol=1e-3, i
     """Batched mixed-precision solve; b, x (nrhs, 2nv) complex128 CUDA tensors.
     Returns the osrc_batched_info record as a dict."""
     info = osrc_batched_info()
+    _need(b, int(b.shape[0]) * _nv2(pb), "osrc_dense_batched_solve b")
+    _need(x, int(b.shape[0]) * _nv2(pb), "osrc_dense_batched_solve x")
     s = lib().osrc_dense_batched_solve(pb, _dev(b), _dev(x), int(b.shape[0]), float(tol),
                                        int(max_refine), float(inner_tol), int(inner_maxit),
                                        float(precond_tol), ctypes.byref(info), _stream(stream))
@@ -477,6 +502,8 @@ def osrc_dense_batched_solve(pb, b, x, tol=1e-6, max_refine=8, inner_tol=1e-3, i
 
 
 def osrc_dense_batched_apply(pb, x, y, what, stream=None):
+    _need(x, int(x.shape[0]) * _nv2(pb), "osrc_dense_batched_apply x")
+    _need(y, int(x.shape[0]) * _nv2(pb), "osrc_dense_batched_apply y")
     _check(lib().osrc_dense_batched_apply(pb, _dev(x), _dev(y), int(x.shape[0]), int(what),
                                           _stream(stream)), "osrc_dense_batched_apply")
 
@@ -485,6 +512,8 @@ def osrc_dense_batched_apply_ex(pb, x, y, what, ptol, pmaxit, stream=None):
     """As osrc_dense_batched_apply with the preconditioner's inner tolerance and
     cap given; returns the largest inner iteration count."""
     k = ctypes.c_int(0)
+    _need(x, int(x.shape[0]) * _nv2(pb), "osrc_dense_batched_apply_ex x")
+    _need(y, int(x.shape[0]) * _nv2(pb), "osrc_dense_batched_apply_ex y")
     _check(lib().osrc_dense_batched_apply_ex(pb, _dev(x), _dev(y), int(x.shape[0]), int(what),
                                              float(ptol), int(pmaxit), ctypes.byref(k),
                                              _stream(stream)), "osrc_dense_batched_apply_ex")
@@ -507,8 +536,16 @@ def osrc_field_eval(pb, x, pts, u, inc_kind=OSRC_INC_NONE, inc_param=None, regio
     float64, u (n,) complex128, region (n,) int32 or None: CUDA tensors."""
     import torch
 
-    assert pts.dtype == torch.float64 and pts.is_cuda and pts.is_contiguous()
+    if not (pts.dtype == torch.float64 and pts.is_cuda and pts.is_contiguous() and pts.dim() == 2
+            and pts.shape[1] == 3):
+        raise TypeError("pts: expected a contiguous (n, 3) float64 CUDA tensor")
     n = int(pts.shape[0])
+    _need(x, _nv2(pb), "osrc_field_eval x")
+    _need(u, n, "osrc_field_eval u")
+    if region is not None:
+        if not (region.dtype == torch.int32 and region.is_cuda and region.is_contiguous()):
+            raise TypeError("region: expected a contiguous int32 CUDA tensor")
+        _need(region, n, "osrc_field_eval region")
     par = None
     if inc_kind != OSRC_INC_NONE:
         par = np.ascontiguousarray(inc_param, dtype=np.float64).reshape(3)

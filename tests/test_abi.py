@@ -126,3 +126,17 @@ def test_unknown_params_rejected(lib):
     v, t = icosphere(1)
     with pytest.raises(TypeError):
         B.Solver(v, t, 2.0, 3.0, 1.5, precision=B.OSRC_FP64_DENSE, dense_asembly=1)
+
+
+def test_short_buffers_rejected_on_the_host():
+    """The binding's size check (the C ABI takes bare pointers) raises for a
+    buffer shorter than the call needs, for tensors and numpy arrays."""
+    from paper_2104_04609_gb300 import binding as B
+
+    B._need(np.zeros(8), 8, "x")
+    with pytest.raises(ValueError):
+        B._need(np.zeros(7), 8, "x")
+    torch = pytest.importorskip("torch")
+    B._need(torch.zeros(2, 4, dtype=torch.complex128), 8, "x")
+    with pytest.raises(ValueError):
+        B._need(torch.zeros(2, 3, dtype=torch.complex128), 8, "x")
