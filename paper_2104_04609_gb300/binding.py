@@ -434,7 +434,13 @@ def osrc_server_submit(sv, verts, tris, params, src, rhs_kind=0, tol=1e-5, maxit
                       int(rhs_kind), s.ctypes.data, s.shape[0], float(tol), int(maxit))
     rid = ctypes.c_longlong()
     _check(lib().osrc_server_submit(sv, ctypes.byref(rq), ctypes.byref(rid)), "osrc_server_submit")
+    _REQ_SHAPE[(sv.value, rid.value)] = (s.shape[0], v.shape[0])
     return rid.value
+
+
+# (server, request id) -> (right-hand sides, vertices) of each submitted
+# request, so that osrc_server_result sizes the host copy from the request
+_REQ_SHAPE = {}
 
 
 def osrc_server_poll(sv, rid):
@@ -454,9 +460,19 @@ def osrc_server_wait(sv, rid, timeout_s=600.0):
     return lib().osrc_server_wait(sv, int(rid), float(timeout_s))
 
 
-def osrc_server_result(sv, rid, nrhs, nv):
-    x = np.zeros((nrhs, 2 * nv), dtype=np.complex128)
+def osrc_server_result(sv, rid, nrhs=None, nv=None):
+    """(status, solution (nrhs, 2nv)); the sizes come from the submitted
+    request (nrhs, nv, when given, must match it)."""
+    key = (sv.value, int(rid))
+    shape = _REQ_SHAPE.get(key)
+    if shape is None:
+        raise ValueError(f"request {rid} was not submitted through this binding")
+    if (nrhs is not None and int(nrhs) != shape[0]) or (nv is not None and int(nv) != shape[1]):
+        raise ValueError(f"request {rid} has {shape[0]} right-hand sides on {shape[1]} vertices")
+    x = np.zeros((shape[0], 2 * shape[1]), dtype=np.complex128)
     s = lib().osrc_server_result(sv, int(rid), ctypes.c_void_p(x.ctypes.data))
+    if s != OSRC_TIMEOUT:  # the library released the request
+        _REQ_SHAPE.pop(key, None)
     return s, x
 
 

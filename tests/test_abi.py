@@ -140,3 +140,14 @@ def test_short_buffers_rejected_on_the_host():
     B._need(torch.zeros(2, 4, dtype=torch.complex128), 8, "x")
     with pytest.raises(ValueError):
         B._need(torch.zeros(2, 3, dtype=torch.complex128), 8, "x")
+
+
+def test_server_result_needs_a_submitted_request():
+    """The host copy of a server result is sized from the submitted request;
+    an id that was never submitted raises before the library is called."""
+    import ctypes
+
+    from paper_2104_04609_gb300 import binding as B
+
+    with pytest.raises(ValueError):
+        B.osrc_server_result(ctypes.c_void_p(0x1234), 7)
