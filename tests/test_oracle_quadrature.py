@@ -116,8 +116,6 @@ def test_coincident_laplace_single_layer_closed_form():
 def test_sauter_schwab_exponential_convergence(pair):
     verts = np.array([[0.0, 0.0, 0.0], [1.0, 0.1, 0.0], [0.2, 0.9, 0.1],
                       [0.6, -0.8, 0.3], [-0.7, -0.2, 0.4]])
-    tris = np.array([[0, 1, 2], [1, 0, 3], [0, 4, 2 if pair != "vertex" else 3]],
-                    dtype=np.int32)
     tris = np.array([[0, 1, 2], [1, 0, 3], [0, 3, 4]], dtype=np.int32)
     s = {"coincident": 0, "edge": 1, "vertex": 2}[pair]
     vals = []
