@@ -424,7 +424,7 @@ void osrc_server_destroy(osrc_server *sv);
  * pattern (n rows) with the library's cluster-batched Krylov kernel:
  * Hermitian CG when conj = 1 (real SPD systems), COCG when conj = 0
  * (complex-symmetric systems), Jacobi-preconditioned, to |r_s| <= tol |f_s|
- * or maxit iterations.  All pointers except alpha, beta and iters_out are
+ * (0 < tol <= 1e-4, else OSRC_INVALID_ARG) or maxit iterations.  All pointers except alpha, beta and iters_out are
  * device pointers owned by the caller: row_ptr (n+1), col_idx, M_vals,
  * S_vals (row_ptr[n] each, int32 / double), f and w (nsys x n complex,
  * interleaved).  alpha, beta: host, nsys complex each.
@@ -435,7 +435,10 @@ void osrc_server_destroy(osrc_server *sv);
  * process exit; requests with nsys * n > 131072 or nsys > 16 are rejected
  * with OSRC_INVALID_ARG.  The work runs on the calling thread's current
  * device.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * (cudaGetSymbolAddress), so make that first call before any stream capture;
+ * the address is looked up again when the device's context has changed
+ * (after cudaDeviceReset), so the first call after a reset also belongs
+ * outside a capture.
  * All calls on a device share the array and it keeps the last call's
  * contents: calls whose kernels overlap on the GPU race and must be
  * serialised by the caller.
@@ -465,6 +468,16 @@ long long osrc_far_pairs(const osrc_problem *pb);
 /* Number of touching triangle pairs (near-field pairs) and near CSR blocks. */
 long long osrc_near_pairs(const osrc_problem *pb);
 long long osrc_near_nnz(const osrc_problem *pb);
+
+/* ---- measurement aid ----------------------------------------------------------------- */
+/* Not part of the paper's method.  Measures the FP32 throughput of the
+ * calling thread's current GPU, the denominator of the far-field kernel's
+ * roofline: FFMA (scalar) and FP32x2 FMA (packed) loops over independent
+ * chains at full occupancy with no memory traffic, each launched reps + 2
+ * times on `stream` (the first two untimed); the fastest launch gives
+ * *tflops_scalar and *tflops_packed (FMA = 2 flops).  Allocates and frees a
+ * small device buffer.  reps in [1, 100]. */
+int osrc_fp32_peak(int reps, double *tflops_scalar, double *tflops_packed, void *stream);
 
 #ifdef __cplusplus
 }

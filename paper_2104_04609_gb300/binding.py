@@ -9,7 +9,6 @@ import fails loudly (there is no fallback).
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 
 import numpy as np
@@ -177,6 +176,7 @@ SIGNATURES = {
     "osrc_far_pairs": (ctypes.c_longlong, [_VP]),
     "osrc_near_pairs": (ctypes.c_longlong, [_VP]),
     "osrc_near_nnz": (ctypes.c_longlong, [_VP]),
+    "osrc_fp32_peak": (ctypes.c_int, [ctypes.c_int, _DP, _DP, _VP]),
 }
 
 _LIB = None
@@ -389,6 +389,24 @@ def osrc_gmres_solve(pb, b, x, nrhs=1, tol=1e-5, maxit=500, host_buffers=False,
     return info
 
 
+def _noalloc_shapes(row_ptr, col_idx, M_vals, S_vals, alpha, beta, f, w):
+    """Shape checks of osrc_shifted_solve_noalloc, before any device call:
+    the C side takes bare pointers, so every buffer must hold what the n rows
+    and nsys systems imply (else ValueError).  Returns (nsys, n)."""
+    if len(getattr(f, "shape", ())) != 2:
+        raise ValueError("f must be a 2-D (nsys, n) array")
+    nsys, n = int(f.shape[0]), int(f.shape[1])
+    if tuple(getattr(w, "shape", ())) != (nsys, n):
+        raise ValueError(f"w must have the shape of f, ({nsys}, {n})")
+    _need(row_ptr, n + 1, "osrc_shifted_solve_noalloc row_ptr")
+    nnz = [int(t.numel()) if hasattr(t, "numel") else int(np.size(t)) for t in (col_idx, M_vals, S_vals)]
+    if len(set(nnz)) != 1:
+        raise ValueError(f"col_idx, M_vals and S_vals must have one length, got {nnz}")
+    if len(np.atleast_1d(alpha)) != nsys or len(np.atleast_1d(beta)) != nsys:
+        raise ValueError(f"alpha and beta must hold nsys = {nsys} values each")
+    return nsys, n
+
+
 def osrc_shifted_solve_noalloc(row_ptr, col_idx, M_vals, S_vals, alpha, beta, f, w,
                                tol=1e-10, maxit=2000, conj=0, stream=None):
     """Allocation-free batched solve of (alpha_s M + beta_s S) w_s = f_s.
@@ -401,13 +419,13 @@ def osrc_shifted_solve_noalloc(row_ptr, col_idx, M_vals, S_vals, alpha, beta, f,
     nsys complex numbers.  Returns the per-system iteration counts."""
     import torch
 
+    nsys, n = _noalloc_shapes(row_ptr, col_idx, M_vals, S_vals, alpha, beta, f, w)
     for t, dt in ((row_ptr, torch.int32), (col_idx, torch.int32), (M_vals, torch.float64),
                   (S_vals, torch.float64)):
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
             raise TypeError("CSR arrays must be contiguous CUDA tensors (int32 / float64)")
-    nsys, n = int(f.shape[0]), int(f.shape[1])
-    a = np.ascontiguousarray(np.asarray(alpha, dtype=np.complex128).view(np.float64))
-    b = np.ascontiguousarray(np.asarray(beta, dtype=np.complex128).view(np.float64))
+    a = np.ascontiguousarray(np.asarray(alpha, dtype=np.complex128).reshape(-1).view(np.float64))
+    b = np.ascontiguousarray(np.asarray(beta, dtype=np.complex128).reshape(-1).view(np.float64))
     it = (ctypes.c_int * nsys)()
     s = lib().osrc_shifted_solve_noalloc(
         n, ctypes.c_void_p(row_ptr.data_ptr()), ctypes.c_void_p(col_idx.data_ptr()),
@@ -484,6 +502,8 @@ def osrc_server_get_stats(sv):
 
 def osrc_server_destroy(sv):
     lib().osrc_server_destroy(sv)
+    for key in [k for k in _REQ_SHAPE if k[0] == sv.value]:
+        del _REQ_SHAPE[key]
 
 
 def osrc_gemm_bf16(A, B, C, err, stream=None):
@@ -597,6 +617,15 @@ def osrc_near_pairs(pb):
 
 def osrc_near_nnz(pb):
     return lib().osrc_near_nnz(pb)
+
+
+def osrc_fp32_peak(reps=5, stream=None):
+    """Measured FP32 throughput of the current GPU: (scalar FFMA TFLOP/s,
+    packed FP32x2 FMA TFLOP/s)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().osrc_fp32_peak(int(reps), ctypes.byref(a), ctypes.byref(b), _stream(stream)),
+           "osrc_fp32_peak")
+    return a.value, b.value
 
 
 # ---------------------------------------------------------------------------

@@ -20,6 +20,7 @@
 // FP64, used whenever a CTA's rows and FP32 entries fit) and kry_kernel
 // (all FP64: larger meshes, in-place systems, the allocation-free entry).
 #include <cooperative_groups.h>
+#include <cuda.h>
 
 #include <algorithm>
 #include <mutex>
@@ -956,6 +957,7 @@ struct NoAllocScratch {
     double2 *work = nullptr;
     int *stat = nullptr;
     double *res = nullptr;
+    unsigned long long ctx_id = 0;  // context the addresses belong to
     bool ready = false;
 };
 
@@ -963,16 +965,53 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 std::mutex g_noalloc_mu;
 NoAllocScratch g_noalloc[NOALLOC_MAX_DEVICES];
 
-// Device address of the scratch array on the current device, looked up once
-// per device (cudaGetSymbolAddress needs that device to be current).
+// Unique id of the context current on this host thread (driver entry
+// points reached through the runtime, so no link against libcuda).  Ids are
+// never reused, so a device reset, which replaces the primary context and
+// with it the array's address, shows up as a new id.
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
+int current_ctx_id(unsigned long long &id) {
+    static PfnCtxGetCurrent get_cur = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    if (!get_cur || !get_id) {
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        OSRC_CK(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void **)&get_cur, 12000,
+                                                 cudaEnableDefault, &q1));
+        OSRC_CK(cudaGetDriverEntryPointByVersion("cuCtxGetId", (void **)&get_id, 12000,
+                                                 cudaEnableDefault, &q2));
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !get_cur || !get_id) {
+            osrc_set_error("driver entry points cuCtxGetCurrent / cuCtxGetId not found");
+            return OSRC_UNSUPPORTED;
+        }
+    }
+    CUcontext c = nullptr;
+    if (get_cur(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) {
+        osrc_set_error("no current CUDA context");
+        return OSRC_CUDA_ERROR;
+    }
+    return OSRC_OK;
+}
+
+// Device address of the scratch array on the current device.  Looked up
+// with cudaGetSymbolAddress (that device current) on the first call on a
+// device and again whenever the device's context has changed since (after
+// cudaDeviceReset), so a kernel is never given an address of a context that
+// no longer exists.
 int noalloc_scratch(int dev, NoAllocScratch &out) {
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return OSRC_UNSUPPORTED;
+    // makes the device's primary context current (created if needed)
+    OSRC_CK(cudaSetDevice(dev));
+    unsigned long long id = 0;
+    OSRC_TRY(current_ctx_id(id));
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     NoAllocScratch &s = g_noalloc[dev];
-    if (!s.ready) {
+    if (!s.ready || s.ctx_id != id) {
+        s.ready = false;
         OSRC_CK(cudaGetSymbolAddress((void **)&s.work, g_noalloc_work));
         OSRC_CK(cudaGetSymbolAddress((void **)&s.stat, g_noalloc_stat));
         OSRC_CK(cudaGetSymbolAddress((void **)&s.res, g_noalloc_res));
+        s.ctx_id = id;
         s.ready = true;
     }
     out = s;

@@ -142,6 +142,62 @@ def test_short_buffers_rejected_on_the_host():
         B._need(torch.zeros(2, 3, dtype=torch.complex128), 8, "x")
 
 
+def test_noalloc_shapes_rejected_on_the_host():
+    """The allocation-free shifted solve takes bare pointers too: every
+    buffer is checked against n and nsys before any device call."""
+    from paper_2104_04609_gb300 import binding as B
+
+    torch = pytest.importorskip("torch")
+    n, nsys, nnz = 10, 3, 28
+    rp = torch.zeros(n + 1, dtype=torch.int32)
+    ci = torch.zeros(nnz, dtype=torch.int32)
+    mv = torch.zeros(nnz, dtype=torch.float64)
+    sv = torch.zeros(nnz, dtype=torch.float64)
+    f = torch.zeros(nsys, n, dtype=torch.complex128)
+    w = torch.zeros(nsys, n, dtype=torch.complex128)
+    al, be = [1.0] * nsys, [0.5] * nsys
+    assert B._noalloc_shapes(rp, ci, mv, sv, al, be, f, w) == (nsys, n)
+    bad = [
+        (rp, ci, mv, sv, al, be, f.reshape(-1), w),                      # f not 2-D
+        (rp, ci, mv, sv, al, be, f, w[:, :-1]),                          # w short
+        (rp[:-1], ci, mv, sv, al, be, f, w),                             # row_ptr short
+        (rp, ci, mv[:-1], sv, al, be, f, w),                             # values differ
+        (rp, ci, mv, sv[:-2], al, be, f, w),
+        (rp, ci, mv, sv, al[:-1], be, f, w),                             # alpha short
+        (rp, ci, mv, sv, al, be + [1.0], f, w),                          # beta long
+    ]
+    for args in bad:
+        with pytest.raises(ValueError):
+            B._noalloc_shapes(*args)
+        # the public wrapper checks shapes before it looks at devices
+        with pytest.raises(ValueError):
+            B.osrc_shifted_solve_noalloc(*args)
+
+
+def test_server_destroy_forgets_request_shapes():
+    """Request shapes kept for sizing results are dropped with their server,
+    so a later server at the same address starts clean."""
+    import ctypes
+
+    from paper_2104_04609_gb300 import binding as B
+
+    class _NoLib:
+        def osrc_server_destroy(self, sv):
+            return None
+
+    sv = ctypes.c_void_p(0x5678)
+    B._REQ_SHAPE[(sv.value, 1)] = (2, 100)
+    B._REQ_SHAPE[(0x9999, 1)] = (1, 50)
+    saved = B._LIB
+    B._LIB = _NoLib()
+    try:
+        B.osrc_server_destroy(sv)
+    finally:
+        B._LIB = saved
+    assert (sv.value, 1) not in B._REQ_SHAPE and (0x9999, 1) in B._REQ_SHAPE
+    del B._REQ_SHAPE[(0x9999, 1)]
+
+
 def test_server_result_needs_a_submitted_request():
     """The host copy of a server result is sized from the submitted request;
     an id that was never submitted raises before the library is called."""
