@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libosrc_pmchwt.so")
 SOURCES = ["osrc_api.cu", "k_far.cu", "k_near.cu", "k_sparse.cu", "k_gmres.cu", "k_rhs.cu",
-           "server.cu", "k_dense.cu", "k_batched.cu", "k_field.cu"]
+           "server.cu", "k_dense.cu", "k_batched.cu", "k_field.cu", "k_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 # per-file flags: the FP32 far-field kernel flushes FP32 subnormals (its

@@ -93,6 +93,29 @@ def test_far_field_parity_large_phase(B, small):
         S.close()
 
 
+def test_far_field_parity_top_of_plain_phase_range(B, small):
+    """The plain far kernel feeds k r straight to the FP32 sine / cosine until
+    k_max x (bounding-box diagonal) exceeds 64 pi; here k_max diag = 63 pi, just
+    below that switch, where its FP32 phase error is largest (phases up to
+    about k_max x diameter = 114 rad on this sphere)."""
+    v, t, _ = small
+    diag = float(np.linalg.norm(v.max(axis=0) - v.min(axis=0)))
+    k1 = 63.0 * math.pi / diag
+    k0 = 0.7 * k1
+    assert max(k0, k1) * diag < 64.0 * math.pi
+    S = B.Solver(v, t, k0, k1, RHO)
+    try:
+        far = O.pmchwt_matrix(v, t, k0, k1, RHO, nss=S.params.n_ss, part=1)
+        for seed in (23, 24):
+            x = _rand(2 * v.shape[0], seed)
+            y = _apply(B, S, x, part=B.OSRC_PART_FAR)
+            ref = far @ x
+            assert _rel(y, ref) < 1e-5
+            assert np.abs(y - ref).max() < 1e-5 * np.abs(ref).max()
+    finally:
+        S.close()
+
+
 def test_near_field_parity(B, small, small_ref):
     v, t, S = small
     _, near, _, _ = small_ref
