@@ -41,6 +41,8 @@ __host__ __device__ inline void rule_point(int q, double bary[3], double &w) {
 }
 
 constexpr int FAR_THREADS = 128;
+// largest k_max x (bounding-box diagonal) for the plain (FP32 k r) variant
+constexpr double FAR_PLAIN_MAX_PHASE = 32.0 * 3.14159265358979323846;
 constexpr int FAR_TS = 64;  // source triangles per shared-memory tile
 
 __global__ void far_geom_kernel(const double *__restrict__ verts, const int *__restrict__ tris,
@@ -597,8 +599,11 @@ int far_setup_geometry(osrc_problem *pb, cudaStream_t st) {
                                                       pb->d_tv.p, pb->d_tgeo.p);
     pb->launches++;
     OSRC_CK(cudaGetLastError());
-    // largest phase k r over the mesh (bounding-box diagonal): beyond 64 pi
-    // radians the centred variant with float-float phases is used
+    // largest phase k r over the mesh (bounding-box diagonal): beyond
+    // FAR_PLAIN_MAX_PHASE radians the centred variant with float-float
+    // phases is used.  The plain variant's FP32 phase error grows linearly
+    // with k r: measured 1.04e-5 relative (operator apply) at
+    // k_max x diagonal = 63 pi, so the switch sits at 32 pi (about 5e-6)
     {
         double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
         for (int i = 0; i < m->nv; ++i)
@@ -610,7 +615,7 @@ int far_setup_geometry(osrc_problem *pb, cudaStream_t st) {
                                  (hi[2] - lo[2]) * (hi[2] - lo[2]));
         double kmax = fmax(pb->p.k_ext, pb->p.k_int);
         for (const ObjMat &o : pb->obj) kmax = fmax(kmax, o.k1);
-        pb->far_reduce = kmax * diag > 64.0 * 3.14159265358979323846;
+        pb->far_reduce = kmax * diag > FAR_PLAIN_MAX_PHASE;
     }
     // split the source range so that the grid covers the GPU several times
     int dev = m->ctx->device, sms = 0, per_sm = 0;

@@ -93,16 +93,17 @@ def test_far_field_parity_large_phase(B, small):
         S.close()
 
 
-def test_far_field_parity_top_of_plain_phase_range(B, small):
+@pytest.mark.parametrize("phase_pi", [31.0, 33.0])
+def test_far_field_parity_top_of_plain_phase_range(B, small, phase_pi):
     """The plain far kernel feeds k r straight to the FP32 sine / cosine until
-    k_max x (bounding-box diagonal) exceeds 64 pi; here k_max diag = 63 pi, just
-    below that switch, where its FP32 phase error is largest (phases up to
-    about k_max x diameter = 114 rad on this sphere)."""
+    k_max x (bounding-box diagonal) exceeds 32 pi, then switches to the centred
+    variant.  31 pi: just below the switch, where the plain variant's FP32
+    phase error is largest (phases up to about k_max x diameter = 56 rad on
+    this sphere); 33 pi: the centred variant just above it."""
     v, t, _ = small
     diag = float(np.linalg.norm(v.max(axis=0) - v.min(axis=0)))
-    k1 = 63.0 * math.pi / diag
+    k1 = phase_pi * math.pi / diag
     k0 = 0.7 * k1
-    assert max(k0, k1) * diag < 64.0 * math.pi
     S = B.Solver(v, t, k0, k1, RHO)
     try:
         far = O.pmchwt_matrix(v, t, k0, k1, RHO, nss=S.params.n_ss, part=1)

@@ -77,11 +77,17 @@ def test_noalloc_shifted_cocg_matches_direct(setup):
 
 def test_noalloc_rejects_oversized_requests(setup):
     B, S, M, Sm, csr, nv = setup
-    # 16 systems of 8193 rows: nsys * n = 131088 > 131072; rejected on the
-    # host before any device work, so the small CSR is never read
-    f = torch.zeros((16, 8193), dtype=torch.complex128, device="cuda")
+    # 16 systems of 8193 rows: nsys * n = 131088 > 131072; rejected by the
+    # library before any device work (a diagonal CSR of 8193 rows, so that the
+    # binding's own buffer checks pass and the call reaches the library)
+    n = 8193
+    diag = (torch.arange(n + 1, dtype=torch.int32, device="cuda"),
+            torch.arange(n, dtype=torch.int32, device="cuda"),
+            torch.ones(n, dtype=torch.float64, device="cuda"),
+            torch.zeros(n, dtype=torch.float64, device="cuda"))
+    f = torch.zeros((16, n), dtype=torch.complex128, device="cuda")
     with pytest.raises(B.OsrcError) as e:
-        B.osrc_shifted_solve_noalloc(*csr, [1.0] * 16, [0.0] * 16, f, f.clone(), conj=1)
+        B.osrc_shifted_solve_noalloc(*diag, [1.0] * 16, [0.0] * 16, f, f.clone(), conj=1)
     assert e.value.status == B.OSRC_INVALID_ARG
     f17 = torch.zeros((17, nv), dtype=torch.complex128, device="cuda")
     with pytest.raises(B.OsrcError) as e:
