@@ -44,6 +44,14 @@ FLOPS_PER_PAIR = 83
 # nominal count for a per-operator evaluation (V, K, T, D separately per
 # wavenumber), reported beside the main figure
 FLOPS_PER_PAIR_NOMINAL = 176
+# executed FP32 flops per far point pair of the several-right-hand-side far
+# kernel: shared per pair (distance, 1/r, 1/r^2, (y - x).n_x, k r, scaled cos
+# and sin, the V / D-normal / D-curl / H combinations with the K and D-normal
+# triangle factors folded in, and negated imaginary parts: 16 FMA, 22 MUL,
+# 5 ADD), plus per right-hand side the four complex multiply-adds into u1, u2
+# (16 FMA)
+FLOPS_PER_PAIR_MULTI_SHARED = 59
+FLOPS_PER_PAIR_MULTI_RHS = 32
 # GMRES iterations of this workload (measured on the GPU path; the oracle's
 # unrestarted GMRES needs the same count within +-2 at smaller sizes): used
 # to turn the oracle's sampled matvec rate into solves/s
@@ -70,14 +78,19 @@ def parse():
                     help="right-hand sides of the batched dense leg (ellipsoid8000; 0: skip)")
     ap.add_argument("--dense-matfree-rhs", type=int, default=1,
                     help="right-hand sides of the same workload solved matrix-free for comparison")
+    ap.add_argument("--multi-rhs", default="8,16",
+                    help="right-hand-side counts of the lockstep (several right-hand sides per "
+                         "far-field launch) leg on the headline mesh ('' to skip)")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the far-field apply on the 80000-vertex bumpy ellipsoid")
     ap.add_argument("--no-objects", action="store_true",
                     help="skip the four-sphere multiple-scattering solve")
-    ap.add_argument("--profile-case", choices=["far-small", "precond-small", "dense-short", "dense-small"],
+    ap.add_argument("--profile-case", choices=["far-small", "far-multi-small", "precond-small", "dense-short",
+                                               "dense-small"],
                     help="instead of the benchmark: run one small case for profiler captures "
                          "(far-small: far-field applies on a 2562-vertex sphere, plain then "
-                         "large-ka; precond-small: five OSRC preconditioner applies on it; "
+                         "large-ka; far-multi-small: the same with 8 right-hand sides per apply; "
+                         "precond-small: five OSRC preconditioner applies on it; "
                          "dense-short: ellipsoid8000, 128 right-hand sides, one "
                          "refinement of 120 inner iterations; dense-small: the same on a "
                          "3000-vertex ellipsoid, 24 inner iterations)")
@@ -387,6 +400,8 @@ def run_ours(args, D):
     single = D.world == 1
     if single:
         out["small_dense"] = run_small_dense(D.local)
+    if args.multi_rhs and single:
+        out["multi_rhs"] = run_multi(args.multi_rhs, D.local, value)
     if args.dense_rhs > 0 and single:
         out["dense_batched"] = run_dense(args.dense_rhs, args.dense_matfree_rhs, D.local)
     if not args.no_large and single:
@@ -398,6 +413,76 @@ def run_ours(args, D):
         out["serving_batched"] = run_serving(args.serve_requests, D.local, batched=True)
     out["_solution"] = (xs, bs, r_gpu) if D.rank == 0 else None
     return out, (infos[-1]["iterations"] if infos else REF_ITERATIONS)
+
+
+# --------------------------------------------------------------------------
+# several right-hand sides, matrix-free: GMRES in lockstep, one far-field
+# launch per iteration for up to 8 right-hand sides
+# --------------------------------------------------------------------------
+def run_multi(spec, device, single_value):
+    import numpy as np
+    import torch
+
+    from paper_2104_04609_gb300 import binding as B
+    from paper_2104_04609_gb300.inputs import plane_wave_dirs, workload
+
+    dev = torch.device("cuda", device)
+    W = workload(WORKLOAD)
+    S = B.Solver(W["verts"], W["tris"], W["k_ext"], W["k_int"], W["rho_ratio"], device=device)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    res = []
+    try:
+        for R in [int(v) for v in str(spec).split(",") if v.strip()]:
+            dirs = np.vstack([[0.0, 0.0, 1.0], plane_wave_dirs(R - 1, seed=21)]) if R > 1 else \
+                np.array([[0.0, 0.0, 1.0]])
+            b = S.rhs_planewave(dirs)
+            S.solve(b, tol=TOL, maxit=1000)                      # warm-up (workspaces)
+            B.osrc_profile_enable(S.pb, True)
+            l0 = S.launches()
+            flush.zero_()
+            clk = ClockSampler([0])
+            clk.start()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x, info = S.solve(b, tol=TOL, maxit=1000)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            c = clk.stop()
+            ms = e0.elapsed_time(e1)
+            n_l, far_ms = B.osrc_far_kernel_stats(S.pb)
+            n_rhs = B.osrc_far_kernel_rhs(S.pb)
+            B.osrc_profile_enable(S.pb, False)
+            pairs = B.osrc_far_pairs(S.pb)
+            flops = (FLOPS_PER_PAIR_MULTI_SHARED * n_l + FLOPS_PER_PAIR_MULTI_RHS * n_rhs) * pairs
+            achieved = flops / (far_ms * 1e-3) / 1e12
+            peak = 152 * 128 * 2 * (c.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+            # the same right-hand sides one at a time would take R / single_value s
+            res.append({
+                "right_hand_sides": R, "solves_per_s": R / (ms * 1e-3), "solve_ms": ms,
+                "speedup_vs_one_at_a_time": (R / (ms * 1e-3)) / single_value,
+                "iterations_sum": info.total_iterations, "iterations_last": info.iterations,
+                "precond_residual_last": info.precond_residual,
+                "true_residual_last": info.true_residual, "converged": bool(info.converged),
+                "gpu_launches": int(S.launches() - l0),
+                "far_kernel": {"launches": n_l, "rhs_processed": n_rhs, "total_ms": far_ms,
+                               "share_of_solve": far_ms / ms,
+                               "ms_per_rhs_apply": far_ms / max(n_rhs, 1),
+                               "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                               "frac": achieved / peak, "bound": "alu",
+                               "flops_per_unit": f"{FLOPS_PER_PAIR_MULTI_SHARED} per launch + "
+                                                 f"{FLOPS_PER_PAIR_MULTI_RHS} per right-hand side",
+                               "units_per_launch": pairs},
+                "clocks": c,
+            })
+            del x, b
+    finally:
+        S.close()
+    return {"workload": "sphere10242 (the headline mesh and physics), R plane waves: +z and seeded "
+                        "directions", "path": "GMRES in lockstep over the right-hand sides; far field "
+                        "of up to 8 right-hand sides per launch sharing each point pair's geometry "
+                        "and sine / cosine", "tol": TOL, "l2": "flushed before the timed solve",
+            "runs": res}
 
 
 # --------------------------------------------------------------------------
@@ -1150,6 +1235,18 @@ def profile_case(name, device=0):
         for k0, k1 in ((20.0, 26.0), (40.0, 100.0)):
             S = B.Solver(v, t, k0, k1, 1.5, device=device)
             x = S.rhs_planewave([[0.0, 0.0, 1.0]])
+            for _ in range(3):
+                S.apply(x)
+            torch.cuda.synchronize()
+            S.close()
+        return
+    if name == "far-multi-small":
+        # several-right-hand-side far field on icosphere(4): three applies of 8
+        # right-hand sides at k 20 / 26 (plain), then three at k 40 / 100 (centred)
+        v, t = icosphere(4)
+        for k0, k1 in ((20.0, 26.0), (40.0, 100.0)):
+            S = B.Solver(v, t, k0, k1, 1.5, device=device)
+            x = S.rhs_planewave(plane_wave_dirs(8, seed=3))
             for _ in range(3):
                 S.apply(x)
             torch.cuda.synchronize()

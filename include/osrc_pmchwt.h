@@ -462,6 +462,9 @@ int osrc_profile_enable(osrc_problem *pb, int on);
  * launches and their summed device time in ms (events recorded on the
  * launching stream around each launch).  Waits for the last timed launch. */
 int osrc_far_kernel_stats(osrc_problem *pb, long long *launches, double *total_ms);
+/* Right-hand sides processed by the timed far-field launches (a launch of the
+ * several-right-hand-side kernel counts each of its vectors). */
+long long osrc_far_kernel_rhs(const osrc_problem *pb);
 /* Number of far-field point pairs one apply evaluates: 36 x (number of
  * triangle pairs sharing no vertex). */
 long long osrc_far_pairs(const osrc_problem *pb);

@@ -177,6 +177,7 @@ SIGNATURES = {
     "osrc_near_pairs": (ctypes.c_longlong, [_VP]),
     "osrc_near_nnz": (ctypes.c_longlong, [_VP]),
     "osrc_fp32_peak": (ctypes.c_int, [ctypes.c_int, _DP, _DP, _VP]),
+    "osrc_far_kernel_rhs": (ctypes.c_longlong, [_VP]),
 }
 
 _LIB = None
@@ -605,6 +606,10 @@ def osrc_far_kernel_stats(pb):
     _check(lib().osrc_far_kernel_stats(pb, ctypes.byref(n), ctypes.byref(ms)),
            "osrc_far_kernel_stats")
     return n.value, ms.value
+
+
+def osrc_far_kernel_rhs(pb):
+    return lib().osrc_far_kernel_rhs(pb)
 
 
 def osrc_far_pairs(pb):

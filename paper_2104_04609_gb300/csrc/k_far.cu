@@ -580,6 +580,365 @@ __global__ void gather_kernel(int nv, int npts, int nsplit, const int *__restric
     y[nv + v] = y2;
 }
 
+// ---------------------------------------------------------------------------
+// Multi-right-hand-side far field: one launch applies B_far to R vectors.
+// Everything that depends only on the point pair (distance, 1/r, the four
+// sine / cosine values, the kernel combinations) is computed once and shared
+// by the R right-hand sides; only the accumulations scale with R.  To keep
+// per-right-hand-side state small, the per-source-triangle factors of the
+// K and D-normal terms ((x - y).n_y and n_x.n_y) are folded into the pair's
+// kernel values, so each right-hand side has just the two complex sums
+//   u1 = sum [ (G0 + rho G1) psi_q + (x - y).n_y (H0 + H1) phi_q ]
+//   u2 = sum [ (H0 + H1)(x - y).n_x psi_q - (n_x.n_y)(k0^2 G0 + k1^2/rho G1) phi_q ]
+// per test point, kept in registers over the whole source range.  The D
+// curl term A = sum_s (sum_q w_q (G0 + G1/rho)) c_s needs only
+// W(tau, s) = sum_p w_p sum_q w_q (G0 + G1/rho), which does not depend on the
+// right-hand side: each thread's share of it goes to shared memory per
+// source triangle, and after each tile the three threads of a test triangle
+// contract it with the right-hand sides' curl sources c_s (each thread a
+// third of the right-hand sides).
+//
+// Block: FARM_THREADS = 192 threads = 64 test triangles, thread j holds test
+// points 2 (j mod 3), 2 (j mod 3) + 1 of triangle j / 3 packed in FP32x2
+// lanes.  Source data (per point, duplicated pairs for the packed lanes):
+//   sG [6nt][2]   (-y.x, -y.x, -y.y, -y.y), (-y.z, -y.z, w_q, w_q)   (static)
+//   sD [nt][6][R][2]  (psi.re, psi.re, psi.im, psi.im), (phi.re, ..., phi.im)
+//   sCm [nt][R][3]    c_s components (complex)
+// Outputs (no atomics; gridDim.y splits the source range):
+//   part  [ns][R][4][npts]  u1 (re, im), u2 (re, im) per test point
+//   partA [ns][R][6][nt]    sum_p w_p A(x_p) per test triangle (x, y, z; re, im)
+// ---------------------------------------------------------------------------
+constexpr int FARM_THREADS = 192;
+constexpr int FARM_TRIS = FARM_THREADS / 3;  // test triangles per block
+constexpr int FARM_TS = 16;                  // source triangles per shared-memory tile
+constexpr int FARM_MAX_R = 8;
+
+struct VecPtrs {
+    const double2 *p[FARM_MAX_R];
+};
+struct OutPtrs {
+    double2 *p[FARM_MAX_R];
+};
+
+size_t farm_smem_bytes(int R, bool centred) {
+    size_t b = 0;
+    b += (size_t)FARM_TS * 6 * 2 * sizeof(float4);         // sG
+    b += (size_t)FARM_TS * 6 * R * 2 * sizeof(float4);     // sD
+    b += (size_t)FARM_TS * R * 3 * sizeof(float2);         // sCm
+    b += (size_t)FARM_TS * sizeof(float4);                 // normals
+    b += (size_t)FARM_TS * sizeof(int4);                   // vertex ids
+    b += (size_t)(centred ? 2 * FARM_TS : 0) * sizeof(float4);
+    b += (size_t)FARM_TS * FARM_THREADS * sizeof(float2);  // W shares
+    return b;
+}
+
+// static source geometry of the multi kernel: coordinates (absolute, or
+// offsets from the triangle centroid for the centred variant) negated and
+// duplicated, and the rule weight w_q
+__global__ void farm_geom_kernel(const float4 *__restrict__ pts, int npts, float4 *__restrict__ sG) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npts) return;
+    const float4 p = pts[k];
+    const int q = k % 6;
+    const float w = (float)(q < 3 ? kQw1 : kQw2);
+    sG[2 * (size_t)k] = make_float4(-p.x, -p.x, -p.y, -p.y);
+    sG[2 * (size_t)k + 1] = make_float4(-p.z, -p.z, w, w);
+}
+
+// densities of R right-hand sides at the source rule points and the curl
+// sources c_s, one thread per (source triangle, right-hand side)
+__global__ void farm_prep_kernel(VecPtrs x, int R, int nv, int nt, const int *__restrict__ tris,
+                                 const double *__restrict__ tgeo, float4 *__restrict__ sD,
+                                 float2 *__restrict__ sCm) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (t >= nt || r >= R) return;
+    const double2 *xr = x.p[r];
+    double2 ps[3], ph[3];
+    for (int a = 0; a < 3; ++a) {
+        const int v = tris[3 * t + a];
+        ps[a] = xr[v];
+        ph[a] = xr[nv + v];
+    }
+    const double *g = tgeo + 16 * (size_t)t;
+    const double area = g[0];
+    for (int q = 0; q < 6; ++q) {
+        double b[3], w;
+        rule_point(q, b, w);
+        const double W = w * area;
+        double2 sv = cd(0, 0), fv = cd(0, 0);
+        for (int a = 0; a < 3; ++a) {
+            sv = cadd(sv, cscale(ps[a], b[a]));
+            fv = cadd(fv, cscale(ph[a], b[a]));
+        }
+        const float psr = (float)(W * sv.x), psi = (float)(W * sv.y);
+        const float phr = (float)(W * fv.x), phi = (float)(W * fv.y);
+        float4 *d = sD + 2 * ((6 * (size_t)t + q) * R + r);
+        d[0] = make_float4(psr, psr, psi, psi);
+        d[1] = make_float4(phr, phr, phi, phi);
+    }
+    for (int j = 0; j < 3; ++j) {
+        double2 cv = cd(0, 0);
+        for (int a = 0; a < 3; ++a) cv = cadd(cv, cscale(ph[a], g[4 + 3 * a + j]));
+        sCm[3 * ((size_t)t * R + r) + j] = make_float2((float)(cv.x * area), (float)(cv.y * area));
+    }
+}
+
+// One source point against the thread's two test points, R right-hand sides.
+template <int R, bool CENTRED>
+__device__ __forceinline__ void farm_pair(f2 X, f2 Y, f2 Z, const float4 G0, const float4 G1,
+                                          const float4 *__restrict__ D, f2 mnx, f2 mny, f2 mnz, f2 xnyn,
+                                          f2 nn, const FarConst2 &c, const CenterPair &cp, f2 &t3r,
+                                          f2 &t3i, f2 (&u1r)[R], f2 (&u1i)[R], f2 (&u2r)[R],
+                                          f2 (&u2i)[R]) {
+    f2 dx, dy, dz, ddx, ddy, ddz;
+    if (CENTRED) {
+        ddx = add2(X, lo2(G0));
+        ddy = add2(Y, hi2(G0));
+        ddz = add2(Z, lo2(G1));
+        dx = add2(ddx, cp.Dx);
+        dy = add2(ddy, cp.Dy);
+        dz = add2(ddz, cp.Dz);
+    } else {
+        dx = add2(X, lo2(G0));
+        dy = add2(Y, hi2(G0));
+        dz = add2(Z, lo2(G1));
+    }
+    f2 r2 = mul2(dx, dx);
+    r2 = fma2(dy, dy, r2);
+    r2 = fma2(dz, dz, r2);
+    const f2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const f2 r = mul2(r2, ri);
+    const f2 ri2 = mul2(ri, ri);
+    f2 dnxn = mul2(dx, mnx);  // (y - x).n_x
+    dnxn = fma2(dy, mny, dnxn);
+    dnxn = fma2(dz, mnz, dnxn);
+    f2 s0, c0, s1, c1;
+    if (CENTRED) {
+        f2 num = mul2(ddx, ddx);
+        num = fma2(ddy, ddy, num);
+        num = fma2(ddz, ddz, num);
+        f2 dd = mul2(ddx, cp.Dx);
+        dd = fma2(ddy, cp.Dy, dd);
+        dd = fma2(ddz, cp.Dz, dd);
+        num = fma2(dd, dup2(2.f), num);
+        const f2 den = add2(r, cp.rc);
+        const f2 dlt = mul2(num, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+        const f2 ph0 = fma2(c.k0, dlt, cp.b0);
+        const f2 ph1 = fma2(c.k1, dlt, cp.b1);
+        __sincosf(ph0.x, &s0.x, &c0.x);
+        __sincosf(ph0.y, &s0.y, &c0.y);
+        __sincosf(ph1.x, &s1.x, &c1.x);
+        __sincosf(ph1.y, &s1.y, &c1.y);
+    } else {
+        const f2 kr0 = mul2(r, c.k0), kr1 = mul2(r, c.k1);
+        __sincosf(kr0.x, &s0.x, &c0.x);
+        __sincosf(kr0.y, &s0.y, &c0.y);
+        __sincosf(kr1.x, &s1.x, &c1.x);
+        __sincosf(kr1.y, &s1.y, &c1.y);
+    }
+    const f2 c0r = mul2(c0, ri), s0r = mul2(s0, ri), c1r = mul2(c1, ri), s1r = mul2(s1, ri);
+    // V: G0 + rho G1
+    const f2 gpr = fma2(c.rho, c1r, c0r), gpi = fma2(c.rho, s1r, s0r);
+    // D normal: (-n_x.n_y) dks (G0 + dk1 G1), nn = -n_x.n_y dks
+    const f2 gkr = mul2(nn, fma2(c.dk1, c1r, c0r)), gki = mul2(nn, fma2(c.dk1, s1r, s0r));
+    // D curl weight: sum_q w_q (G0 + G1/rho)
+    const f2 wq = hi2(G1);
+    t3r = fma2(fma2(c.irho, c1r, c0r), wq, t3r);
+    t3i = fma2(fma2(c.irho, s1r, s0r), wq, t3i);
+    // -(H0 + H1) with the scaled c, s (see far_pair2)
+    const f2 hp = mul2(fma2(c.k1, s1, fma2(c.k0, s0, add2(c0r, c1r))), ri2);
+    const f2 hq = mul2(fma2(c.nk1, c1, fma2(c.nk0, c0, add2(s0r, s1r))), ri2);
+    // K: (x - y).n_y (H0 + H1) = (-(x - y).n_y)(-(H0 + H1));  T: (H0 + H1)(x - y).n_x
+    const f2 kr = mul2(xnyn, hp), ki = mul2(xnyn, hq);
+    const f2 tr = mul2(dnxn, hp), ti = mul2(dnxn, hq);
+    const f2 m1 = dup2(-1.f);
+    const f2 ngpi = mul2(gpi, m1), nki = mul2(ki, m1), nti = mul2(ti, m1), ngki = mul2(gki, m1);
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+        const float4 Ps = D[2 * rr], Ph = D[2 * rr + 1];
+        const f2 psr = lo2(Ps), psi = hi2(Ps), phr = lo2(Ph), phi = hi2(Ph);
+        u1r[rr] = fma2(gpr, psr, fma2(ngpi, psi, fma2(kr, phr, fma2(nki, phi, u1r[rr]))));
+        u1i[rr] = fma2(gpr, psi, fma2(gpi, psr, fma2(kr, phi, fma2(ki, phr, u1i[rr]))));
+        u2r[rr] = fma2(tr, psr, fma2(nti, psi, fma2(gkr, phr, fma2(ngki, phi, u2r[rr]))));
+        u2i[rr] = fma2(tr, psi, fma2(ti, psr, fma2(gkr, phi, fma2(gki, phr, u2i[rr]))));
+    }
+}
+
+template <int R, bool CENTRED>
+__global__ void __launch_bounds__(FARM_THREADS, 2)
+farm_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen, const float4 *__restrict__ tn,
+            const int4 *__restrict__ tv, const float4 *__restrict__ sG, const float4 *__restrict__ sD,
+            const float2 *__restrict__ sCm, int nt, int npts, int tris_per_split, FarConst2 c,
+            float4 kff, float *__restrict__ part, float *__restrict__ partA) {
+    extern __shared__ float4 farm_smem[];
+    float4 *shG = farm_smem;                                   // [TS*6][2]
+    float4 *shD = shG + FARM_TS * 6 * 2;                       // [TS*6][R][2]
+    float2 *shC = reinterpret_cast<float2 *>(shD + FARM_TS * 6 * R * 2);  // [TS][R][3]
+    float4 *shN = reinterpret_cast<float4 *>(shC + FARM_TS * R * 3);      // [TS]
+    int4 *shV = reinterpret_cast<int4 *>(shN + FARM_TS);                  // [TS]
+    float4 *shCen = reinterpret_cast<float4 *>(shV + FARM_TS);            // [2 TS] (centred)
+    float2 *shW = reinterpret_cast<float2 *>(shCen + (CENTRED ? 2 * FARM_TS : 0));  // [TS][threads]
+
+    const int j = threadIdx.x;
+    const int lt = j / 3, sub = j - 3 * (j / 3);
+    const int tau_raw = blockIdx.x * FARM_TRIS + lt;
+    const bool active = tau_raw < nt;
+    const int tau = active ? tau_raw : 0;
+    const int p0 = 6 * tau + 2 * sub;
+    const int split = blockIdx.y;
+    const int s_begin = split * tris_per_split;
+    const int s_end = min(nt, s_begin + tris_per_split);
+    const float4 xa = pt[p0], xb = pt[p0 + 1];
+    const f2 X = make_float2(xa.x, xb.x), Y = make_float2(xa.y, xb.y), Z = make_float2(xa.z, xb.z);
+    const float4 n4 = tn[tau];
+    const int4 vt = tv[tau];
+    const f2 mnx = dup2(-n4.x), mny = dup2(-n4.y), mnz = dup2(-n4.z);
+    const float wa = (float)(2 * sub < 3 ? kQw1 : kQw2), wb = (float)(2 * sub + 1 < 3 ? kQw1 : kQw2);
+    float4 cth = make_float4(0.f, 0.f, 0.f, 0.f), ctl = cth;
+    if (CENTRED) {
+        cth = cen[2 * tau];
+        ctl = cen[2 * tau + 1];
+    }
+    f2 u1r[R], u1i[R], u2r[R], u2i[R];
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) u1r[rr] = u1i[rr] = u2r[rr] = u2i[rr] = make_float2(0.f, 0.f);
+
+    for (int t0 = s_begin; t0 < s_end; t0 += FARM_TS) {
+        const int cnt = min(FARM_TS, s_end - t0);
+        __syncthreads();
+        for (int i = j; i < cnt * 12; i += FARM_THREADS) shG[i] = sG[12 * (size_t)t0 + i];
+        for (int i = j; i < cnt * 12 * R; i += FARM_THREADS) shD[i] = sD[12 * (size_t)R * t0 + i];
+        for (int i = j; i < cnt * 3 * R; i += FARM_THREADS) shC[i] = sCm[3 * (size_t)R * t0 + i];
+        for (int i = j; i < cnt; i += FARM_THREADS) {
+            const float4 ns = tn[t0 + i];
+            shN[i] = make_float4(-ns.x, -ns.y, -ns.z, ns.w);
+            shV[i] = tv[t0 + i];
+        }
+        if (CENTRED)
+            for (int i = j; i < 2 * cnt; i += FARM_THREADS) shCen[i] = cen[2 * (size_t)t0 + i];
+        __syncthreads();
+
+        for (int s = 0; s < cnt; ++s) {
+            const int4 vs = shV[s];
+            const bool touch = (vs.x == vt.x) | (vs.x == vt.y) | (vs.x == vt.z) |
+                               (vs.y == vt.x) | (vs.y == vt.y) | (vs.y == vt.z) |
+                               (vs.z == vt.x) | (vs.z == vt.y) | (vs.z == vt.z);
+            if (touch) {
+                shW[s * FARM_THREADS + j] = make_float2(0.f, 0.f);
+                continue;
+            }
+            const float4 mns = shN[s];
+            CenterPair cp;
+            f2 xnyn;
+            if (CENTRED) {
+                cp = center_pair(cth, ctl, shCen[2 * s], shCen[2 * s + 1], kff.x, kff.y, kff.z, kff.w);
+                const float dn = cp.Dx.x * mns.x + cp.Dy.x * mns.y + cp.Dz.x * mns.z;
+                xnyn = fma2(Z, dup2(mns.z), fma2(Y, dup2(mns.y), fma2(X, dup2(mns.x), dup2(dn))));
+            } else {
+                xnyn = fma2(Z, dup2(mns.z), fma2(Y, dup2(mns.y), fma2(X, dup2(mns.x), dup2(mns.w))));
+            }
+            const f2 nn = dup2((n4.x * mns.x + n4.y * mns.y + n4.z * mns.z) * c.dk0.x);
+            f2 t3r = make_float2(0.f, 0.f), t3i = t3r;
+#pragma unroll 2
+            for (int q = 0; q < 6; ++q)
+                farm_pair<R, CENTRED>(X, Y, Z, shG[12 * s + 2 * q], shG[12 * s + 2 * q + 1],
+                                      &shD[2 * R * (6 * s + q)], mnx, mny, mnz, xnyn, nn, c, cp, t3r,
+                                      t3i, u1r, u1i, u2r, u2i);
+            shW[s * FARM_THREADS + j] = make_float2(wa * t3r.x + wb * t3r.y, wa * t3i.x + wb * t3i.y);
+        }
+        __syncthreads();
+        // curl term of this tile: thread (lt, sub) takes right-hand sides sub, sub + 3, ...
+        if (active) {
+            for (int rr = sub; rr < R; rr += 3) {
+                float ar[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int s = 0; s < cnt; ++s) {
+                    const float2 *w3 = shW + s * FARM_THREADS + 3 * lt;
+                    const float wr = w3[0].x + w3[1].x + w3[2].x, wi = w3[0].y + w3[1].y + w3[2].y;
+                    const float2 *cc = shC + 3 * (s * R + rr);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const float2 cv = cc[d];
+                        ar[2 * d] += wr * cv.x - wi * cv.y;
+                        ar[2 * d + 1] += wr * cv.y + wi * cv.x;
+                    }
+                }
+                float *pa = partA + (((size_t)split * R + rr) * 6) * nt + tau;
+#pragma unroll
+                for (int d = 0; d < 6; ++d) pa[(size_t)d * nt] = t0 == s_begin ? ar[d] : pa[(size_t)d * nt] + ar[d];
+            }
+        }
+    }
+    if (active) {
+        f2 *pp = reinterpret_cast<f2 *>(part);
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) {
+            const size_t base = (((size_t)split * R + rr) * 4) * npts + p0;
+            pp[base / 2] = u1r[rr];
+            pp[(base + (size_t)npts) / 2] = u1i[rr];
+            pp[(base + 2 * (size_t)npts) / 2] = u2r[rr];
+            pp[(base + 3 * (size_t)npts) / 2] = u2i[rr];
+        }
+        if (s_begin >= s_end)  // empty split: zero curl sums
+            for (int rr = sub; rr < R; rr += 3)
+                for (int d = 0; d < 6; ++d) partA[(((size_t)split * R + rr) * 6 + d) * nt + tau] = 0.f;
+    }
+}
+
+// Per (vertex, right-hand side): the far-field partial sums gathered with the
+// test weights, plus the near-field CSR product (as gather_kernel).
+__global__ void farm_gather_kernel(int nv, int nt, int npts, int nsplit, int R, const int *__restrict__ vt_ptr,
+                                   const int *__restrict__ vt_idx, const double *__restrict__ tgeo,
+                                   const float *__restrict__ part, const float *__restrict__ partA,
+                                   int use_far, const int *__restrict__ nr_ptr, const int *__restrict__ nr_col,
+                                   const double2 *__restrict__ nr_val, int use_near, VecPtrs x, OutPtrs y) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const int rr = blockIdx.y;
+    if (v >= nv || rr >= R) return;
+    double2 y1 = cd(0, 0), y2 = cd(0, 0);
+    if (use_far) {
+        for (int e = vt_ptr[v]; e < vt_ptr[v + 1]; ++e) {
+            const int t = vt_idx[e] / 3, a = vt_idx[e] % 3;
+            const double *g = tgeo + 16 * (size_t)t;
+            double2 s1 = cd(0, 0), s2 = cd(0, 0), ax = cd(0, 0), ay = cd(0, 0), az = cd(0, 0);
+            for (int sp = 0; sp < nsplit; ++sp) {
+                const float *P = part + (((size_t)sp * R + rr) * 4) * npts;
+                for (int q = 0; q < 6; ++q) {
+                    double b[3], w;
+                    rule_point(q, b, w);
+                    const double wl = w * b[a];
+                    const size_t p = 6 * (size_t)t + q;
+                    s1 = cadd(s1, cd(wl * P[p], wl * P[p + (size_t)npts]));
+                    s2 = cadd(s2, cd(wl * P[p + 2 * (size_t)npts], wl * P[p + 3 * (size_t)npts]));
+                }
+                const float *PA = partA + (((size_t)sp * R + rr) * 6) * nt + t;
+                ax = cadd(ax, cd(PA[0], PA[(size_t)nt]));
+                ay = cadd(ay, cd(PA[2 * (size_t)nt], PA[3 * (size_t)nt]));
+                az = cadd(az, cd(PA[4 * (size_t)nt], PA[5 * (size_t)nt]));
+            }
+            const double *cu = g + 4 + 3 * a;
+            s2 = cadd(s2, cadd(cadd(cscale(ax, cu[0]), cscale(ay, cu[1])), cscale(az, cu[2])));
+            y1 = cadd(y1, cscale(s1, g[0]));
+            y2 = cadd(y2, cscale(s2, g[0]));
+        }
+        const double inv4pi = 0.079577471545947667884;
+        y1 = cscale(y1, inv4pi);
+        y2 = cscale(y2, inv4pi);
+    }
+    if (use_near) {
+        const double2 *xr = x.p[rr];
+        for (int e = nr_ptr[v]; e < nr_ptr[v + 1]; ++e) {
+            const int jc = nr_col[e];
+            const double2 xa = xr[jc], xb = xr[nv + jc];
+            const double2 *Bk = nr_val + 4 * (size_t)e;
+            y1 = cadd(y1, cadd(cmul(Bk[0], xa), cmul(Bk[1], xb)));
+            y2 = cadd(y2, cadd(cmul(Bk[2], xa), cmul(Bk[3], xb)));
+        }
+    }
+    y.p[rr][v] = y1;
+    y.p[rr][nv + v] = y2;
+}
+
 }  // namespace
 
 int far_setup_geometry(osrc_problem *pb, cudaStream_t st) {
@@ -644,6 +1003,8 @@ int far_prof_collect(osrc_problem *pb) {
     OSRC_CK(cudaEventElapsedTime(&ms, pb->prof_ev[0], pb->prof_ev[1]));
     pb->prof_ms += ms;
     pb->prof_launches++;
+    pb->prof_rhs += pb->prof_rhs_pending;
+    pb->prof_rhs_pending = 1;
     pb->prof_pending = false;
     return OSRC_OK;
 }
@@ -708,5 +1069,159 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
         pb->d_nr_ptr.p, pb->d_nr_col.p, pb->d_nr_val.p, use_near, x, y);
     pb->launches++;
     OSRC_CK(cudaGetLastError());
+    return OSRC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// multi-right-hand-side apply: y_r = B_far x_r (+ near) for r < nrhs, in
+// launches of up to FARM_MAX_R right-hand sides (chunks of 8, then 4, 2;
+// a last single vector takes the one-right-hand-side kernel)
+// ---------------------------------------------------------------------------
+template <int R, bool C>
+static int farm_setup_kernel_attr(size_t smem) {
+    OSRC_CK(cudaFuncSetAttribute(farm_kernel<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return OSRC_OK;
+}
+
+static PerDeviceOnce g_farm_once;
+
+static int farm_prepare(osrc_problem *pb, int rmax, cudaStream_t st) {
+    OSRC_TRY(per_device_once(g_farm_once, [](int) {
+        int s = OSRC_OK;
+        if (!s) s = farm_setup_kernel_attr<2, false>(farm_smem_bytes(2, false));
+        if (!s) s = farm_setup_kernel_attr<4, false>(farm_smem_bytes(4, false));
+        if (!s) s = farm_setup_kernel_attr<8, false>(farm_smem_bytes(8, false));
+        if (!s) s = farm_setup_kernel_attr<2, true>(farm_smem_bytes(2, true));
+        if (!s) s = farm_setup_kernel_attr<4, true>(farm_smem_bytes(4, true));
+        if (!s) s = farm_setup_kernel_attr<8, true>(farm_smem_bytes(8, true));
+        return s;
+    }));
+    osrc_ctx *ctx = pb->mesh->ctx;
+    const int nt = pb->nt, npts = pb->npts;
+    if (!pb->d_sG.p) {
+        OSRC_TRY(pb->d_sG.alloc(ctx, 2 * (size_t)npts));
+        const float4 *pts = pb->far_reduce ? pb->d_poff.p : pb->d_pt.p;
+        farm_geom_kernel<<<(npts + 127) / 128, 128, 0, st>>>(pts, npts, pb->d_sG.p);
+        pb->launches++;
+        OSRC_CK(cudaGetLastError());
+    }
+    if (pb->farm_cap < rmax) {
+        int dev = ctx->device, sms = 0, per_sm = 0;
+        OSRC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const size_t sm8 = farm_smem_bytes(8, pb->far_reduce);
+        if (pb->far_reduce)
+            OSRC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, farm_kernel<8, true>, FARM_THREADS, sm8));
+        else
+            OSRC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, farm_kernel<8, false>, FARM_THREADS, sm8));
+        if (per_sm < 1) per_sm = 1;
+        const int bx = (nt + FARM_TRIS - 1) / FARM_TRIS;
+        int ns = (4 * sms * per_sm + bx - 1) / bx;
+        const int max_ns = (nt + FARM_TS - 1) / FARM_TS;
+        if (ns > max_ns) ns = max_ns;
+        if (ns < 1) ns = 1;
+        pb->farm_ns = ns;
+        pb->d_sD.release();
+        pb->d_sCm.release();
+        pb->d_partm.release();
+        pb->d_partA.release();
+        OSRC_TRY(pb->d_sD.alloc(ctx, 12 * (size_t)nt * FARM_MAX_R));
+        OSRC_TRY(pb->d_sCm.alloc(ctx, 3 * (size_t)nt * FARM_MAX_R));
+        OSRC_TRY(pb->d_partm.alloc(ctx, (size_t)ns * FARM_MAX_R * 4 * npts));
+        OSRC_TRY(pb->d_partA.alloc(ctx, (size_t)ns * FARM_MAX_R * 6 * nt));
+        pb->farm_cap = FARM_MAX_R;
+    }
+    return OSRC_OK;
+}
+
+static int farm_launch(osrc_problem *pb, const double2 *const *xs, double2 *const *ys, int R, int part,
+                       cudaStream_t st) {
+    osrc_mesh *m = pb->mesh;
+    const int nt = pb->nt, nv = pb->nv, npts = pb->npts;
+    const int use_far = (part & OSRC_PART_FAR) ? 1 : 0;
+    const int use_near = (part & OSRC_PART_NEAR) ? 1 : 0;
+    VecPtrs xp{};
+    OutPtrs yp{};
+    for (int r = 0; r < R; ++r) {
+        xp.p[r] = xs[r];
+        yp.p[r] = ys[r];
+    }
+    const int ns = pb->farm_ns;
+    if (use_far) {
+        farm_prep_kernel<<<dim3((nt + 127) / 128, R), 128, 0, st>>>(xp, R, nv, nt, m->d_tris.p, pb->d_tgeo.p,
+                                                                   pb->d_sD.p, pb->d_sCm.p);
+        pb->launches++;
+        const double k0 = pb->p.k_ext, k1 = pb->p.k_int, rho = pb->p.rho_ratio;
+        const double inv2pi = 0.15915494309189533577;
+        auto d2 = [](double v) { return make_float2((float)v, (float)v); };
+        FarConst2 c;
+        c.k0 = d2(k0);
+        c.k1 = d2(k1);
+        c.nk0 = d2(-k0);
+        c.nk1 = d2(-k1);
+        c.rho = d2(rho);
+        c.irho = d2(1.0 / rho);
+        c.dk0 = d2(pb->far_dks);
+        c.dk1 = d2(k1 * k1 / rho / pb->far_dks);
+        const double q0 = k0 * inv2pi, q1 = k1 * inv2pi;
+        const float q0h = (float)q0, q1h = (float)q1;
+        const float4 kff = make_float4(q0h, (float)(q0 - (double)q0h), q1h, (float)(q1 - (double)q1h));
+        const int tps = (nt + ns - 1) / ns;
+        dim3 grid((nt + FARM_TRIS - 1) / FARM_TRIS, ns);
+        const float4 *pts = pb->far_reduce ? pb->d_poff.p : pb->d_pt.p;
+        const size_t smem = farm_smem_bytes(R, pb->far_reduce);
+        if (pb->prof_on) {
+            OSRC_TRY(far_prof_collect(pb));
+            OSRC_CK(cudaEventRecord(pb->prof_ev[0], st));
+        }
+#define OSRC_FARM_LAUNCH(RR, C)                                                                          \
+    farm_kernel<RR, C><<<grid, FARM_THREADS, smem, st>>>(pts, pb->d_cen.p, pb->d_tn.p, pb->d_tv.p, pb->d_sG.p, \
+                                                         pb->d_sD.p, pb->d_sCm.p, nt, npts, tps, c, kff,    \
+                                                         pb->d_partm.p, pb->d_partA.p)
+        if (pb->far_reduce) {
+            if (R == 8) OSRC_FARM_LAUNCH(8, true);
+            else if (R == 4) OSRC_FARM_LAUNCH(4, true);
+            else OSRC_FARM_LAUNCH(2, true);
+        } else {
+            if (R == 8) OSRC_FARM_LAUNCH(8, false);
+            else if (R == 4) OSRC_FARM_LAUNCH(4, false);
+            else OSRC_FARM_LAUNCH(2, false);
+        }
+#undef OSRC_FARM_LAUNCH
+        pb->launches++;
+        OSRC_CK(cudaGetLastError());
+        if (pb->prof_on) {
+            OSRC_CK(cudaEventRecord(pb->prof_ev[1], st));
+            pb->prof_pending = true;
+            pb->prof_rhs_pending = R;
+        }
+    }
+    farm_gather_kernel<<<dim3((nv + 127) / 128, R), 128, 0, st>>>(
+        nv, nt, npts, ns, R, m->d_vt_ptr.p, m->d_vt_idx.p, pb->d_tgeo.p, pb->d_partm.p, pb->d_partA.p, use_far,
+        pb->d_nr_ptr.p, pb->d_nr_col.p, pb->d_nr_val.p, use_near, xp, yp);
+    pb->launches++;
+    OSRC_CK(cudaGetLastError());
+    return OSRC_OK;
+}
+
+bool far_multi_supported(const osrc_problem *pb) {
+    return pb->p.precision == OSRC_FP32_MATFREE && !pb->far_obj;
+}
+
+int far_apply_multi(osrc_problem *pb, const double2 *const *xs, double2 *const *ys, int nrhs, int part,
+                    cudaStream_t st) {
+    if (nrhs < 1) return OSRC_INVALID_ARG;
+    if (nrhs == 1 || !far_multi_supported(pb) || !(part & OSRC_PART_FAR)) {
+        for (int r = 0; r < nrhs; ++r) OSRC_TRY(far_apply(pb, xs[r], ys[r], part, st));
+        return OSRC_OK;
+    }
+    OSRC_TRY(farm_prepare(pb, FARM_MAX_R, st));
+    int r0 = 0;
+    while (r0 < nrhs) {
+        const int left = nrhs - r0;
+        const int R = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        if (R == 1) OSRC_TRY(far_apply(pb, xs[r0], ys[r0], part, st));
+        else OSRC_TRY(farm_launch(pb, xs + r0, ys + r0, R, part, st));
+        r0 += R;
+    }
     return OSRC_OK;
 }

@@ -589,6 +589,7 @@ extern "C" int osrc_profile_enable(osrc_problem *pb, int on) {
     pb->prof_on = on != 0;
     pb->prof_launches = 0;
     pb->prof_ms = 0.0;
+    pb->prof_rhs = 0;
     return OSRC_OK;
 }
 
@@ -600,6 +601,8 @@ extern "C" int osrc_far_kernel_stats(osrc_problem *pb, long long *launches, doub
     *total_ms = pb->prof_ms;
     return OSRC_OK;
 }
+
+extern "C" long long osrc_far_kernel_rhs(const osrc_problem *pb) { return pb ? pb->prof_rhs : 0; }
 
 extern "C" long long osrc_far_pairs(const osrc_problem *pb) {
     return pb ? 36LL * ((long long)pb->nt * pb->nt - pb->near_pairs) : 0;
@@ -654,6 +657,16 @@ extern "C" int osrc_pmchwt_apply(osrc_problem *pb, const void *x, void *y, int n
     if (x == y) return OSRC_INVALID_ARG;
     OSRC_CK(cudaSetDevice(pb->mesh->ctx->device));
     const size_t n = 2 * (size_t)pb->nv;
+    if (nrhs > 1 && form == OSRC_WEAK && far_multi_supported(pb)) {
+        // several right-hand sides per far-field launch
+        std::vector<const double2 *> xs(nrhs);
+        std::vector<double2 *> ys(nrhs);
+        for (int r = 0; r < nrhs; ++r) {
+            xs[r] = (const double2 *)x + n * r;
+            ys[r] = (double2 *)y + n * r;
+        }
+        return far_apply_multi(pb, xs.data(), ys.data(), nrhs, part, (cudaStream_t)stream);
+    }
     for (int r = 0; r < nrhs; ++r)
         OSRC_TRY(apply_one(pb, (const double2 *)x + n * r, (double2 *)y + n * r, form, part,
                            (cudaStream_t)stream));
@@ -729,17 +742,27 @@ static int end_step(GmresRun &g) {
     return OSRC_OK;
 }
 
-// one Arnoldi step: w = P M^-1 B v_j, CGS2 against v_0..v_j, Givens, |g_{j+1}|/beta
-static int enqueue_iteration(GmresRun &g) {
+// one Arnoldi step: w = P M^-1 B v_j, CGS2 against v_0..v_j, Givens, |g_{j+1}|/beta.
+// Split in two so that a batch of runs can share one several-right-hand-side
+// apply: enqueue_apply (B v_j into d_tmp2) and enqueue_iteration_rest.
+static int enqueue_apply(GmresRun &g) {
+    osrc_problem *pb = g.pb;
+    cudaStream_t st = g.st;
+    const int n = 2 * pb->nv, j = g.j;
+    double2 *V = pb->d_basis.p;
+    OSRC_CK(cudaEventRecord(g.tev[0], st));
+    if (pb->p.precision == OSRC_FP64_DENSE) OSRC_TRY(dense_apply(pb, V + (size_t)j * n, pb->d_tmp2.p, st));
+    else OSRC_TRY(far_apply(pb, V + (size_t)j * n, pb->d_tmp2.p, OSRC_PART_ALL, st));
+    OSRC_CK(cudaEventRecord(g.tev[1], st));
+    return OSRC_OK;
+}
+
+static int enqueue_iteration_rest(GmresRun &g) {
     osrc_problem *pb = g.pb;
     cudaStream_t st = g.st;
     const int n = 2 * pb->nv, j = g.j, ldh = g.maxit + 1;
     double2 *V = pb->d_basis.p, *H = pb->d_h.p, *gv = pb->d_givens.p, *w = pb->d_w.p;
     double *sc = pb->d_scalars.p;
-    OSRC_CK(cudaEventRecord(g.tev[0], st));
-    if (pb->p.precision == OSRC_FP64_DENSE) OSRC_TRY(dense_apply(pb, V + (size_t)j * n, pb->d_tmp2.p, st));
-    else OSRC_TRY(far_apply(pb, V + (size_t)j * n, pb->d_tmp2.p, OSRC_PART_ALL, st));
-    OSRC_CK(cudaEventRecord(g.tev[1], st));
     OSRC_TRY(osrc_precond_fused_async(pb, pb->d_tmp2.p, w, st));
     OSRC_CK(cudaEventRecord(g.tev[2], st));
     double2 *hc = H + (size_t)ldh * j;
@@ -759,26 +782,62 @@ static int enqueue_iteration(GmresRun &g) {
     return end_step(g);
 }
 
-// x = V y, then the true weak residual |b - B x| / |b|
-static int enqueue_finish(GmresRun &g) {
+static int enqueue_iteration(GmresRun &g) {
+    OSRC_TRY(enqueue_apply(g));
+    return enqueue_iteration_rest(g);
+}
+
+// x = V y, then the true weak residual |b - B x| / |b|; split like the
+// iteration: enqueue_finish_x (x = V y), the apply B x into d_w,
+// enqueue_finish_rest
+static int enqueue_finish_x(GmresRun &g) {
+    osrc_problem *pb = g.pb;
+    const int n = 2 * pb->nv;
+    if (g.j > 0) {
+        OSRC_TRY(gmres_finish(pb, g.j, g.maxit + 1, pb->d_h.p, pb->d_givens.p, pb->d_basis.p, g.x, n, g.st));
+    } else {
+        OSRC_CK(cudaMemsetAsync(g.x, 0, n * sizeof(double2), g.st));
+    }
+    return OSRC_OK;
+}
+
+static int enqueue_finish_rest(GmresRun &g) {
     osrc_problem *pb = g.pb;
     cudaStream_t st = g.st;
     const int n = 2 * pb->nv;
     double *sc = pb->d_scalars.p;
-    if (g.j > 0) {
-        OSRC_TRY(gmres_finish(pb, g.j, g.maxit + 1, pb->d_h.p, pb->d_givens.p, pb->d_basis.p, g.x, n, st));
-    } else {
-        OSRC_CK(cudaMemsetAsync(g.x, 0, n * sizeof(double2), st));
-    }
     double2 *t = pb->d_w.p;
-    if (pb->p.precision == OSRC_FP64_DENSE) OSRC_TRY(dense_apply(pb, g.x, t, st));
-    else OSRC_TRY(far_apply(pb, g.x, t, OSRC_PART_ALL, st));
     OSRC_TRY(vec_axpby(pb, cd(1, 0), g.b, cd(-1, 0), t, t, n, st));
     OSRC_TRY(vec_norm(pb, t, n, sc + 4, st));
     OSRC_TRY(vec_norm(pb, g.b, n, sc + 5, st));
     OSRC_CK(cudaMemcpyAsync(pb->h_res + 4, sc + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     OSRC_CK(cudaEventRecord(g.ev, st));
     return OSRC_OK;
+}
+
+static int enqueue_finish(GmresRun &g) {
+    osrc_problem *pb = g.pb;
+    OSRC_TRY(enqueue_finish_x(g));
+    if (pb->p.precision == OSRC_FP64_DENSE) OSRC_TRY(dense_apply(pb, g.x, pb->d_w.p, g.st));
+    else OSRC_TRY(far_apply(pb, g.x, pb->d_w.p, OSRC_PART_ALL, g.st));
+    return enqueue_finish_rest(g);
+}
+
+// next step of a deferred run: the batch driver enqueues it (GmresRun::defer)
+static int schedule_iteration(GmresRun &g) {
+    if (g.defer) {
+        g.next = 1;
+        return OSRC_OK;
+    }
+    return enqueue_iteration(g);
+}
+
+static int schedule_finish(GmresRun &g) {
+    if (g.defer) {
+        g.next = 2;
+        return OSRC_OK;
+    }
+    return enqueue_finish(g);
 }
 
 int GmresRun::start(osrc_problem *p, cudaStream_t s, const double2 *b_, double2 *x_, double tol_,
@@ -838,7 +897,7 @@ int GmresRun::advance() {
         if (!(beta > 0.0)) {  // zero right-hand side: x = 0
             converged = true;
             res = 0.0;
-            OSRC_TRY(enqueue_finish(*this));
+            OSRC_TRY(schedule_finish(*this));
             phase = 3;
             return OSRC_OK;
         }
@@ -849,7 +908,7 @@ int GmresRun::advance() {
         pb->h_res[6] = beta;  // g_0 = (beta, 0), copied from pinned memory
         pb->h_res[7] = 0.0;
         OSRC_CK(cudaMemcpyAsync(gv + 2 * ldh, pb->h_res + 6, sizeof(double2), cudaMemcpyHostToDevice, st));
-        OSRC_TRY(enqueue_iteration(*this));
+        OSRC_TRY(schedule_iteration(*this));
         phase = 2;
         return OSRC_OK;
     }
@@ -872,11 +931,11 @@ int GmresRun::advance() {
     }
     if (res <= tol) converged = true;
     if (converged || j >= maxit) {
-        OSRC_TRY(enqueue_finish(*this));
+        OSRC_TRY(schedule_finish(*this));
         phase = 3;
         return OSRC_OK;
     }
-    OSRC_TRY(enqueue_iteration(*this));
+    OSRC_TRY(schedule_iteration(*this));
     return OSRC_OK;
 }
 
@@ -976,6 +1035,153 @@ size_t estimate_work_bytes(int nv, int nt, const osrc_params &p, int maxit) {
     return b;
 }
 
+// ---------------------------------------------------------------------------
+// GMRES for several right-hand sides in lockstep: one run per right-hand
+// side, each on a clone of the problem (own Krylov basis, Hessenberg matrix,
+// inner-solver workspace; shared resident operator state), all on one
+// stream.  Every iteration applies B to the newest basis vectors of all
+// runs that are still iterating in one several-right-hand-side far-field
+// launch (far_apply_multi), then each run does its own preconditioner,
+// Gram-Schmidt and Givens steps.  Runs stop independently (a converged run
+// drops out of the shared apply).  Up to kBatchRuns runs are in flight; more
+// right-hand sides are taken in groups.
+// ---------------------------------------------------------------------------
+static const int kBatchRuns = 16;
+
+struct CloneSet {
+    std::vector<osrc_problem *> c;
+    ~CloneSet() {
+        for (osrc_problem *p : c) osrc_problem_destroy(p);
+    }
+};
+
+static int gmres_solve_lockstep(osrc_problem *pb, const void *b, void *x, int nrhs, double tol, int maxit,
+                                bool host, osrc_solve_info &info, cudaStream_t st) {
+    const int n = 2 * pb->nv;
+    const int G = std::min(nrhs, kBatchRuns);
+    CloneSet cs;
+    cs.c.assign(G, nullptr);
+    for (int g = 0; g < G; ++g) OSRC_TRY(problem_clone(pb, &cs.c[g]));
+    DBuf<double2> db, dx;
+    if (host) {
+        OSRC_TRY(db.alloc(pb->mesh->ctx, (size_t)G * n));
+        OSRC_TRY(dx.alloc(pb->mesh->ctx, (size_t)G * n));
+    }
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    OSRC_CK(cudaEventCreate(&ea));
+    OSRC_CK(cudaEventCreate(&eb));
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } evg{ea, eb};
+    double ms_apply = 0.0;
+    bool apply_pending = false;
+    int last_its = 0;
+    double last_pres = 0.0, last_tres = 0.0;
+    for (int r0 = 0; r0 < nrhs; r0 += G) {
+        const int R = std::min(G, nrhs - r0);
+        std::vector<GmresRun> runs(R);
+        for (int r = 0; r < R; ++r) {
+            const double2 *br;
+            double2 *xr;
+            if (host) {
+                OSRC_CK(cudaMemcpyAsync(db.p + (size_t)r * n, (const double2 *)b + (size_t)n * (r0 + r),
+                                        n * sizeof(double2), cudaMemcpyHostToDevice, st));
+                br = db.p + (size_t)r * n;
+                xr = dx.p + (size_t)r * n;
+            } else {
+                br = (const double2 *)b + (size_t)n * (r0 + r);
+                xr = (double2 *)x + (size_t)n * (r0 + r);
+            }
+            cs.c[r]->inner_last_max = 0;
+            runs[r].defer = true;
+            OSRC_TRY(runs[r].start(cs.c[r], st, br, xr, tol, maxit));
+        }
+        std::vector<const double2 *> xs;
+        std::vector<double2 *> ys;
+        std::vector<int> it, fin;
+        for (;;) {
+            OSRC_CK(cudaStreamSynchronize(st));
+            if (apply_pending) {
+                float ms = 0.f;
+                OSRC_CK(cudaEventElapsedTime(&ms, ea, eb));
+                ms_apply += ms;
+                apply_pending = false;
+            }
+            it.clear();
+            fin.clear();
+            for (int r = 0; r < R; ++r) {
+                GmresRun &g = runs[r];
+                if (g.done()) continue;
+                g.next = 0;
+                const int s = g.advance();
+                if (s != OSRC_OK) return s;
+                if (g.done()) continue;
+                if (g.next == 1) it.push_back(r);
+                else if (g.next == 2) fin.push_back(r);
+            }
+            if (it.empty() && fin.empty()) break;
+            if (!it.empty()) {
+                xs.clear();
+                ys.clear();
+                for (int r : it) {
+                    osrc_problem *c = cs.c[r];
+                    xs.push_back(c->d_basis.p + (size_t)runs[r].j * n);
+                    ys.push_back(c->d_tmp2.p);
+                }
+                OSRC_CK(cudaEventRecord(ea, st));
+                OSRC_TRY(far_apply_multi(pb, xs.data(), ys.data(), (int)it.size(), OSRC_PART_ALL, st));
+                OSRC_CK(cudaEventRecord(eb, st));
+                apply_pending = true;
+                for (int r : it) {
+                    // the shared apply's time is counted once by the driver
+                    OSRC_CK(cudaEventRecord(runs[r].tev[0], st));
+                    OSRC_CK(cudaEventRecord(runs[r].tev[1], st));
+                    OSRC_TRY(enqueue_iteration_rest(runs[r]));
+                }
+            }
+            if (!fin.empty()) {
+                xs.clear();
+                ys.clear();
+                for (int r : fin) {
+                    OSRC_TRY(enqueue_finish_x(runs[r]));
+                    xs.push_back(runs[r].x);
+                    ys.push_back(cs.c[r]->d_w.p);
+                }
+                OSRC_TRY(far_apply_multi(pb, xs.data(), ys.data(), (int)fin.size(), OSRC_PART_ALL, st));
+                for (int r : fin) OSRC_TRY(enqueue_finish_rest(runs[r]));
+            }
+        }
+        for (int r = 0; r < R; ++r) {
+            const GmresRun &g = runs[r];
+            if (host)
+                OSRC_CK(cudaMemcpyAsync((double2 *)x + (size_t)n * (r0 + r), dx.p + (size_t)r * n,
+                                        n * sizeof(double2), cudaMemcpyDeviceToHost, st));
+            last_its = g.info.iterations;
+            last_pres = g.info.precond_residual;
+            last_tres = g.info.true_residual;
+            info.ms_precond += g.info.ms_precond;
+            info.ms_arnoldi += g.info.ms_arnoldi;
+            info.total_iterations += g.info.iterations;
+            info.inner_iterations_max = std::max(info.inner_iterations_max, cs.c[r]->inner_last_max);
+            if (!g.converged) info.converged = 0;
+        }
+    }
+    for (osrc_problem *c : cs.c) {  // the clones' launches count as the problem's
+        pb->launches += c->launches;
+        c->launches = 0;
+    }
+    OSRC_CK(cudaStreamSynchronize(st));
+    info.iterations = last_its;
+    info.precond_residual = last_pres;
+    info.true_residual = last_tres;
+    info.ms_matvec += ms_apply;
+    return OSRC_OK;
+}
+
 extern "C" int osrc_gmres_solve(osrc_problem *pb, const void *b, void *x, int nrhs, double tol, int maxit,
                                 int flags, osrc_solve_info *info_out, void *stream) {
     if (!pb || !b || !x || nrhs < 1 || !(tol > 0.0) || maxit < 1 || maxit > 100000) return OSRC_INVALID_ARG;
@@ -988,6 +1194,12 @@ extern "C" int osrc_gmres_solve(osrc_problem *pb, const void *b, void *x, int nr
     info.converged = 1;
     pb->inner_last_max = 0;
     const bool host = (flags & OSRC_HOST_BUFFERS) != 0;
+    if (nrhs > 1 && far_multi_supported(pb) && pb->p.precond != OSRC_PRECOND_CALDERON) {
+        OSRC_TRY(gmres_solve_lockstep(pb, b, x, nrhs, tol, maxit, host, info, st));
+        info.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (info_out) *info_out = info;
+        return info.converged ? OSRC_OK : OSRC_NOT_CONVERGED;
+    }
     GmresRun run;
     for (int r = 0; r < nrhs; ++r) {
         const double2 *br;

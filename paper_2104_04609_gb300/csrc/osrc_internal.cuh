@@ -188,6 +188,13 @@ struct osrc_problem {
     DBuf<float4> d_sC;   // [nt][5] c_sigma components with both signs, duplicated pairs
     DBuf<float> d_part;       // [nsplit][6nt][10] per test point partial sums
     int nsplit = 1;
+    // ---- far field, several right-hand sides per launch (k_far.cu farm_*) ----
+    DBuf<float4> d_sG;        // [6nt][2] static source geometry (coordinates, rule weight)
+    DBuf<float4> d_sD;        // [nt][6][R][2] densities of R right-hand sides
+    DBuf<float2> d_sCm;       // [nt][R][3] curl sources
+    DBuf<float> d_partm;      // [ns][R][4][6nt] u1, u2 partial sums
+    DBuf<float> d_partA;      // [ns][R][6][nt] curl-term partial sums per test triangle
+    int farm_ns = 1, farm_cap = 0;
     bool far_reduce = false;  // centred far kernel with float-float phases (large k r)
     // ---- FP64 per-triangle geometry: area, normal, curls of the hat functions
     DBuf<double> d_tgeo;      // [nt][16]
@@ -243,6 +250,8 @@ struct osrc_problem {
     DBuf<int> d_fobeg;        // [objects + 1] source-point ranges of the objects
     // ---- far-kernel event timing -------------------------------------------------
     bool prof_on = false, prof_pending = false;
+    int prof_rhs_pending = 1;    // right-hand sides of the last timed far launch
+    long long prof_rhs = 0;      // right-hand sides summed over the timed launches
     cudaEvent_t prof_ev[2] = {nullptr, nullptr};
     long long prof_launches = 0;
     double prof_ms = 0.0;
@@ -256,6 +265,11 @@ int far_prof_collect(osrc_problem *pb);
 // far field (k_far.cu)
 int far_setup_geometry(osrc_problem *pb, cudaStream_t st);
 int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStream_t st);
+// y_r = B x_r for nrhs vectors (far part of several right-hand sides per launch
+// where the problem allows it: one object, PMCHWT, lossless interior)
+int far_apply_multi(osrc_problem *pb, const double2 *const *xs, double2 *const *ys, int nrhs, int part,
+                    cudaStream_t st);
+bool far_multi_supported(const osrc_problem *pb);
 
 // near field (k_near.cu)
 int near_build(osrc_problem *pb, const std::vector<NearPair> &pairs,
@@ -319,6 +333,11 @@ struct GmresRun {
     cudaEvent_t ev = nullptr;
     cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
     osrc_solve_info info{};
+    // deferred mode (batches of runs sharing one several-right-hand-side
+    // apply): advance() only records the next step, 1 iteration or 2 finish,
+    // and the batch driver enqueues it
+    bool defer = false;
+    int next = 0;
     int start(osrc_problem *p, cudaStream_t s, const double2 *b_, double2 *x_, double tol_, int maxit_);
     bool ready() const;   // the work enqueued last has finished
     int advance();        // consumes the finished step and enqueues the next

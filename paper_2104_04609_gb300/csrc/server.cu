@@ -1,8 +1,11 @@
 // server.cu -- continuous-batching serving loop for OSRC-PMCHWT solve
 // requests (resident state kept across requests, admission by device memory).
 //
-// A worker thread owns the GPU work.  Each request (mesh, parameters, one or
-// more right-hand sides) is split into one GMRES job per right-hand side.
+// A worker thread owns the GPU work.  A request with one right-hand side is
+// one GMRES job; a request with several is one block job (same-mesh
+// right-hand sides batched): matrix-free requests run GMRES in lockstep over
+// their right-hand sides with one several-right-hand-side far-field launch
+// per iteration, FP64-dense requests the batched mixed-precision solve.
 // Jobs are admitted into a fixed number of slots as slots free up and as the
 // context's device-memory budget allows; each slot has its own CUDA stream
 // and its own workspace (a clone of a resident problem), so the kernels of
@@ -89,6 +92,7 @@ struct Slot {
     bool bdone = false;
     int bstatus = OSRC_OK;
     osrc_solve_info binfo{};
+    bool lockstep = false;  // the block is a matrix-free lockstep GMRES, not the dense batched solve
 };
 
 constexpr int ADMIT_WAIT = -1;  // the head of the queue must wait (its problem is busy)
@@ -139,6 +143,7 @@ struct osrc_server {
     int admit_one(Slot &slot);
     int start_batched(Slot &slot, Request *r);
     void batched_body(Slot &slot, Request *r, CacheEntry *entry);
+    void lockstep_body(Slot &slot, Request *r, CacheEntry *entry);
     void finish_batched(Slot &slot);
     int acquire_entry(Request *r, CacheEntry **out, cudaStream_t st);
     void release_slot_workspace(Slot &slot);
@@ -219,6 +224,7 @@ int osrc_server::admit_one(Slot &slot) {
         r = pending.front();
     }
     if (r->params.precision == OSRC_FP64_DENSE) return start_batched(slot, r);
+    if (r->nrhs > 1 && r->params.precond != OSRC_PRECOND_CALDERON) return start_batched(slot, r);
     // workspace: reuse the slot's clone if it serves the same problem
     CacheEntry *entry = nullptr;
     if (slot.entry && slot.entry_key == r->key) {
@@ -287,10 +293,18 @@ int osrc_server::start_batched(Slot &slot, Request *r) {
     int s = acquire_entry(r, &entry, slot.st);
     if (s != OSRC_OK) return s;
     entry->refs++;
+    const bool lockstep = r->params.precision != OSRC_FP64_DENSE;
     const int blk = std::min(r->nrhs, BATCH_MAX);
-    const size_t need = estimate_batched_bytes(r->nv, r->params.n_pade, blk, BATCH_INNER_MAXIT) +
-                        (size_t)blk * 2 * r->nv * 32;
-    const size_t have = entry->pb->batched ? 0 : need;  // state of an earlier block is reused
+    size_t need, have;
+    if (lockstep) {  // one GMRES workspace per right-hand side in flight, and the block's vectors
+        need = (size_t)std::min(r->nrhs, 16) * estimate_work_bytes(r->nv, r->nt, r->params, r->maxit) +
+               (size_t)r->nrhs * 2 * r->nv * 32;
+        have = need;
+    } else {
+        need = estimate_batched_bytes(r->nv, r->params.n_pade, blk, BATCH_INNER_MAXIT) +
+               (size_t)blk * 2 * r->nv * 32;
+        have = entry->pb->batched ? 0 : need;  // state of an earlier block is reused
+    }
     while (ctx->budget && ctx->used + have > ctx->budget)
         if (!evict_one()) {
             entry->refs--;
@@ -311,8 +325,39 @@ int osrc_server::start_batched(Slot &slot, Request *r) {
     slot.batched = true;
     slot.bentry = entry;
     slot.bdone = false;
-    slot.bth = std::thread([this, &slot, r, entry] { batched_body(slot, r, entry); });
+    slot.lockstep = lockstep;
+    if (lockstep) slot.bth = std::thread([this, &slot, r, entry] { lockstep_body(slot, r, entry); });
+    else slot.bth = std::thread([this, &slot, r, entry] { batched_body(slot, r, entry); });
     return OSRC_OK;
+}
+
+// The GPU work of a matrix-free request with several right-hand sides: GMRES
+// advanced in lockstep over all of them (osrc_gmres_solve), sharing one
+// far-field launch per iteration for the right-hand sides still iterating.
+// Runs on its own host thread with the slot's stream, like a batched job.
+void osrc_server::lockstep_body(Slot &slot, Request *r, CacheEntry *entry) {
+    cudaSetDevice(ctx->device);
+    const int n2 = 2 * r->nv;
+    int status = OSRC_OK, s;
+    osrc_solve_info info{};
+    if ((s = slot.d_b.alloc(ctx, (size_t)r->nrhs * n2)) || (s = slot.d_x.alloc(ctx, (size_t)r->nrhs * n2)))
+        status = s;
+    for (int i = 0; i < r->nrhs && status == OSRC_OK; ++i)
+        status = rhs_build(entry->pb, r->kind, r->src.data() + 3 * (size_t)i, slot.d_b.p + (size_t)i * n2, slot.st);
+    if (status == OSRC_OK) {
+        const int gs = osrc_gmres_solve(entry->pb, slot.d_b.p, slot.d_x.p, r->nrhs, r->tol, r->maxit, 0, &info,
+                                        slot.st);
+        if (gs != OSRC_OK && gs != OSRC_NOT_CONVERGED) status = gs;
+        if (status == OSRC_OK &&
+            (cudaMemcpyAsync(r->x.data(), slot.d_x.p, (size_t)r->nrhs * n2 * sizeof(double2),
+                             cudaMemcpyDeviceToHost, slot.st) != cudaSuccess ||
+             cudaStreamSynchronize(slot.st) != cudaSuccess))
+            status = OSRC_CUDA_ERROR;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    slot.bstatus = status;
+    slot.binfo = info;
+    slot.bdone = true;
 }
 
 // The GPU work of a batched job (its own host thread; touches only the job's
@@ -377,8 +422,11 @@ void osrc_server::finish_batched(Slot &slot) {
         r->info.iterations = agg.iterations;
         r->info.total_iterations = agg.total_iterations;
         r->info.true_residual = agg.true_residual;
-        r->info.precond_residual = agg.true_residual;
+        r->info.precond_residual = slot.lockstep ? agg.precond_residual : agg.true_residual;
         r->info.converged = agg.converged;
+        r->info.ms_matvec = agg.ms_matvec;
+        r->info.ms_precond = agg.ms_precond;
+        r->info.ms_arnoldi = agg.ms_arnoldi;
         if (status == OSRC_OK && !agg.converged) status = OSRC_NOT_CONVERGED;
         r->status = status;
         r->rhs_done = r->nrhs;
@@ -393,6 +441,7 @@ void osrc_server::finish_batched(Slot &slot) {
     slot.req = nullptr;
     slot.bentry = nullptr;
     slot.batched = false;
+    slot.lockstep = false;
     slot.bdone = false;
     slot.busy = false;
 }

@@ -64,6 +64,8 @@ def test_server_alone_equals_mix_and_direct(B):
     assert np.array_equal(mixed[3][0], xa)
     assert stats["cache_hits"] >= 1              # the repeated request reused resident state
     assert stats["active_peak"] >= 2             # jobs overlapped
+    # requests with several right-hand sides ran as one lockstep block each
+    assert stats["batched_jobs"] == 3
     # the synchronous entry point on its own problem gives the same solution
     S = B.Solver(va, ta, 2.0, 3.0, 1.5)
     try:
