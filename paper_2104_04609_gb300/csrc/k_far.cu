@@ -23,6 +23,8 @@
 // and so is n_x.n_y; the surface curl of the P1 density is constant per
 // triangle.  These per-triangle factors are applied once per (test point,
 // source triangle), not per point pair.
+#include <algorithm>
+
 #include "osrc_internal.cuh"
 
 namespace {
@@ -41,6 +43,11 @@ __host__ __device__ inline void rule_point(int q, double bary[3], double &w) {
 }
 
 constexpr int FAR_THREADS = 128;
+// resident blocks per SM the one-right-hand-side kernel is compiled for
+// (registers per thread = 65536 / (FAR_THREADS x FAR_MIN_BLOCKS))
+#ifndef OSRC_FAR_MIN_BLOCKS
+#define OSRC_FAR_MIN_BLOCKS 4
+#endif
 // largest k_max x (bounding-box diagonal) for the plain (FP32 k r) variant
 constexpr double FAR_PLAIN_MAX_PHASE = 32.0 * 3.14159265358979323846;
 constexpr int FAR_TS = 64;  // source triangles per shared-memory tile
@@ -395,7 +402,7 @@ __device__ __forceinline__ void far_pair2(f2 X, f2 Y, f2 Z, const float4 *P, con
 // sources on other objects and change sign for Mueller.  ABSORB (with MULTI):
 // complex interior wavenumbers (attenuation).
 template <bool CENTRED, bool MULTI, bool ABSORB>
-__global__ void __launch_bounds__(FAR_THREADS, 4)
+__global__ void __launch_bounds__(FAR_THREADS, OSRC_FAR_MIN_BLOCKS)
 far_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen,
            const float4 *__restrict__ tn, const int4 *__restrict__ tv,
            const float4 *__restrict__ sP, const float2 *__restrict__ sP5,
@@ -598,7 +605,7 @@ __global__ void gather_kernel(int nv, int npts, int nsplit, const int *__restric
 // contract it with the right-hand sides' curl sources c_s (each thread a
 // third of the right-hand sides).
 //
-// Block: FARM_THREADS = 192 threads = 64 test triangles, thread j holds test
+// Block: FARM_THREADS = 384 threads = 128 test triangles, thread j holds test
 // points 2 (j mod 3), 2 (j mod 3) + 1 of triangle j / 3 packed in FP32x2
 // lanes.  Source data (per point, duplicated pairs for the packed lanes):
 //   sG [6nt][2]   (-y.x, -y.x, -y.y, -y.y), (-y.z, -y.z, w_q, w_q)   (static)
@@ -608,7 +615,17 @@ __global__ void gather_kernel(int nv, int npts, int nsplit, const int *__restric
 //   part  [ns][R][4][npts]  u1 (re, im), u2 (re, im) per test point
 //   partA [ns][R][6][nt]    sum_p w_p A(x_p) per test triangle (x, y, z; re, im)
 // ---------------------------------------------------------------------------
-constexpr int FARM_THREADS = 192;
+// 384 threads = 12 warps, 3 on each of the SM's four schedulers (a block
+// whose warps spread unevenly over the schedulers waits at every tile
+// barrier for its most crowded scheduler); one block per SM at <= 170
+// registers per thread
+#ifndef OSRC_FARM_THREADS
+#define OSRC_FARM_THREADS 384
+#endif
+constexpr int FARM_THREADS = OSRC_FARM_THREADS;
+#ifndef OSRC_FARM_MIN_BLOCKS
+#define OSRC_FARM_MIN_BLOCKS 1
+#endif
 constexpr int FARM_TRIS = FARM_THREADS / 3;  // test triangles per block
 constexpr int FARM_TS = 16;                  // source triangles per shared-memory tile
 constexpr int FARM_MAX_R = 8;
@@ -620,16 +637,50 @@ struct OutPtrs {
     double2 *p[FARM_MAX_R];
 };
 
+// one shared-memory tile buffer: sG, sD, sCm, normals, vertex ids, centroids
+constexpr size_t farm_buf_bytes(int R, bool centred) {
+    return (size_t)FARM_TS * (12 * 16 + 12 * 16 * R + 24 * R + 16 + 16 + (centred ? 32 : 0));
+}
+
 size_t farm_smem_bytes(int R, bool centred) {
-    size_t b = 0;
-    b += (size_t)FARM_TS * 6 * 2 * sizeof(float4);         // sG
-    b += (size_t)FARM_TS * 6 * R * 2 * sizeof(float4);     // sD
-    b += (size_t)FARM_TS * R * 3 * sizeof(float2);         // sCm
-    b += (size_t)FARM_TS * sizeof(float4);                 // normals
-    b += (size_t)FARM_TS * sizeof(int4);                   // vertex ids
-    b += (size_t)(centred ? 2 * FARM_TS : 0) * sizeof(float4);
-    b += (size_t)FARM_TS * FARM_THREADS * sizeof(float2);  // W shares
-    return b;
+    return 2 * farm_buf_bytes(R, centred) + (size_t)FARM_TS * FARM_THREADS * sizeof(float2) + 2 * sizeof(uint64_t);
+}
+
+constexpr unsigned long long FARM_TIMEOUT_NS = 2000000000ULL;
+
+__device__ __forceinline__ uint32_t farm_saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long farm_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// waits for phase `parity` of the mbarrier, at most FARM_TIMEOUT_NS of global time
+__device__ __forceinline__ bool farm_wait(uint64_t *bar, uint32_t parity) {
+    const unsigned long long t0 = farm_ns();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(farm_saddr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (farm_ns() - t0 > FARM_TIMEOUT_NS) return false;
+    }
+}
+
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple
+// of 16), completion counted on the mbarrier
+__device__ __forceinline__ void farm_bulk(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            farm_saddr(dst)),
+        "l"((uint64_t)src), "r"(bytes), "r"(farm_saddr(bar))
+        : "memory");
 }
 
 // static source geometry of the multi kernel: coordinates (absolute, or
@@ -766,19 +817,39 @@ __device__ __forceinline__ void farm_pair(f2 X, f2 Y, f2 Z, const float4 G0, con
 }
 
 template <int R, bool CENTRED>
-__global__ void __launch_bounds__(FARM_THREADS, 2)
+struct FarmBuf {
+    float4 *G;   // [TS*6][2]
+    float4 *D;   // [TS*6][R][2]
+    float2 *C;   // [TS][R][3]
+    float4 *N;   // [TS] normal, plane offset
+    int4 *V;     // [TS] vertex ids
+    float4 *Cen; // [2 TS] (centred)
+    __device__ FarmBuf(unsigned char *base) {
+        G = reinterpret_cast<float4 *>(base);
+        D = G + FARM_TS * 12;
+        C = reinterpret_cast<float2 *>(D + FARM_TS * 12 * R);
+        N = reinterpret_cast<float4 *>(C + FARM_TS * 3 * R);
+        V = reinterpret_cast<int4 *>(N + FARM_TS);
+        Cen = reinterpret_cast<float4 *>(V + FARM_TS);
+    }
+};
+
+// Source tiles are staged by 1-D TMA bulk copies (cp.async.bulk) into a
+// two-buffer shared-memory ring: thread 0 issues tile k + 1 while every
+// thread computes tile k, and an mbarrier per buffer counts the bytes in.
+// Every wait is bounded (FARM_TIMEOUT_NS of global time); a thread that
+// gives up sets *err, stops waiting, and writes NaN instead of its sums, and
+// thread 0 waits (bounded) for the copies it issued before the block exits.
+template <int R, bool CENTRED>
+__global__ void __launch_bounds__(FARM_THREADS, OSRC_FARM_MIN_BLOCKS)
 farm_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen, const float4 *__restrict__ tn,
             const int4 *__restrict__ tv, const float4 *__restrict__ sG, const float4 *__restrict__ sD,
             const float2 *__restrict__ sCm, int nt, int npts, int tris_per_split, FarConst2 c,
-            float4 kff, float *__restrict__ part, float *__restrict__ partA) {
-    extern __shared__ float4 farm_smem[];
-    float4 *shG = farm_smem;                                   // [TS*6][2]
-    float4 *shD = shG + FARM_TS * 6 * 2;                       // [TS*6][R][2]
-    float2 *shC = reinterpret_cast<float2 *>(shD + FARM_TS * 6 * R * 2);  // [TS][R][3]
-    float4 *shN = reinterpret_cast<float4 *>(shC + FARM_TS * R * 3);      // [TS]
-    int4 *shV = reinterpret_cast<int4 *>(shN + FARM_TS);                  // [TS]
-    float4 *shCen = reinterpret_cast<float4 *>(shV + FARM_TS);            // [2 TS] (centred)
-    float2 *shW = reinterpret_cast<float2 *>(shCen + (CENTRED ? 2 * FARM_TS : 0));  // [TS][threads]
+            float4 kff, float *__restrict__ part, float *__restrict__ partA, int *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char farm_smem[];
+    constexpr size_t BUF = farm_buf_bytes(R, CENTRED);
+    float2 *shW = reinterpret_cast<float2 *>(farm_smem + 2 * BUF);  // [TS][threads]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(shW + FARM_TS * FARM_THREADS);
 
     const int j = threadIdx.x;
     const int lt = j / 3, sub = j - 3 * (j / 3);
@@ -789,6 +860,7 @@ farm_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen, const
     const int split = blockIdx.y;
     const int s_begin = split * tris_per_split;
     const int s_end = min(nt, s_begin + tris_per_split);
+    const int ntiles = s_end > s_begin ? (s_end - s_begin + FARM_TS - 1) / FARM_TS : 0;
     const float4 xa = pt[p0], xb = pt[p0 + 1];
     const f2 X = make_float2(xa.x, xb.x), Y = make_float2(xa.y, xb.y), Z = make_float2(xa.z, xb.z);
     const float4 n4 = tn[tau];
@@ -804,23 +876,47 @@ farm_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen, const
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) u1r[rr] = u1i[rr] = u2r[rr] = u2i[rr] = make_float2(0.f, 0.f);
 
-    for (int t0 = s_begin; t0 < s_end; t0 += FARM_TS) {
+    // thread 0: the copies of tile k into buffer k & 1
+    auto issue = [&](int k) {
+        const int t0 = s_begin + k * FARM_TS;
         const int cnt = min(FARM_TS, s_end - t0);
-        __syncthreads();
-        for (int i = j; i < cnt * 12; i += FARM_THREADS) shG[i] = sG[12 * (size_t)t0 + i];
-        for (int i = j; i < cnt * 12 * R; i += FARM_THREADS) shD[i] = sD[12 * (size_t)R * t0 + i];
-        for (int i = j; i < cnt * 3 * R; i += FARM_THREADS) shC[i] = sCm[3 * (size_t)R * t0 + i];
-        for (int i = j; i < cnt; i += FARM_THREADS) {
-            const float4 ns = tn[t0 + i];
-            shN[i] = make_float4(-ns.x, -ns.y, -ns.z, ns.w);
-            shV[i] = tv[t0 + i];
-        }
-        if (CENTRED)
-            for (int i = j; i < 2 * cnt; i += FARM_THREADS) shCen[i] = cen[2 * (size_t)t0 + i];
-        __syncthreads();
+        FarmBuf<R, CENTRED> fb(farm_smem + (k & 1) * BUF);
+        uint64_t *mb = &bar[k & 1];
+        const uint32_t bytes = (uint32_t)cnt * (12 * 16 + 12 * 16 * R + 24 * R + 16 + 16 + (CENTRED ? 32 : 0));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(farm_saddr(mb)), "r"(bytes)
+                     : "memory");
+        farm_bulk(fb.G, sG + 12 * (size_t)t0, (uint32_t)cnt * 12 * 16, mb);
+        farm_bulk(fb.D, sD + 12 * (size_t)R * t0, (uint32_t)cnt * 12 * 16 * R, mb);
+        farm_bulk(fb.C, sCm + 3 * (size_t)R * t0, (uint32_t)cnt * 24 * R, mb);
+        farm_bulk(fb.N, tn + t0, (uint32_t)cnt * 16, mb);
+        farm_bulk(fb.V, tv + t0, (uint32_t)cnt * 16, mb);
+        if (CENTRED) farm_bulk(fb.Cen, cen + 2 * (size_t)t0, (uint32_t)cnt * 32, mb);
+    };
+    if (j == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(farm_saddr(&bar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(farm_saddr(&bar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (j == 0 && ntiles > 0) issue(0);
+    bool dead = false;      // a bounded wait gave up
+    int issued = ntiles > 0 ? 1 : 0;  // tiles issued (thread 0)
 
+    for (int k = 0; k < ntiles; ++k) {
+        const int t0 = s_begin + k * FARM_TS;
+        const int cnt = min(FARM_TS, s_end - t0);
+        FarmBuf<R, CENTRED> fb(farm_smem + (k & 1) * BUF);
+        if (!dead && !farm_wait(&bar[k & 1], (uint32_t)(k >> 1) & 1u)) {
+            dead = true;
+            atomicExch(err, 1);
+        }
+        // the other buffer held tile k - 1, released by the barrier that ended it
+        if (j == 0 && !dead && k + 1 < ntiles) {
+            issue(k + 1);
+            issued = k + 2;
+        }
         for (int s = 0; s < cnt; ++s) {
-            const int4 vs = shV[s];
+            const int4 vs = fb.V[s];
             const bool touch = (vs.x == vt.x) | (vs.x == vt.y) | (vs.x == vt.z) |
                                (vs.y == vt.x) | (vs.y == vt.y) | (vs.y == vt.z) |
                                (vs.z == vt.x) | (vs.z == vt.y) | (vs.z == vt.z);
@@ -828,11 +924,12 @@ farm_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen, const
                 shW[s * FARM_THREADS + j] = make_float2(0.f, 0.f);
                 continue;
             }
-            const float4 mns = shN[s];
+            const float4 ns = fb.N[s];
+            const float4 mns = make_float4(-ns.x, -ns.y, -ns.z, ns.w);
             CenterPair cp;
             f2 xnyn;
             if (CENTRED) {
-                cp = center_pair(cth, ctl, shCen[2 * s], shCen[2 * s + 1], kff.x, kff.y, kff.z, kff.w);
+                cp = center_pair(cth, ctl, fb.Cen[2 * s], fb.Cen[2 * s + 1], kff.x, kff.y, kff.z, kff.w);
                 const float dn = cp.Dx.x * mns.x + cp.Dy.x * mns.y + cp.Dz.x * mns.z;
                 xnyn = fma2(Z, dup2(mns.z), fma2(Y, dup2(mns.y), fma2(X, dup2(mns.x), dup2(dn))));
             } else {
@@ -842,8 +939,8 @@ farm_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen, const
             f2 t3r = make_float2(0.f, 0.f), t3i = t3r;
 #pragma unroll 2
             for (int q = 0; q < 6; ++q)
-                farm_pair<R, CENTRED>(X, Y, Z, shG[12 * s + 2 * q], shG[12 * s + 2 * q + 1],
-                                      &shD[2 * R * (6 * s + q)], mnx, mny, mnz, xnyn, nn, c, cp, t3r,
+                farm_pair<R, CENTRED>(X, Y, Z, fb.G[12 * s + 2 * q], fb.G[12 * s + 2 * q + 1],
+                                      &fb.D[2 * R * (6 * s + q)], mnx, mny, mnz, xnyn, nn, c, cp, t3r,
                                       t3i, u1r, u1i, u2r, u2i);
             shW[s * FARM_THREADS + j] = make_float2(wa * t3r.x + wb * t3r.y, wa * t3i.x + wb * t3i.y);
         }
@@ -855,7 +952,7 @@ farm_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen, const
                 for (int s = 0; s < cnt; ++s) {
                     const float2 *w3 = shW + s * FARM_THREADS + 3 * lt;
                     const float wr = w3[0].x + w3[1].x + w3[2].x, wi = w3[0].y + w3[1].y + w3[2].y;
-                    const float2 *cc = shC + 3 * (s * R + rr);
+                    const float2 *cc = fb.C + 3 * (s * R + rr);
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
                         const float2 cv = cc[d];
@@ -865,21 +962,28 @@ farm_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen, const
                 }
                 float *pa = partA + (((size_t)split * R + rr) * 6) * nt + tau;
 #pragma unroll
-                for (int d = 0; d < 6; ++d) pa[(size_t)d * nt] = t0 == s_begin ? ar[d] : pa[(size_t)d * nt] + ar[d];
+                for (int d = 0; d < 6; ++d) pa[(size_t)d * nt] = k == 0 ? ar[d] : pa[(size_t)d * nt] + ar[d];
             }
         }
+        __syncthreads();
+    }
+    if (j == 0 && dead) {  // copies still in flight land before the block exits: the
+                           // last tile issued into each buffer
+        for (int k = max(0, issued - 2); k < issued; ++k)
+            if (!farm_wait(&bar[k & 1], (uint32_t)(k >> 1) & 1u)) break;
     }
     if (active) {
         f2 *pp = reinterpret_cast<f2 *>(part);
+        const f2 nan2 = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
 #pragma unroll
         for (int rr = 0; rr < R; ++rr) {
             const size_t base = (((size_t)split * R + rr) * 4) * npts + p0;
-            pp[base / 2] = u1r[rr];
-            pp[(base + (size_t)npts) / 2] = u1i[rr];
-            pp[(base + 2 * (size_t)npts) / 2] = u2r[rr];
-            pp[(base + 3 * (size_t)npts) / 2] = u2i[rr];
+            pp[base / 2] = dead ? nan2 : u1r[rr];
+            pp[(base + (size_t)npts) / 2] = dead ? nan2 : u1i[rr];
+            pp[(base + 2 * (size_t)npts) / 2] = dead ? nan2 : u2r[rr];
+            pp[(base + 3 * (size_t)npts) / 2] = dead ? nan2 : u2i[rr];
         }
-        if (s_begin >= s_end)  // empty split: zero curl sums
+        if (ntiles == 0)  // empty split: zero curl sums
             for (int rr = sub; rr < R; rr += 3)
                 for (int d = 0; d < 6; ++d) partA[(((size_t)split * R + rr) * 6 + d) * nt + tau] = 0.f;
     }
@@ -1114,11 +1218,23 @@ static int farm_prepare(osrc_problem *pb, int rmax, cudaStream_t st) {
         else
             OSRC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, farm_kernel<8, false>, FARM_THREADS, sm8));
         if (per_sm < 1) per_sm = 1;
+        // source splits: at least four blocks per resident slot, and among
+        // the counts up to twice that, the one whose last wave is fullest
         const int bx = (nt + FARM_TRIS - 1) / FARM_TRIS;
-        int ns = (4 * sms * per_sm + bx - 1) / bx;
-        const int max_ns = (nt + FARM_TS - 1) / FARM_TS;
-        if (ns > max_ns) ns = max_ns;
-        if (ns < 1) ns = 1;
+        const int slots = sms * per_sm;
+        const int max_ns = std::max(1, (nt + 4 * FARM_TS - 1) / (4 * FARM_TS));
+        int ns0 = std::min(max_ns, std::max(1, (4 * slots + bx - 1) / bx));
+        int ns = ns0;
+        double best = -1.0;
+        for (int cand = ns0; cand <= std::min(max_ns, 2 * ns0); ++cand) {
+            const long long blocks = (long long)bx * cand;
+            const long long waves = (blocks + slots - 1) / slots;
+            const double eff = (double)blocks / (double)(waves * slots);
+            if (eff > best + 1e-9) {
+                best = eff;
+                ns = cand;
+            }
+        }
         pb->farm_ns = ns;
         pb->d_sD.release();
         pb->d_sCm.release();
@@ -1128,6 +1244,10 @@ static int farm_prepare(osrc_problem *pb, int rmax, cudaStream_t st) {
         OSRC_TRY(pb->d_sCm.alloc(ctx, 3 * (size_t)nt * FARM_MAX_R));
         OSRC_TRY(pb->d_partm.alloc(ctx, (size_t)ns * FARM_MAX_R * 4 * npts));
         OSRC_TRY(pb->d_partA.alloc(ctx, (size_t)ns * FARM_MAX_R * 6 * nt));
+        if (!pb->d_farm_err.p) {
+            OSRC_TRY(pb->d_farm_err.alloc(ctx, 1));
+            OSRC_CK(cudaMemsetAsync(pb->d_farm_err.p, 0, sizeof(int), st));
+        }
         pb->farm_cap = FARM_MAX_R;
     }
     return OSRC_OK;
@@ -1176,7 +1296,7 @@ static int farm_launch(osrc_problem *pb, const double2 *const *xs, double2 *cons
 #define OSRC_FARM_LAUNCH(RR, C)                                                                          \
     farm_kernel<RR, C><<<grid, FARM_THREADS, smem, st>>>(pts, pb->d_cen.p, pb->d_tn.p, pb->d_tv.p, pb->d_sG.p, \
                                                          pb->d_sD.p, pb->d_sCm.p, nt, npts, tps, c, kff,    \
-                                                         pb->d_partm.p, pb->d_partA.p)
+                                                         pb->d_partm.p, pb->d_partA.p, pb->d_farm_err.p)
         if (pb->far_reduce) {
             if (R == 8) OSRC_FARM_LAUNCH(8, true);
             else if (R == 4) OSRC_FARM_LAUNCH(4, true);
@@ -1200,6 +1320,21 @@ static int farm_launch(osrc_problem *pb, const double2 *const *xs, double2 *cons
         pb->d_nr_ptr.p, pb->d_nr_col.p, pb->d_nr_val.p, use_near, xp, yp);
     pb->launches++;
     OSRC_CK(cudaGetLastError());
+    return OSRC_OK;
+}
+
+// OSRC_TIMEOUT if a several-right-hand-side far kernel gave up a bounded
+// wait since the last check (the flag is cleared); synchronises the stream
+int far_multi_check(osrc_problem *pb, cudaStream_t st) {
+    if (!pb->d_farm_err.p) return OSRC_OK;
+    int h = 0;
+    OSRC_CK(cudaMemcpyAsync(&h, pb->d_farm_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    OSRC_CK(cudaStreamSynchronize(st));
+    if (h) {
+        OSRC_CK(cudaMemsetAsync(pb->d_farm_err.p, 0, sizeof(int), st));
+        osrc_set_error("far kernel: a bounded wait for a staged source tile gave up");
+        return OSRC_TIMEOUT;
+    }
     return OSRC_OK;
 }
 

@@ -1105,6 +1105,7 @@ static int gmres_solve_lockstep(osrc_problem *pb, const void *b, void *x, int nr
         std::vector<int> it, fin;
         for (;;) {
             OSRC_CK(cudaStreamSynchronize(st));
+            OSRC_TRY(far_multi_check(pb, st));
             if (apply_pending) {
                 float ms = 0.f;
                 OSRC_CK(cudaEventElapsedTime(&ms, ea, eb));

@@ -194,6 +194,7 @@ struct osrc_problem {
     DBuf<float2> d_sCm;       // [nt][R][3] curl sources
     DBuf<float> d_partm;      // [ns][R][4][6nt] u1, u2 partial sums
     DBuf<float> d_partA;      // [ns][R][6][nt] curl-term partial sums per test triangle
+    DBuf<int> d_farm_err;     // set when the kernel gave up a bounded wait
     int farm_ns = 1, farm_cap = 0;
     bool far_reduce = false;  // centred far kernel with float-float phases (large k r)
     // ---- FP64 per-triangle geometry: area, normal, curls of the hat functions
@@ -270,6 +271,7 @@ int far_apply(osrc_problem *pb, const double2 *x, double2 *y, int part, cudaStre
 int far_apply_multi(osrc_problem *pb, const double2 *const *xs, double2 *const *ys, int nrhs, int part,
                     cudaStream_t st);
 bool far_multi_supported(const osrc_problem *pb);
+int far_multi_check(osrc_problem *pb, cudaStream_t st);
 
 // near field (k_near.cu)
 int near_build(osrc_problem *pb, const std::vector<NearPair> &pairs,
