@@ -139,6 +139,8 @@ typedef struct osrc_solve_info {
     int inner_iterations_max;  /* largest inner CG/COCG iteration count seen (FP32
                                   iterations over all refinements when refined) */
     int total_iterations;      /* GMRES iterations summed over right-hand sides */
+    double ms_queued;          /* server requests: submit to the start of the request's
+                                  first GPU work, ms (0 for direct calls) */
 } osrc_solve_info;
 
 /* ---- context -------------------------------------------------------------- */

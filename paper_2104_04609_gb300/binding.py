@@ -71,6 +71,7 @@ class osrc_solve_info(ctypes.Structure):
         ("ms_total", ctypes.c_double), ("ms_matvec", ctypes.c_double),
         ("ms_precond", ctypes.c_double), ("ms_arnoldi", ctypes.c_double),
         ("inner_iterations_max", ctypes.c_int), ("total_iterations", ctypes.c_int),
+        ("ms_queued", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -626,6 +626,10 @@ constexpr int FARM_THREADS = OSRC_FARM_THREADS;
 #ifndef OSRC_FARM_MIN_BLOCKS
 #define OSRC_FARM_MIN_BLOCKS 1
 #endif
+#ifndef OSRC_FARM_QUNROLL
+#define OSRC_FARM_QUNROLL 2
+#endif
+constexpr int FARM_QUNROLL = OSRC_FARM_QUNROLL;  // unroll of the rule-point loop
 constexpr int FARM_TRIS = FARM_THREADS / 3;  // test triangles per block
 constexpr int FARM_TS = 16;                  // source triangles per shared-memory tile
 constexpr int FARM_MAX_R = 8;
@@ -937,7 +941,7 @@ farm_kernel(const float4 *__restrict__ pt, const float4 *__restrict__ cen, const
             }
             const f2 nn = dup2((n4.x * mns.x + n4.y * mns.y + n4.z * mns.z) * c.dk0.x);
             f2 t3r = make_float2(0.f, 0.f), t3i = t3r;
-#pragma unroll 2
+#pragma unroll FARM_QUNROLL
             for (int q = 0; q < 6; ++q)
                 farm_pair<R, CENTRED>(X, Y, Z, fb.G[12 * s + 2 * q], fb.G[12 * s + 2 * q + 1],
                                       &fb.D[2 * R * (6 * s + q)], mnx, mny, mnz, xnyn, nn, c, cp, t3r,

@@ -55,7 +55,8 @@ struct Request {
     double tol = 1e-5;
     int maxit = 500;
     std::string key;
-    Clock::time_point t_submit, t_done;
+    Clock::time_point t_submit, t_start, t_done;
+    bool started = false;  // t_start set (first job admitted)
     int next_rhs = 0;
     int rhs_done = 0;
     int inflight = 0;  // jobs of this request running in slots
@@ -263,6 +264,10 @@ int osrc_server::admit_one(Slot &slot) {
         std::lock_guard<std::mutex> lock(mu);
         rhs = r->next_rhs++;
         r->inflight++;
+        if (!r->started) {
+            r->started = true;
+            r->t_start = Clock::now();
+        }
         if (r->next_rhs >= r->nrhs) pending.pop_front();
     }
     slot.req = r;
@@ -315,6 +320,10 @@ int osrc_server::start_batched(Slot &slot, Request *r) {
         r->next_rhs = r->nrhs;
         r->inflight++;
         pending.pop_front();
+        if (!r->started) {
+            r->started = true;
+            r->t_start = Clock::now();
+        }
     }
     entry->last_use = ++tick;
     entry->batched_busy = true;
@@ -434,6 +443,8 @@ void osrc_server::finish_batched(Slot &slot) {
         r->finished = true;
         r->t_done = Clock::now();
         r->info.ms_total = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+        r->info.ms_queued =
+            r->started ? std::chrono::duration<double, std::milli>(r->t_start - r->t_submit).count() : r->info.ms_total;
         stats.completed++;
         if (status != OSRC_OK) stats.failed++;
         cv.notify_all();
@@ -476,6 +487,8 @@ void osrc_server::finish_job(Slot &slot, int status) {
             r->finished = true;
             r->t_done = Clock::now();
             r->info.ms_total = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+            r->info.ms_queued =
+            r->started ? std::chrono::duration<double, std::milli>(r->t_start - r->t_submit).count() : r->info.ms_total;
             stats.completed++;
             if (r->status != OSRC_OK) stats.failed++;
         }
