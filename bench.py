@@ -72,7 +72,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle sample")
-    ap.add_argument("--serve-requests", type=int, default=4,
+    ap.add_argument("--serve-route", default="both", choices=["both", "matrix_free", "hybrid"],
+                    help="serving legs to run")
+    ap.add_argument("--serve-requests", type=int, default=2,
                     help="requests of the seeded Poisson stream in the serving legs, at their stated "
                          "sizes (0: skip; 50 for the full measurement, about 20 minutes)")
     ap.add_argument("--dense-rhs", type=int, default=128,
@@ -412,8 +414,10 @@ def run_ours(args, D):
     if not args.no_objects and single:
         out["four_spheres"] = run_four_spheres(D.local)
     if args.serve_requests > 0 and single:
-        out["serving"] = run_serving(args.serve_requests, D.local)
-        out["serving_batched"] = run_serving(args.serve_requests, D.local, route="hybrid")
+        if args.serve_route in ("both", "matrix_free"):
+            out["serving"] = run_serving(args.serve_requests, D.local)
+        if args.serve_route in ("both", "hybrid"):
+            out["serving_batched"] = run_serving(args.serve_requests, D.local, route="hybrid")
     out["_solution"] = (xs, bs, r_gpu) if D.rank == 0 else None
     return out, (infos[-1]["iterations"] if infos else REF_ITERATIONS)
 

@@ -14,6 +14,9 @@
 // 1/r and 1/r^2 singularities, leaving integrands that tensor Gauss-Legendre
 // rules integrate with exponential convergence.
 #include "ffmath.cuh"
+#include <algorithm>
+#include <vector>
+
 #include "osrc_internal.cuh"
 
 namespace {
@@ -268,6 +271,112 @@ constexpr double kDa1 = 0.445948490915965, kDw1 = 0.223381589678011;
 constexpr double kDa2 = 0.091576213509771, kDw2 = 0.109951743655322;
 constexpr int DA_PAIRS = 16;  // triangle pairs per block (6 threads each)
 
+// Deterministic accumulation of the dense matrix without atomics.  The
+// triangles are coloured so that no two of one colour share a vertex; the
+// unordered far pairs are visited colour pair by colour pair (ca <= cb, one
+// launch each).  Within a launch every matrix entry (row of a vertex of the
+// test triangle, column of a vertex of the source triangle) then has at most
+// one contributing pair, so the kernel adds with plain loads and stores.
+// For ca == cb the pair's reverse orientation (test s, source t) is written
+// in the same launch: an entry gets a forward contribution only from the
+// pair whose first triangle has the smaller index in the colour list and a
+// reverse one only from the other order, never both.  For ca < cb the reverse
+// values go to a stash and a second launch (dense_reverse_kernel) adds them.
+// Every entry therefore receives its contributions in a fixed order and the
+// assembled matrix is the same bit for bit from run to run.
+struct DenseSched {
+    const int *la, *lb;  // triangles of colour ca and cb
+    int na, nb;
+    int diag;            // ca == cb
+    double2 *stash;      // ca < cb: [na * nb][9][4] reverse values
+};
+
+// pair of launch block (bx, by), slot lp: triangles t (from la), s (from lb)
+// and the stash row; false when out of range
+__device__ __forceinline__ bool dense_pair(const DenseSched &sc, int lp, int &t, int &s, long long &row) {
+    if (sc.diag) {  // folded triangular enumeration of i < k within one list
+        const int f = blockIdx.y, n = sc.na;
+        const long long j = (long long)blockIdx.x * DA_PAIRS + lp;
+        int i = -1, k = -1;
+        if (j < n - 1 - f) {
+            i = f;
+            k = f + 1 + (int)j;
+        } else if (n - 1 - f != f && j < n - 1) {
+            i = n - 1 - f;
+            k = i + 1 + (int)(j - (n - 1 - f));
+        }
+        if (i < 0 || k >= n) return false;
+        t = sc.la[i];
+        s = sc.la[k];
+        row = -1;
+        return true;
+    }
+    const int i = blockIdx.y;
+    const int k = blockIdx.x * DA_PAIRS + lp;
+    if (i >= sc.na || k >= sc.nb) return false;
+    t = sc.la[i];
+    s = sc.lb[k];
+    row = (long long)i * sc.nb + k;
+    return true;
+}
+
+// Adds the values of entry (a, b) of pair (t, s) to the four blocks, forward
+// and (same launch, or stashed) reversed; reversed K and T blocks are the
+// negated T and K values.
+__device__ __forceinline__ void dense_emit(const DenseSched &sc, long long row, int e, double2 *__restrict__ A,
+                                           int nv, size_t ra, size_t rb, double2 v, double2 k, double2 tt,
+                                           double2 dd) {
+    const size_t n2 = 2 * (size_t)nv;
+    double2 *q;
+    q = &A[ra * n2 + rb];                q->x += v.x;  q->y += v.y;
+    q = &A[ra * n2 + nv + rb];           q->x += k.x;  q->y += k.y;
+    q = &A[(nv + ra) * n2 + rb];         q->x += tt.x; q->y += tt.y;
+    q = &A[(nv + ra) * n2 + nv + rb];    q->x += dd.x; q->y += dd.y;
+    if (sc.diag) {
+        q = &A[rb * n2 + ra];            q->x += v.x;  q->y += v.y;
+        q = &A[rb * n2 + nv + ra];       q->x -= tt.x; q->y -= tt.y;
+        q = &A[(nv + rb) * n2 + ra];     q->x -= k.x;  q->y -= k.y;
+        q = &A[(nv + rb) * n2 + nv + ra]; q->x += dd.x; q->y += dd.y;
+    } else {
+        double2 *o = sc.stash + (row * 9 + e) * 4;
+        o[0] = v;
+        o[1] = cd(-tt.x, -tt.y);
+        o[2] = cd(-k.x, -k.y);
+        o[3] = dd;
+    }
+}
+
+// zero stash rows of pairs that contribute nothing (touching pairs), so that
+// the reverse launch can add every row
+__device__ __forceinline__ void dense_emit_zero(const DenseSched &sc, long long row, int p) {
+    if (sc.diag) return;
+    for (int e = p; e < 9; e += 6) {
+        double2 *o = sc.stash + (row * 9 + e) * 4;
+        o[0] = o[1] = o[2] = o[3] = cd(0, 0);
+    }
+}
+
+// Reverse orientation of colour pair (ca < cb): entry (vertex b of s, vertex
+// a of t) of the four blocks, one thread per (pair, entry).
+__global__ void dense_reverse_kernel(int nv, const int *__restrict__ tris, DenseSched sc,
+                                     double2 *__restrict__ A) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long npairs = (long long)sc.na * sc.nb;
+    if (g >= npairs * 9) return;
+    const long long row = g / 9;
+    const int e = (int)(g - row * 9);
+    const int i = (int)(row / sc.nb), k = (int)(row - (long long)i * sc.nb);
+    const int t = sc.la[i], s = sc.lb[k];
+    const size_t ra = tris[3 * t + e / 3], rb = tris[3 * s + e % 3];
+    const size_t n2 = 2 * (size_t)nv;
+    const double2 *o = sc.stash + g * 4;
+    double2 *q;
+    q = &A[rb * n2 + ra];                 q->x += o[0].x; q->y += o[0].y;
+    q = &A[rb * n2 + nv + ra];            q->x += o[1].x; q->y += o[1].y;
+    q = &A[(nv + rb) * n2 + ra];          q->x += o[2].x; q->y += o[2].y;
+    q = &A[(nv + rb) * n2 + nv + ra];     q->x += o[3].x; q->y += o[3].y;
+}
+
 __device__ __forceinline__ double dense_bary(int q, int j) {
     const double a = q < 3 ? kDa1 : kDa2;
     return (j == q % 3) ? 1.0 - 2.0 * a : a;
@@ -275,24 +384,17 @@ __device__ __forceinline__ double dense_bary(int q, int j) {
 
 __device__ __forceinline__ double dense_w(int q) { return q < 3 ? kDw1 : kDw2; }
 
-// Folded triangular enumeration of the pairs t < s: folded row f holds row f
-// (s in (f, nt)) followed by row nt - 1 - f, nt - 1 entries in all.
+// One launch per colour pair (DenseSched): each unordered far pair once, six
+// threads per pair (one per test rule point).
 __global__ void __launch_bounds__(DA_PAIRS * 6)
 dense_far_kernel(int nv, int nt, const double *__restrict__ verts, const int *__restrict__ tris,
-                 const double *__restrict__ tgeo, NearConst c, double2 *__restrict__ A) {
+                 const double *__restrict__ tgeo, NearConst c, DenseSched sc, double2 *__restrict__ A) {
     __shared__ double2 zs[DA_PAIRS][6][13];  // per pair, per test point: V[3], K[3], T[3], D[3], dc
     const int lp = threadIdx.x / 6, p = threadIdx.x % 6;
-    const int f = blockIdx.y;
-    const long long j = (long long)blockIdx.x * DA_PAIRS + lp;
     int t = -1, s = -1;
-    if (j < nt - 1 - f) {
-        t = f;
-        s = f + 1 + (int)j;
-    } else if (nt - 1 - f != f && j < nt - 1) {
-        t = nt - 1 - f;
-        s = t + 1 + (int)(j - (nt - 1 - f));
-    }
-    bool live = t >= 0 && s < nt;
+    long long row = -1;
+    const bool inrange = dense_pair(sc, lp, t, s, row);
+    bool live = inrange;
     int vt[3] = {0, 0, 0}, vs[3] = {0, 0, 0};
     if (live) {
         for (int a = 0; a < 3; ++a) {
@@ -360,11 +462,13 @@ dense_far_kernel(int nv, int nt, const double *__restrict__ verts, const int *__
     }
     for (int i = 0; i < 13; ++i) zs[lp][p][i] = Z[i];
     __syncthreads();
-    if (!live) return;
+    if (!live) {
+        if (inrange) dense_emit_zero(sc, row, p);
+        return;
+    }
     const double nn = gt[1] * gs[1] + gt[2] * gs[2] + gt[3] * gs[3];
     double2 dc = cd(0, 0);
     for (int pp = 0; pp < 6; ++pp) dc = cadd(dc, zs[lp][pp][12]);
-    const size_t n2 = 2 * (size_t)nv;
     // thread p writes entries (a, b) = (e / 3, e % 3) for e = p, p + 6 (the 9
     // entries of the four blocks: 36 values over 6 threads)
     for (int e = p; e < 9; e += 6) {
@@ -380,18 +484,7 @@ dense_far_kernel(int nv, int nt, const double *__restrict__ verts, const int *__
         const double *ca = gt + 4 + 3 * a, *cb = gs + 4 + 3 * b;
         const double cc = ca[0] * cb[0] + ca[1] * cb[1] + ca[2] * cb[2];
         const double2 dd = csub(cscale(dc, cc), cscale(d, nn));
-        const size_t ra = vt[a], rb = vs[b];
-        double *q;
-        // forward (test t, source s)
-        q = (double *)&A[ra * n2 + rb];                     atomicAdd(q, v.x);   atomicAdd(q + 1, v.y);
-        q = (double *)&A[ra * n2 + nv + rb];                atomicAdd(q, k.x);   atomicAdd(q + 1, k.y);
-        q = (double *)&A[(nv + ra) * n2 + rb];              atomicAdd(q, tt.x);  atomicAdd(q + 1, tt.y);
-        q = (double *)&A[(nv + ra) * n2 + nv + rb];         atomicAdd(q, dd.x);  atomicAdd(q + 1, dd.y);
-        // reversed (test s, source t)
-        q = (double *)&A[rb * n2 + ra];                     atomicAdd(q, v.x);   atomicAdd(q + 1, v.y);
-        q = (double *)&A[rb * n2 + nv + ra];                atomicAdd(q, -tt.x); atomicAdd(q + 1, -tt.y);
-        q = (double *)&A[(nv + rb) * n2 + ra];              atomicAdd(q, -k.x);  atomicAdd(q + 1, -k.y);
-        q = (double *)&A[(nv + rb) * n2 + nv + ra];         atomicAdd(q, dd.x);  atomicAdd(q + 1, dd.y);
+        dense_emit(sc, row, e, A, nv, vt[a], vs[b], v, k, tt, dd);
     }
 }
 
@@ -436,21 +529,14 @@ __global__ void dense_geom_ff_kernel(int nt, const double *__restrict__ verts, c
 
 __global__ void __launch_bounds__(DA_PAIRS * 6)
 dense_far_ff_kernel(int nv, int nt, const int *__restrict__ tris, const ff *__restrict__ G, DenseFFConst c,
-                    double2 *__restrict__ A) {
+                    DenseSched sc, double2 *__restrict__ A) {
     // complex values as ff2 with (re, im) in the two lanes
     __shared__ ff2 zs[DA_PAIRS][6][13];  // per pair, per test point: V[3], K[3], T[3], D[3], dc
     const int lp = threadIdx.x / 6, p = threadIdx.x % 6;
-    const int f = blockIdx.y;
-    const long long j = (long long)blockIdx.x * DA_PAIRS + lp;
     int t = -1, s = -1;
-    if (j < nt - 1 - f) {
-        t = f;
-        s = f + 1 + (int)j;
-    } else if (nt - 1 - f != f && j < nt - 1) {
-        t = nt - 1 - f;
-        s = t + 1 + (int)(j - (nt - 1 - f));
-    }
-    bool live = t >= 0 && s < nt;
+    long long row = -1;
+    const bool inrange = dense_pair(sc, lp, t, s, row);
+    bool live = inrange;
     int vt[3] = {0, 0, 0}, vs[3] = {0, 0, 0};
     if (live) {
         for (int a = 0; a < 3; ++a) {
@@ -521,11 +607,13 @@ dense_far_ff_kernel(int nv, int nt, const int *__restrict__ tris, const ff *__re
     }
     for (int i = 0; i < 13; ++i) zs[lp][p][i] = Z[i];
     __syncthreads();
-    if (!live) return;
+    if (!live) {
+        if (inrange) dense_emit_zero(sc, row, p);
+        return;
+    }
     const ff nn = ff_dot3(gt + 1, gs + 1);
     ff2 dc = zs[lp][0][12];
     for (int pp = 1; pp < 6; ++pp) dc = ff2_add(dc, zs[lp][pp][12]);
-    const size_t n2 = 2 * (size_t)nv;
     for (int e = p; e < 9; e += 6) {
         const int a = e / 3, b = e % 3;
         ff2 v = zero, k = zero, tt = zero, d = zero;
@@ -542,18 +630,7 @@ dense_far_ff_kernel(int nv, int nt, const int *__restrict__ tris, const ff *__re
         const double kx = ff_to_double(ff2_x(k)), ky = ff_to_double(ff2_y(k));
         const double tx = ff_to_double(ff2_x(tt)), ty = ff_to_double(ff2_y(tt));
         const double dx = ff_to_double(ff2_x(dd)), dy = ff_to_double(ff2_y(dd));
-        const size_t ra = vt[a], rb = vs[b];
-        double *o;
-        // forward (test t, source s)
-        o = (double *)&A[ra * n2 + rb];                     atomicAdd(o, vx);  atomicAdd(o + 1, vy);
-        o = (double *)&A[ra * n2 + nv + rb];                atomicAdd(o, kx);  atomicAdd(o + 1, ky);
-        o = (double *)&A[(nv + ra) * n2 + rb];              atomicAdd(o, tx);  atomicAdd(o + 1, ty);
-        o = (double *)&A[(nv + ra) * n2 + nv + rb];         atomicAdd(o, dx);  atomicAdd(o + 1, dy);
-        // reversed (test s, source t)
-        o = (double *)&A[rb * n2 + ra];                     atomicAdd(o, vx);  atomicAdd(o + 1, vy);
-        o = (double *)&A[rb * n2 + nv + ra];                atomicAdd(o, -tx); atomicAdd(o + 1, -ty);
-        o = (double *)&A[(nv + rb) * n2 + ra];              atomicAdd(o, -kx); atomicAdd(o + 1, -ky);
-        o = (double *)&A[(nv + rb) * n2 + nv + ra];         atomicAdd(o, dx);  atomicAdd(o + 1, dy);
+        dense_emit(sc, row, e, A, nv, vt[a], vs[b], cd(vx, vy), cd(kx, ky), cd(tx, ty), cd(dx, dy));
     }
 }
 
@@ -687,12 +764,77 @@ int dense_assemble(osrc_problem *pb, cudaStream_t st) {
     OSRC_CK(cudaMemsetAsync(pb->d_dense.p, 0, n2 * n2 * sizeof(double2), st));
     NearConst c{pb->p.k_ext, pb->p.k_int, pb->p.rho_ratio, pb->p.n_ss, pb->multi ? pb->d_obj.p : nullptr,
                  pb->mesh->d_tcomp.p, pb->p.formulation == OSRC_MULLER ? -1.0 : 1.0, pb->p.k_int_im};
-    const int folded = (nt + 1) / 2;
-    if (folded > 65535) {
+    // colours: greedy, in triangle order, so that triangles sharing a vertex
+    // differ; lists of each colour's triangles (ascending)
+    std::vector<int> col(nt, -1);
+    int ncol = 0;
+    {
+        std::vector<int> seen(64, -1);
+        for (int t = 0; t < nt; ++t) {
+            for (int a = 0; a < 3; ++a) {
+                const int v = m->tris[3 * t + a];
+                for (int e = m->vt_ptr[v]; e < m->vt_ptr[v + 1]; ++e) {
+                    const int c2 = col[m->vt_idx[e] / 3];
+                    if (c2 >= 0) {
+                        if (c2 >= (int)seen.size()) seen.resize(2 * c2 + 2, -1);
+                        seen[c2] = t;
+                    }
+                }
+            }
+            int c = 0;
+            while (c < (int)seen.size() && seen[c] == t) ++c;
+            col[t] = c;
+            if (c >= (int)seen.size()) seen.resize(2 * c + 2, -1);
+            ncol = std::max(ncol, c + 1);
+        }
+    }
+    std::vector<int> cbeg(ncol + 1, 0), order(nt);
+    for (int t = 0; t < nt; ++t) cbeg[col[t] + 1]++;
+    for (int c = 0; c < ncol; ++c) cbeg[c + 1] += cbeg[c];
+    {
+        std::vector<int> fill(cbeg.begin(), cbeg.end() - 1);
+        for (int t = 0; t < nt; ++t) order[fill[col[t]]++] = t;
+    }
+    int cmax = 0;
+    for (int c = 0; c < ncol; ++c) cmax = std::max(cmax, cbeg[c + 1] - cbeg[c]);
+    if ((cmax + 1) / 2 > 65535) {
         osrc_set_error("dense assembly: too many triangles for the dense path");
         return OSRC_UNSUPPORTED;
     }
-    dim3 grid((unsigned)((nt - 1 + DA_PAIRS - 1) / DA_PAIRS), (unsigned)folded);
+    DBuf<int> d_order;
+    DBuf<double2> stash;
+    OSRC_TRY(d_order.alloc(m->ctx, nt));
+    OSRC_CK(cudaMemcpyAsync(d_order.p, order.data(), nt * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (ncol > 1) OSRC_TRY(stash.alloc(m->ctx, (size_t)cmax * cmax * 36));
+    // launches: colour pairs in a fixed order; launch(sched) runs one pair
+    // kernel, then the stashed reverse values for ca < cb
+    auto for_each_pair = [&](auto launch) -> int {
+        for (int ca = 0; ca < ncol; ++ca)
+            for (int cb = ca; cb < ncol; ++cb) {
+                DenseSched sc{};
+                sc.la = d_order.p + cbeg[ca];
+                sc.lb = d_order.p + cbeg[cb];
+                sc.na = cbeg[ca + 1] - cbeg[ca];
+                sc.nb = cbeg[cb + 1] - cbeg[cb];
+                sc.diag = ca == cb;
+                sc.stash = stash.p;
+                if (sc.diag && sc.na < 2) continue;
+                if (sc.na < 1 || sc.nb < 1) continue;
+                const dim3 grid = sc.diag ? dim3((unsigned)((sc.na - 1 + DA_PAIRS - 1) / DA_PAIRS),
+                                                 (unsigned)((sc.na + 1) / 2))
+                                          : dim3((unsigned)((sc.nb + DA_PAIRS - 1) / DA_PAIRS), (unsigned)sc.na);
+                launch(sc, grid);
+                pb->launches++;
+                if (!sc.diag) {
+                    const long long work = (long long)sc.na * sc.nb * 9;
+                    dense_reverse_kernel<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(nv, m->d_tris.p, sc,
+                                                                                          pb->d_dense.p);
+                    pb->launches++;
+                }
+                OSRC_CK(cudaGetLastError());
+            }
+        return OSRC_OK;
+    };
     // float-float assembly on request, for lossless materials
     const bool use_ff = pb->p.dense_assembly == OSRC_ASSEMBLE_FF && !pb->absorb;
     DBuf<ff> geo;
@@ -719,17 +861,21 @@ int dense_assemble(osrc_problem *pb, cudaStream_t st) {
             OSRC_CK(cudaMemcpyAsync(fobj.p, h.data(), h.size() * sizeof(FFMat), cudaMemcpyHostToDevice, st));
             fc.obj = fobj.p;
         }
-        dense_far_ff_kernel<<<grid, DA_PAIRS * 6, 0, st>>>(nv, nt, m->d_tris.p, geo.p, fc, pb->d_dense.p);
+        OSRC_TRY(for_each_pair([&](const DenseSched &sc, dim3 grid) {
+            dense_far_ff_kernel<<<grid, DA_PAIRS * 6, 0, st>>>(nv, nt, m->d_tris.p, geo.p, fc, sc, pb->d_dense.p);
+        }));
     } else if (nt > 1) {
-        dense_far_kernel<<<grid, DA_PAIRS * 6, 0, st>>>(nv, nt, m->d_verts.p, m->d_tris.p, pb->d_tgeo.p, c,
-                                                         pb->d_dense.p);
+        OSRC_TRY(for_each_pair([&](const DenseSched &sc, dim3 grid) {
+            dense_far_kernel<<<grid, DA_PAIRS * 6, 0, st>>>(nv, nt, m->d_verts.p, m->d_tris.p, pb->d_tgeo.p, c, sc,
+                                                             pb->d_dense.p);
+        }));
     }
-    pb->launches++;
     dense_add_near_kernel<<<(nv + 127) / 128, 128, 0, st>>>(nv, pb->d_nr_ptr.p, pb->d_nr_col.p,
                                                             pb->d_nr_val.p, pb->d_dense.p);
     pb->launches++;
     OSRC_CK(cudaGetLastError());
-    if (use_ff) OSRC_CK(cudaStreamSynchronize(st));  // the float-float tables are released on return
+    // the colour lists, stash and float-float tables are released on return
+    OSRC_CK(cudaStreamSynchronize(st));
     return OSRC_OK;
 }
 

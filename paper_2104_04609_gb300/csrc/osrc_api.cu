@@ -1019,7 +1019,11 @@ size_t estimate_problem_bytes(int nv, int nt, const osrc_params &p) {
     b += (size_t)nv * 20 * (4 + 64) + (size_t)nv * 4;               // near CSR
     b += (size_t)nv * 8 * (4 + 16) + (size_t)nv * 4;                // M, S
     b += (size_t)nt * 14 * (576 + 16 + 9 * 8);                      // transient Sauter-Schwab build
-    if (p.precision == OSRC_FP64_DENSE) b += (size_t)4 * nv * nv * 16;
+    if (p.precision == OSRC_FP64_DENSE) {
+        b += (size_t)4 * nv * nv * 16;
+        const size_t cmax = (size_t)nt / 10 + 1;  // largest triangle colour (transient stash of the assembly)
+        b += cmax * cmax * 36 * 16;
+    }
     return b;
 }
 
