@@ -323,20 +323,36 @@ __device__ __forceinline__ bool dense_pair(const DenseSched &sc, int lp, int &t,
 // Adds the values of entry (a, b) of pair (t, s) to the four blocks, forward
 // and (same launch, or stashed) reversed; reversed K and T blocks are the
 // negated T and K values.
+// Adds v to the entry: within one launch every entry has at most one
+// writer (the colour-pair schedule), so the sum of each entry forms in the
+// fixed launch order whichever way the add is issued; OSRC_DENSE_RED issues
+// it as a reduction (no value returned) instead of a load and a store.
+#ifndef OSRC_DENSE_RED
+#define OSRC_DENSE_RED 1
+#endif
+__device__ __forceinline__ void dense_add(double2 *q, double x, double y) {
+#if OSRC_DENSE_RED
+    atomicAdd(&q->x, x);
+    atomicAdd(&q->y, y);
+#else
+    q->x += x;
+    q->y += y;
+#endif
+}
+
 __device__ __forceinline__ void dense_emit(const DenseSched &sc, long long row, int e, double2 *__restrict__ A,
                                            int nv, size_t ra, size_t rb, double2 v, double2 k, double2 tt,
                                            double2 dd) {
     const size_t n2 = 2 * (size_t)nv;
-    double2 *q;
-    q = &A[ra * n2 + rb];                q->x += v.x;  q->y += v.y;
-    q = &A[ra * n2 + nv + rb];           q->x += k.x;  q->y += k.y;
-    q = &A[(nv + ra) * n2 + rb];         q->x += tt.x; q->y += tt.y;
-    q = &A[(nv + ra) * n2 + nv + rb];    q->x += dd.x; q->y += dd.y;
+    dense_add(&A[ra * n2 + rb], v.x, v.y);
+    dense_add(&A[ra * n2 + nv + rb], k.x, k.y);
+    dense_add(&A[(nv + ra) * n2 + rb], tt.x, tt.y);
+    dense_add(&A[(nv + ra) * n2 + nv + rb], dd.x, dd.y);
     if (sc.diag) {
-        q = &A[rb * n2 + ra];            q->x += v.x;  q->y += v.y;
-        q = &A[rb * n2 + nv + ra];       q->x -= tt.x; q->y -= tt.y;
-        q = &A[(nv + rb) * n2 + ra];     q->x -= k.x;  q->y -= k.y;
-        q = &A[(nv + rb) * n2 + nv + ra]; q->x += dd.x; q->y += dd.y;
+        dense_add(&A[rb * n2 + ra], v.x, v.y);
+        dense_add(&A[rb * n2 + nv + ra], -tt.x, -tt.y);
+        dense_add(&A[(nv + rb) * n2 + ra], -k.x, -k.y);
+        dense_add(&A[(nv + rb) * n2 + nv + ra], dd.x, dd.y);
     } else {
         double2 *o = sc.stash + (row * 9 + e) * 4;
         o[0] = v;
@@ -370,11 +386,10 @@ __global__ void dense_reverse_kernel(int nv, const int *__restrict__ tris, Dense
     const size_t ra = tris[3 * t + e / 3], rb = tris[3 * s + e % 3];
     const size_t n2 = 2 * (size_t)nv;
     const double2 *o = sc.stash + g * 4;
-    double2 *q;
-    q = &A[rb * n2 + ra];                 q->x += o[0].x; q->y += o[0].y;
-    q = &A[rb * n2 + nv + ra];            q->x += o[1].x; q->y += o[1].y;
-    q = &A[(nv + rb) * n2 + ra];          q->x += o[2].x; q->y += o[2].y;
-    q = &A[(nv + rb) * n2 + nv + ra];     q->x += o[3].x; q->y += o[3].y;
+    dense_add(&A[rb * n2 + ra], o[0].x, o[0].y);
+    dense_add(&A[rb * n2 + nv + ra], o[1].x, o[1].y);
+    dense_add(&A[(nv + rb) * n2 + ra], o[2].x, o[2].y);
+    dense_add(&A[(nv + rb) * n2 + nv + ra], o[3].x, o[3].y);
 }
 
 __device__ __forceinline__ double dense_bary(int q, int j) {
