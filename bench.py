@@ -74,6 +74,11 @@ def parse():
                     help="target CPU time of the oracle sample")
     ap.add_argument("--serve-route", default="both", choices=["both", "matrix_free", "hybrid"],
                     help="serving legs to run")
+    ap.add_argument("--serve-deadline", type=float, default=None, metavar="S",
+                    help="stop the serving leg S seconds after its first submission (unfinished "
+                         "requests are reported as such)")
+    ap.add_argument("--serve-progress", default=None, metavar="FILE",
+                    help="append one JSON line per finished request to FILE")
     ap.add_argument("--serve-requests", type=int, default=2,
                     help="requests of the seeded Poisson stream in the serving legs, at their stated "
                          "sizes (0: skip; 50 for the full measurement, about 20 minutes)")
@@ -415,9 +420,11 @@ def run_ours(args, D):
         out["four_spheres"] = run_four_spheres(D.local)
     if args.serve_requests > 0 and single:
         if args.serve_route in ("both", "matrix_free"):
-            out["serving"] = run_serving(args.serve_requests, D.local)
+            out["serving"] = run_serving(args.serve_requests, D.local, progress=args.serve_progress,
+                                         deadline=args.serve_deadline)
         if args.serve_route in ("both", "hybrid"):
-            out["serving_batched"] = run_serving(args.serve_requests, D.local, route="hybrid")
+            out["serving_batched"] = run_serving(args.serve_requests, D.local, route="hybrid",
+                                                 progress=args.serve_progress, deadline=args.serve_deadline)
     out["_solution"] = (xs, bs, r_gpu) if D.rank == 0 else None
     return out, (infos[-1]["iterations"] if infos else REF_ITERATIONS)
 
@@ -915,7 +922,7 @@ def serving_workload(n_req):
     return out
 
 
-def run_serving(n_req, device, route="matrix_free"):
+def run_serving(n_req, device, route="matrix_free", progress=None, deadline=None):
     """route "matrix_free": every request FP32 matrix-free (a request with
     several right-hand sides runs GMRES in lockstep over them, one far-field
     launch per iteration for all); "hybrid": requests with several
@@ -949,9 +956,13 @@ def run_serving(n_req, device, route="matrix_free"):
                                             maxit=1000))
         t_sub = time.perf_counter() - t0
         lat, que, its, ok, per = [], [], 0, 0, []
+        unfinished = 0
         for rid, w in zip(ids, work):
-            B.osrc_server_wait(sv, rid, 3600.0)
+            wait = 3600.0 if deadline is None else max(0.0, deadline - (time.perf_counter() - t0))
+            B.osrc_server_wait(sv, rid, wait)
             done, st, l, info = B.osrc_server_poll(sv, rid)
+            if not done:
+                unfinished += 1
             if done:
                 lat.append(l)
                 que.append(info["ms_queued"])
@@ -961,23 +972,33 @@ def run_serving(n_req, device, route="matrix_free"):
                             "route": w["route"], "latency_s": round(l / 1e3, 3),
                             "queued_s": round(info["ms_queued"] / 1e3, 3),
                             "iterations": info["total_iterations"], "status": int(st)})
+                if progress:  # one line per finished request, for long runs
+                    with open(progress, "a") as f:
+                        f.write(json.dumps({"t_s": time.perf_counter() - t0, **per[-1]}) + "\n")
         t1 = time.perf_counter()
         stats = B.osrc_server_get_stats(sv)
     finally:
         B.osrc_server_destroy(sv)
         B.osrc_destroy(ctx)
-    nrhs = sum(len(w["dirs"]) for w in work)
+    nrhs = sum(p["rhs"] for p in per)
     lat, que = np.asarray(lat), np.asarray(que)
     span = max(work[-1]["t"], 1e-9)
     wall = t1 - t0
+    if unfinished:  # censored: the unfinished requests' latency is at least the deadline
+        lat = np.concatenate([lat, np.full(unfinished, 1e3 * wall)])
     return {
-        "route": route, "requests": len(work), "right_hand_sides": nrhs, "converged_requests": ok,
-        "offered_requests_per_s": len(work) / span, "served_requests_per_s": len(work) / wall,
+        "route": route, "requests": len(work), "finished_requests": len(per),
+        "unfinished_at_deadline": unfinished, "deadline_s": deadline,
+        "right_hand_sides_solved": nrhs, "converged_requests": ok,
+        "offered_requests_per_s": len(work) / span, "served_requests_per_s": len(per) / wall,
         "solves_per_s": nrhs / wall, "wall_s": wall, "submit_span_s": t_sub,
+        "right_hand_sides_submitted": sum(len(w["dirs"]) for w in work),
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                       "max": float(lat.max())},
+                       "max": float(lat.max()),
+                       "note": "unfinished requests count with the deadline as their latency (a lower "
+                               "bound)" if unfinished else "all requests finished"},
         "queued_ms": {"p50": float(np.percentile(que, 50)), "p99": float(np.percentile(que, 99))},
-        "queueing_share_of_latency": float(que.sum() / lat.sum()),
+        "queueing_share_of_latency": float(que.sum() / max(np.asarray(lat[:len(que)]).sum(), 1e-9)),
         "gmres_iterations": its, "max_active": 4, "active_peak": stats["active_peak"],
         "cache_hits": stats["cache_hits"], "cache_misses": stats["cache_misses"],
         "mem_peak_bytes": stats["mem_peak"], "block_requests": stats["batched_jobs"],

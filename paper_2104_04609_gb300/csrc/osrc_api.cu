@@ -1110,6 +1110,10 @@ static int gmres_solve_lockstep(osrc_problem *pb, const void *b, void *x, int nr
         for (;;) {
             OSRC_CK(cudaStreamSynchronize(st));
             OSRC_TRY(far_multi_check(pb, st));
+            if (pb->cancel && pb->cancel->load()) {
+                osrc_set_error("lockstep GMRES cancelled");
+                return OSRC_TIMEOUT;
+            }
             if (apply_pending) {
                 float ms = 0.f;
                 OSRC_CK(cudaEventElapsedTime(&ms, ea, eb));

@@ -195,6 +195,9 @@ struct osrc_problem {
     DBuf<float> d_partm;      // [ns][R][4][6nt] u1, u2 partial sums
     DBuf<float> d_partA;      // [ns][R][6][nt] curl-term partial sums per test triangle
     DBuf<int> d_farm_err;     // set when the kernel gave up a bounded wait
+    // when set and true, a lockstep GMRES on this problem stops at its next
+    // iteration with OSRC_TIMEOUT (the serving loop's shutdown)
+    const std::atomic<bool> *cancel = nullptr;
     int farm_ns = 1, farm_cap = 0;
     bool far_reduce = false;  // centred far kernel with float-float phases (large k r)
     // ---- FP64 per-triangle geometry: area, normal, curls of the hat functions

@@ -354,8 +354,10 @@ void osrc_server::lockstep_body(Slot &slot, Request *r, CacheEntry *entry) {
     for (int i = 0; i < r->nrhs && status == OSRC_OK; ++i)
         status = rhs_build(entry->pb, r->kind, r->src.data() + 3 * (size_t)i, slot.d_b.p + (size_t)i * n2, slot.st);
     if (status == OSRC_OK) {
+        entry->pb->cancel = &stop;  // server shutdown ends the solve at its next iteration
         const int gs = osrc_gmres_solve(entry->pb, slot.d_b.p, slot.d_x.p, r->nrhs, r->tol, r->maxit, 0, &info,
                                         slot.st);
+        entry->pb->cancel = nullptr;
         if (gs != OSRC_OK && gs != OSRC_NOT_CONVERGED) status = gs;
         if (status == OSRC_OK &&
             (cudaMemcpyAsync(r->x.data(), slot.d_x.p, (size_t)r->nrhs * n2 * sizeof(double2),
