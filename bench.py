@@ -577,6 +577,7 @@ def run_dense(nrhs, n_matfree, device):
         gemm_ms = g0.elapsed_time(g1) / reps
         gemm_tf = 2.0 * Mp * N * Kp / (gemm_ms * 1e-3) / 1e12
         peaks = measured_peaks() or {}
+        hbm_peak = peaks.get("hbm_gbs") or 6800.0
         peak = peaks.get("bf16_tflops")
         basis = "measured burst (MEASURED_PEAKS.json)"
         if not peak:
@@ -598,7 +599,14 @@ def run_dense(nrhs, n_matfree, device):
             "residual": info["residual"], "gpu_launches": int(launches),
             "gemm": {"bound": "tensor", "M": Mp, "N": N, "K": Kp, "avg_ms": gemm_ms,
                      "achieved": gemm_tf, "peak": peak, "unit": "TFLOP/s", "frac": gemm_tf / peak,
-                     "peak_basis": basis},
+                     "peak_basis": basis,
+                     # 2 N flops per byte of A (BF16) is below the ridge of this part (bf16 peak
+                     # / HBM bandwidth, about 280): the product is bound by streaming A
+                     "hbm_view": {"bound": "hbm", "a_bytes": Mp * Kp * 2,
+                                  "achieved_gbs": Mp * Kp * 2 / (gemm_ms * 1e-3) / 1e9,
+                                  "peak_gbs": hbm_peak,
+                                  "frac": Mp * Kp * 2 / (gemm_ms * 1e-3) / 1e9 / hbm_peak,
+                                  "flops_per_a_byte": N, "ridge": peak / hbm_peak * 1e3}},
         }
         # the FP32 matrix-free path on the same right-hand sides, one at a time
         if n_matfree > 0:
