@@ -167,3 +167,35 @@ def test_multi_sampled_rows_sphere10242(B):
         assert np.linalg.norm(Y[0] - y1) / np.linalg.norm(y1) < 2e-6
     finally:
         S.close()
+
+
+def test_lockstep_more_than_sixteen_and_not_converged(B, small):
+    """19 right-hand sides (two groups: 16 + 3) equal one-at-a-time solves;
+    with an iteration cap below what some need, the call reports
+    OSRC_NOT_CONVERGED and every run stopped at the cap."""
+    v, t, S, _, _ = small
+    b = S.rhs_planewave(plane_wave_dirs(19, seed=12))
+    x, info = S.solve(b, tol=1e-8, maxit=300)
+    assert info.converged == 1
+    for r in (0, 15, 16, 18):
+        xs, _ = S.solve(b[r:r + 1].contiguous(), tol=1e-8, maxit=300)
+        d = np.linalg.norm(x[r].cpu().numpy() - xs[0].cpu().numpy()) / np.linalg.norm(xs[0].cpu().numpy())
+        assert d < 1e-5, (r, d)
+    x2, info2 = S.solve(b[:4].contiguous(), tol=1e-12, maxit=5, raise_on_nonconvergence=False)
+    assert info2.converged == 0 and info2.total_iterations == 4 * 5
+    assert np.isfinite(x2.cpu().numpy()).all()
+
+
+def test_lockstep_calderon_falls_back(B, small):
+    """The Calderon preconditioner applies the operator inside the
+    preconditioner: several right-hand sides are then solved one at a time,
+    with the same results as single solves."""
+    v, t, _, far, near = small
+    S = B.Solver(v, t, K0, K1, RHO, precond=B.OSRC_PRECOND_CALDERON)
+    try:
+        b = S.rhs_planewave(plane_wave_dirs(2, seed=8))
+        x, _ = S.solve(b, tol=1e-8, maxit=300)
+        xd = np.linalg.solve(far + near, b.cpu().numpy().T).T
+        assert np.linalg.norm(x.cpu().numpy() - xd) / np.linalg.norm(xd) < 1e-5
+    finally:
+        S.close()
