@@ -94,14 +94,15 @@ def parse():
     ap.add_argument("--no-objects", action="store_true",
                     help="skip the four-sphere multiple-scattering solve")
     ap.add_argument("--profile-case", choices=["far-small", "far-multi-small", "precond-small", "dense-short",
-                                               "dense-small"],
+                                               "dense-small", "gemm"],
                     help="instead of the benchmark: run one small case for profiler captures "
                          "(far-small: far-field applies on a 2562-vertex sphere, plain then "
                          "large-ka; far-multi-small: the same with 8 right-hand sides per apply; "
                          "precond-small: five OSRC preconditioner applies on it; "
                          "dense-short: ellipsoid8000, 128 right-hand sides, one "
                          "refinement of 120 inner iterations; dense-small: the same on a "
-                         "3000-vertex ellipsoid, 24 inner iterations)")
+                         "3000-vertex ellipsoid, 24 inner iterations; gemm: three tensor-core "
+                         "GEMMs at M 16000, N 256, K 32000)")
     ap.add_argument("--sponge-sweep", action="store_true",
                     help="instead of the benchmark: GMRES iterations of the four formulations on "
                          "the level-2 Menger sponge at 0.5 and 1 MHz")
@@ -565,13 +566,14 @@ def run_dense(nrhs, n_matfree, device):
         gB = torch.randn(N, Kp, device=dev).to(torch.bfloat16)
         gC = torch.empty(Mp, N, device=dev, dtype=torch.float32)
         gE = torch.zeros(1, device=dev, dtype=torch.int32)
+        gW = torch.empty(max(B.osrc_gemm_bf16_ws_bytes(Mp, N, Kp), 16), dtype=torch.uint8, device=dev)
         for _ in range(3):
-            B.osrc_gemm_bf16(gA, gB, gC, gE)
+            B.osrc_gemm_bf16(gA, gB, gC, gE, ws=gW)
         reps = 20
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record(stream)
         for _ in range(reps):
-            B.osrc_gemm_bf16(gA, gB, gC, gE)
+            B.osrc_gemm_bf16(gA, gB, gC, gE, ws=gW)
         g1.record(stream)
         torch.cuda.synchronize()
         gemm_ms = g0.elapsed_time(g1) / reps
@@ -582,7 +584,7 @@ def run_dense(nrhs, n_matfree, device):
         basis = "measured burst (MEASURED_PEAKS.json)"
         if not peak:
             peak, basis = FALLBACK_BF16_TFLOPS, "fallback 1.9 PFLOP/s burst (no MEASURED_PEAKS.json)"
-        del gA, gB, gC
+        del gA, gB, gC, gW
         out = {
             "workload": f"{DENSE_WORKLOAD}: ellipsoid (1, 0.7, 0.5), {S.nv} vertices, k_ext "
                         f"{W['k_ext']:g}, k_int {W['k_int']:g}, rho ratio {W['rho_ratio']:g}, "
@@ -1319,6 +1321,20 @@ def profile_case(name, device=0):
             S.precond(x)
         torch.cuda.synchronize()
         S.close()
+        return
+    if name == "gemm":
+        # the tensor-core GEMM alone at the batched path's shape for ellipsoid8000
+        # (M 16000, N 2 x 128, K 32000; 1 GB of A), three launches
+        M, N, K = 16000, 256, 32000
+        A = torch.randn(M, K, device=f"cuda:{device}").to(torch.bfloat16)
+        Bm = torch.randn(N, K, device=f"cuda:{device}").to(torch.bfloat16)
+        C = torch.empty(M, N, device=f"cuda:{device}")
+        err = torch.zeros(1, dtype=torch.int32, device=f"cuda:{device}")
+        ws = torch.empty(max(B.osrc_gemm_bf16_ws_bytes(M, N, K), 16), dtype=torch.uint8, device=f"cuda:{device}")
+        for _ in range(3):
+            B.osrc_gemm_bf16(A, Bm, C, err, ws=ws)
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0
         return
     if name == "dense-short":
         W = workload(DENSE_WORKLOAD)

@@ -253,12 +253,23 @@ int osrc_gmres_solve(osrc_problem *pb, const void *b, void *x, int nrhs, double 
  * in tensor memory, TMA-staged operands): the dense complex products of the
  * assembled path (Sec. 2.3 system applied to blocks of right-hand sides) run
  * through it in their real embedding.  A: device BF16, M x K row-major;
- * B: device BF16, N x K row-major (both K-major); C: device FP32, M x ldc.
- * M % 128 == 0, K % 64 == 0, 16 <= N <= 256 with N % 16 == 0, rows 16-byte
- * aligned; otherwise OSRC_INVALID_ARG.  err_flag_dev: device int that the
- * kernel sets to 1 if a bounded wait gave up (then C is unspecified). */
+ * B: device BF16, N x K row-major (both K-major); C: device FP32, M x ldc,
+ * ldc >= N.  M % 128 == 0, K % 64 == 0, 16 <= N <= 256 with N % 16 == 0,
+ * rows 16-byte aligned; otherwise OSRC_INVALID_ARG.  The tile x K-slice work
+ * is spread over one CTA per SM; tiles split between CTAs leave their pieces
+ * in ws_dev (device, caller-owned, 16-byte aligned, at least
+ * osrc_gemm_bf16_ws_bytes bytes; may be NULL when that is 0, else
+ * OSRC_INVALID_ARG) and a second launch on the same stream sums them in a
+ * fixed order, so C is identical from run to run.  Calls that share ws_dev
+ * must not overlap on the GPU.  err_flag_dev: device int that the kernel
+ * sets to 1 if a bounded wait gave up (then C is unspecified). */
 int osrc_gemm_bf16(const void *A, int M, int K, const void *B, int N, float *C, int ldc,
-                   int *err_flag_dev, void *stream);
+                   void *ws_dev, size_t ws_bytes, int *err_flag_dev, void *stream);
+
+/* Workspace bytes osrc_gemm_bf16 needs for this shape on the current device
+ * (depends on its SM count; 0 when no tile is split).  Unsupported shapes:
+ * OSRC_INVALID_ARG. */
+int osrc_gemm_bf16_ws_bytes(int M, int N, int K, size_t *bytes);
 
 /* ---- batched mixed-precision solve (dense assembled path) ---------------------------- */
 typedef struct osrc_batched_info {

@@ -157,7 +157,9 @@ SIGNATURES = {
     "osrc_server_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(osrc_server_stats)]),
     "osrc_server_destroy": (None, [_VP]),
     "osrc_gemm_bf16": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, _VP,
-                                      ctypes.c_int, _VP, _VP]),
+                                      ctypes.c_int, _VP, ctypes.c_size_t, _VP, _VP]),
+    "osrc_gemm_bf16_ws_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_size_t)]),
     "osrc_dense_batched_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
                                                 ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                                 ctypes.c_double, ctypes.POINTER(osrc_batched_info),
@@ -508,10 +510,19 @@ def osrc_server_destroy(sv):
         del _REQ_SHAPE[key]
 
 
-def osrc_gemm_bf16(A, B, C, err, stream=None):
+def osrc_gemm_bf16_ws_bytes(M, N, K):
+    """Workspace bytes the tensor-core GEMM needs for this shape on the current device."""
+    out = ctypes.c_size_t(0)
+    _check(lib().osrc_gemm_bf16_ws_bytes(int(M), int(N), int(K), ctypes.byref(out)), "osrc_gemm_bf16_ws_bytes")
+    return int(out.value)
+
+
+def osrc_gemm_bf16(A, B, C, err, ws=None, stream=None):
     """C = A B^T on the tensor cores; A (M, K), B (N, K) bfloat16 CUDA tensors,
     C (M, ldc) float32, err a one-element int32 CUDA tensor (set to 1 if the
-    kernel's bounded waits gave up)."""
+    kernel's bounded waits gave up).  ws: CUDA tensor of at least
+    osrc_gemm_bf16_ws_bytes(M, N, K) bytes for the pieces of split tiles (one
+    is allocated per call when None)."""
     import torch
 
     assert A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16 and C.dtype == torch.float32
@@ -519,8 +530,14 @@ def osrc_gemm_bf16(A, B, C, err, stream=None):
     assert A.is_contiguous() and B.is_contiguous() and C.is_contiguous()
     M, K = A.shape
     N = B.shape[0]
+    if ws is None:
+        nb = osrc_gemm_bf16_ws_bytes(M, N, K) if M % 128 == 0 and K % 64 == 0 and 16 <= N <= 256 \
+            and N % 16 == 0 else 0
+        ws = torch.empty(max(nb, 16), dtype=torch.uint8, device=A.device)
+    assert ws.is_cuda and ws.is_contiguous()
     _check(lib().osrc_gemm_bf16(ctypes.c_void_p(A.data_ptr()), M, K, ctypes.c_void_p(B.data_ptr()), N,
                                 ctypes.c_void_p(C.data_ptr()), C.shape[1],
+                                ctypes.c_void_p(ws.data_ptr()), ws.numel() * ws.element_size(),
                                 ctypes.c_void_p(err.data_ptr()), _stream(stream)), "osrc_gemm_bf16")
 
 

@@ -746,8 +746,9 @@ __global__ void add_block32_kernel(int n2, int nrhs, int R, const float2 *__rest
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-int umma_gemm_bf16(const void *A, int M, int K, const void *Bm, int N, float *C, int ldc, int *err,
-                   cudaStream_t st);
+int umma_gemm_bf16(const void *A, int M, int K, const void *Bm, int N, float *C, int ldc, float *ws,
+                   size_t ws_floats, int *err, cudaStream_t st);
+size_t umma_gemm_ws_floats(int M, int N, int K);
 
 struct BatchedState {
     int n2 = 0, Mp = 0, Kp = 0, R = 0;
@@ -755,6 +756,7 @@ struct BatchedState {
     DBuf<__nv_bfloat16> Pcat;   // explicit preconditioner matrix P M^-1 (packed like Acat), if built
     bool pdense = false;
     DBuf<float> C;
+    DBuf<float> gws;            // pieces of the GEMM's split tiles
     DBuf<float> M32, S32;
     DBuf<float4> AFF;           // float-float split of the FP64 system matrix (residuals)
     DBuf<float2> nr32;          // touching-pair CSR values in FP32
@@ -824,6 +826,7 @@ int batched_prepare(osrc_problem *pb, int R, int maxit_inner, cudaStream_t st) {
         OSRC_TRY(bs->Bcat.alloc(ctx, (size_t)2 * R * bs->Kp));
         OSRC_CK(cudaMemsetAsync(bs->Bcat.p, 0, (size_t)2 * R * bs->Kp * sizeof(__nv_bfloat16), st));
         OSRC_TRY(bs->C.alloc(ctx, (size_t)bs->Mp * 2 * R));
+        OSRC_TRY(bs->gws.alloc(ctx, umma_gemm_ws_floats(bs->Mp, 2 * R, bs->Kp)));
         OSRC_TRY(bs->kwork.alloc(ctx, (size_t)nsys * 3 * vplane));
         OSRC_TRY(bs->kdinv.alloc(ctx, (size_t)nsys * nv));
         OSRC_TRY(bs->kW.alloc(ctx, (size_t)nsys * vplane));
@@ -858,7 +861,8 @@ static int batched_matvec(osrc_problem *pb, const float2 *x, float2 *y, cudaStre
     const int n2 = bs->n2, R = bs->R, nv = pb->nv;
     dim3 gb((n2 + 31) / 32, (R + 31) / 32);
     pack_b_kernel<<<gb, dim3(32, 8), 0, st>>>(n2, R, bs->Kp, x, bs->Bcat.p);
-    OSRC_TRY(umma_gemm_bf16(bs->Acat.p, bs->Mp, bs->Kp, bs->Bcat.p, 2 * R, bs->C.p, 2 * R, bs->err.p, st));
+    OSRC_TRY(umma_gemm_bf16(bs->Acat.p, bs->Mp, bs->Kp, bs->Bcat.p, 2 * R, bs->C.p, 2 * R, bs->gws.p,
+                            bs->gws.n, bs->err.p, st));
     unpack_near_kernel<<<nv, R, 0, st>>>(nv, R, 2 * R, bs->C.p, pb->d_nr_ptr.p, pb->d_nr_col.p, bs->nr32.p, x,
                                          y);
     pb->launches += 3;
@@ -939,7 +943,8 @@ static int batched_precond_dense(osrc_problem *pb, const float2 *y, float2 *z, c
     const int n2 = bs->n2, R = bs->R;
     dim3 gb((n2 + 31) / 32, (R + 31) / 32);
     pack_b_kernel<<<gb, dim3(32, 8), 0, st>>>(n2, R, bs->Kp, y, bs->Bcat.p);
-    OSRC_TRY(umma_gemm_bf16(bs->Pcat.p, bs->Mp, bs->Kp, bs->Bcat.p, 2 * R, bs->C.p, 2 * R, bs->err.p, st));
+    OSRC_TRY(umma_gemm_bf16(bs->Pcat.p, bs->Mp, bs->Kp, bs->Bcat.p, 2 * R, bs->C.p, 2 * R, bs->gws.p,
+                            bs->gws.n, bs->err.p, st));
     const size_t plane = (size_t)n2 * R;
     unpack_plain_kernel<<<(unsigned)((plane + 255) / 256), 256, 0, st>>>(n2, R, 2 * R, bs->C.p, z);
     pb->launches += 3;
@@ -1195,6 +1200,7 @@ size_t estimate_batched_bytes(int nv, int n_pade, int nrhs, int maxit) {
     b += (size_t)(maxit + 1) * (maxit + 1) * R * 8;             // Hessenberg
     b += (size_t)(maxit + 1) * 64 * R * 8 + 8 * (size_t)(maxit + 1) * R * 8;
     b += 4 * n2 * R * 8 + Mp * 2 * R * 4 + 2 * R * Kp * 2;     // block vectors, GEMM in/out
+    b += umma_gemm_ws_floats((int)Mp, (int)(2 * R), (int)Kp) * 4;  // GEMM split-tile pieces
     b += nsys * (4 * (size_t)nv * R + nv) * 8;                  // shifted solves
     b += (size_t)nrhs * n2 * 16;                                // FP64 residual block
     return b;

@@ -20,7 +20,7 @@ def B():
 @pytest.mark.parametrize("N", [16, 48, 256])
 def test_tcgen05_gemm_matches_fp32(B, N):
     g = torch.Generator(device="cpu").manual_seed(N)
-    M, K = 384, 512          # 3 CTAs, 8 K slices: the 4-stage ring wraps twice
+    M, K = 384, 512          # three 128-row tiles, 8 K slices: one CTA, three segments
     A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
     Bm = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
     C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
@@ -34,6 +34,34 @@ def test_tcgen05_gemm_matches_fp32(B, N):
     assert rel < 1e-5, rel
 
 
+# (M, K, N): one tile; tiles split between two CTAs; tiles split between up
+# to four CTAs (a CTA holding the end of one tile and the start of the next);
+# 50 whole tiles per CTA (the two accumulators alternate); whole tiles
+# between split ones; the batched path's shape class (85 CTAs, 4 pieces)
+@pytest.mark.parametrize("M,K,N", [(128, 512, 256), (768, 4096, 256), (384, 8192, 48),
+                                   (102400, 64, 128), (51200, 320, 256), (4096, 8192, 256)])
+def test_tcgen05_gemm_stream_k(B, M, K, N):
+    g = torch.Generator(device="cpu").manual_seed(M + K + N)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    Bm = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    nb = B.osrc_gemm_bf16_ws_bytes(M, N, K)
+    ws = torch.full((max(nb, 16) // 4,), float("nan"), dtype=torch.float32, device="cuda")
+    B.osrc_gemm_bf16(A, Bm, C, err, ws=ws)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    ref = (A.double() @ Bm.double().T).float()
+    assert torch.isfinite(C).all()
+    rel = float((C - ref).abs().max() / ref.abs().max())
+    assert rel < 1e-5, rel
+    # split tiles are summed in a fixed order: the same bytes every run
+    C2 = torch.full_like(C, float("nan"))
+    B.osrc_gemm_bf16(A, Bm, C2, err, ws=ws)
+    torch.cuda.synchronize()
+    assert torch.equal(C, C2)
+
+
 def test_tcgen05_gemm_rejects_bad_shapes(B):
     A = torch.zeros(100, 64, dtype=torch.bfloat16, device="cuda")
     Bm = torch.zeros(16, 64, dtype=torch.bfloat16, device="cuda")
@@ -41,6 +69,19 @@ def test_tcgen05_gemm_rejects_bad_shapes(B):
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
     with pytest.raises(B.OsrcError):
         B.osrc_gemm_bf16(A, Bm, C, err)
+
+
+def test_tcgen05_gemm_rejects_short_workspace(B):
+    M, K, N = 768, 4096, 256
+    nb = B.osrc_gemm_bf16_ws_bytes(M, N, K)
+    assert nb > 0
+    A = torch.zeros(M, K, dtype=torch.bfloat16, device="cuda")
+    Bm = torch.zeros(N, K, dtype=torch.bfloat16, device="cuda")
+    C = torch.zeros(M, N, dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.zeros(nb - 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.OsrcError):
+        B.osrc_gemm_bf16(A, Bm, C, err, ws=ws)
 
 
 def test_batched_inner_pieces(B):
