@@ -442,7 +442,7 @@ static bool umma_shape_ok(int M, int N, int K) {
 }
 
 // One CTA per SM, but at least UM_MIN_ITERS K slices each.
-int umma_plan(int M, int N, int K, UmmaPlan *p) {
+static int umma_plan(int M, int N, int K, UmmaPlan *p) {
     if (!umma_shape_ok(M, N, K)) {
         osrc_set_error("umma_gemm_bf16: unsupported shape");
         return OSRC_INVALID_ARG;
@@ -477,8 +477,8 @@ size_t umma_gemm_ws_floats(int M, int N, int K) {
 // C = A B^T for BF16 A (M x K), B (N x K), FP32 C (M x ldc); ws holds
 // ws_floats >= umma_gemm_ws_floats(M, N, K) floats (may be null when that is
 // 0).  err: device int set to 1 if a bounded wait gave up.
-int umma_gemm_run(const void *A, int M, int K, const void *Bm, int N, float *C, int ldc, float *ws,
-                  size_t ws_floats, int *err, cudaStream_t st) {
+static int umma_gemm_run(const void *A, int M, int K, const void *Bm, int N, float *C, int ldc, float *ws,
+                         size_t ws_floats, int *err, cudaStream_t st) {
     UmmaPlan p;
     OSRC_TRY(umma_plan(M, N, K, &p));
     if (ldc < N || !A || !Bm || !C || !err) return OSRC_INVALID_ARG;
