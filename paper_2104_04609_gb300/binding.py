@@ -517,6 +517,22 @@ def osrc_gemm_bf16_ws_bytes(M, N, K):
     return int(out.value)
 
 
+def _gemm_shapes(A, B, C, err):
+    """(M, K, N) of C = A B^T, checked before any device call: the C ABI
+    takes bare pointers and sizes, so B must have A's K columns, C must have
+    M rows and at least N columns, and err one element."""
+    if A.dim() != 2 or B.dim() != 2 or C.dim() != 2:
+        raise ValueError("osrc_gemm_bf16: A, B and C must be matrices")
+    M, K = (int(v) for v in A.shape)
+    N = int(B.shape[0])
+    if int(B.shape[1]) != K:
+        raise ValueError(f"osrc_gemm_bf16: B has {int(B.shape[1])} columns, A has {K}")
+    if int(C.shape[0]) != M or int(C.shape[1]) < N:
+        raise ValueError(f"osrc_gemm_bf16: C is {tuple(C.shape)}, ({M}, >= {N}) needed")
+    _need(err, 1, "osrc_gemm_bf16 err")
+    return M, K, N
+
+
 def osrc_gemm_bf16(A, B, C, err, ws=None, stream=None):
     """C = A B^T on the tensor cores; A (M, K), B (N, K) bfloat16 CUDA tensors,
     C (M, ldc) float32, err a one-element int32 CUDA tensor (set to 1 if the
@@ -525,11 +541,10 @@ def osrc_gemm_bf16(A, B, C, err, ws=None, stream=None):
     is allocated per call when None)."""
     import torch
 
+    M, K, N = _gemm_shapes(A, B, C, err)
     assert A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16 and C.dtype == torch.float32
     assert A.is_cuda and B.is_cuda and C.is_cuda and err.is_cuda and err.dtype == torch.int32
     assert A.is_contiguous() and B.is_contiguous() and C.is_contiguous()
-    M, K = A.shape
-    N = B.shape[0]
     if ws is None:
         nb = osrc_gemm_bf16_ws_bytes(M, N, K) if M % 128 == 0 and K % 64 == 0 and 16 <= N <= 256 \
             and N % 16 == 0 else 0

@@ -142,6 +142,27 @@ def test_short_buffers_rejected_on_the_host():
         B._need(torch.zeros(2, 3, dtype=torch.complex128), 8, "x")
 
 
+def test_gemm_shapes_rejected_on_the_host():
+    """The tensor-core GEMM takes M, K, N and bare pointers: B must have A's
+    K columns and C at least M x N, checked before any device call."""
+    from paper_2104_04609_gb300 import binding as B
+
+    torch = pytest.importorskip("torch")
+    A = torch.zeros(256, 128, dtype=torch.bfloat16)
+    Bm = torch.zeros(32, 128, dtype=torch.bfloat16)
+    C = torch.zeros(256, 32)
+    err = torch.zeros(1, dtype=torch.int32)
+    assert B._gemm_shapes(A, Bm, C, err) == (256, 128, 32)
+    assert B._gemm_shapes(A, Bm, torch.zeros(256, 48), err) == (256, 128, 32)  # ldc > N
+    for bad in [(A, torch.zeros(32, 64, dtype=torch.bfloat16), C, err),   # K mismatch
+                (A, Bm, torch.zeros(128, 32), err),                        # C too short
+                (A, Bm, torch.zeros(256, 16), err),                        # C too narrow
+                (A, Bm, C, torch.zeros(0, dtype=torch.int32)),             # no error word
+                (A.reshape(-1), Bm, C, err)]:                              # not a matrix
+        with pytest.raises(ValueError):
+            B._gemm_shapes(*bad)
+
+
 def test_noalloc_shapes_rejected_on_the_host():
     """The allocation-free shifted solve takes bare pointers too: every
     buffer is checked against n and nsys before any device call."""
