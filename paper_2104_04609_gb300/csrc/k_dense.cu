@@ -39,6 +39,7 @@
 #include <mutex>
 
 #include "osrc_internal.cuh"
+#include "stream_k.cuh"
 
 namespace {
 
@@ -120,20 +121,6 @@ __host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-// The iterations [it, end) of a CTA cut at tile boundaries: one segment per
-// tile touched, K slices kb0 .. kb0 + n - 1 of tile `tile`.
-struct Seg {
-    int tile, kb0, n;
-};
-__device__ __forceinline__ Seg next_seg(long long it, long long end, int KB) {
-    Seg s;
-    s.tile = (int)(it / KB);
-    s.kb0 = (int)(it - (long long)s.tile * KB);
-    const long long left = end - it;
-    s.n = (int)((long long)(KB - s.kb0) < left ? (long long)(KB - s.kb0) : left);
-    return s;
-}
-
 // ncols = tensor-memory columns of one accumulator (a power of two >= N);
 // two accumulators alternate between the tile segments of a CTA.
 __global__ void __launch_bounds__(UM_THREADS, 1)
@@ -153,7 +140,7 @@ umma_sk_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int G = gridDim.x, cta = blockIdx.x;
-    const long long it_begin = (long long)cta * iters / G, it_end = (long long)(cta + 1) * iters / G;
+    const long long it_begin = sk_begin(cta, iters, G), it_end = sk_begin(cta + 1, iters, G);
     const uint32_t tcols = (uint32_t)nbuf * ncols;
 
     if (threadIdx.x == 0) {
@@ -188,7 +175,7 @@ umma_sk_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
             uint32_t g = 0;  // K slices issued
             bool ok = true;
             for (long long it = it_begin; it < it_end && ok;) {
-                const Seg sg = next_seg(it, it_end, KB);
+                const SkSeg sg = sk_next(it, it_end, KB);
                 for (int j = 0; j < sg.n; ++j) {
                     const uint32_t s = g % (uint32_t)stages, u = g / (uint32_t)stages;
                     if (g >= (uint32_t)stages && !mbar_wait(&empty[s], (u - 1) & 1)) {
@@ -223,7 +210,7 @@ umma_sk_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
             int seg = 0;
             bool ok = true;
             for (long long it = it_begin; it < it_end && ok; ++seg) {
-                const Seg sg = next_seg(it, it_end, KB);
+                const SkSeg sg = sk_next(it, it_end, KB);
                 const int b = seg % nbuf;
                 const uint32_t use = (uint32_t)(seg / nbuf);
                 if (seg >= nbuf && !mbar_wait(&acce[b], (use - 1) & 1)) {
@@ -273,7 +260,7 @@ umma_sk_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
         // epilogue: warps 0-3
         int seg = 0;
         for (long long it = it_begin; it < it_end; ++seg) {
-            const Seg sg = next_seg(it, it_end, KB);
+            const SkSeg sg = sk_next(it, it_end, KB);
             const int b = seg % nbuf;
             const uint32_t use = (uint32_t)(seg / nbuf);
             // the warp decides together: tcgen05.ld below needs all 32 lanes
@@ -291,8 +278,7 @@ umma_sk_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
                 rows = M - sg.tile * UM_BM;
                 vec = (ldc & 3) == 0 && ((uintptr_t)C & 15) == 0;
             } else {
-                const int slot = 2 * cta + (seg == 0 ? 0 : 1);
-                dst = ws + (size_t)slot * UM_BM * N;
+                dst = ws + (size_t)sk_slot(cta, seg) * UM_BM * N;
                 ld = N;
                 rows = UM_BM;
                 vec = true;
@@ -353,9 +339,8 @@ umma_sk_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
 __global__ void umma_sk_fixup_kernel(int M, int N, int bmt, int KB, long long iters, int G,
                                      const float *__restrict__ ws, float *__restrict__ C, int ldc, bool vec) {
     const int tile = blockIdx.x;
-    const long long x0 = (long long)tile * KB, x1 = x0 + KB - 1;
-    const int c_lo = (int)(((x0 + 1) * G + iters - 1) / iters - 1);
-    const int c_hi = (int)(((x1 + 1) * G + iters - 1) / iters - 1);
+    int c_lo, c_hi;
+    sk_tile_ctas(tile, KB, iters, G, &c_lo, &c_hi);
     if (c_lo == c_hi) return;  // one CTA covered the tile and wrote C itself
     const int rows = min(bmt, M - tile * bmt), n4 = N / 4;
     const int rbeg = blockIdx.y * UM_FIX_ROWS, rend = min(rows, rbeg + UM_FIX_ROWS);
@@ -363,8 +348,7 @@ __global__ void umma_sk_fixup_kernel(int M, int N, int bmt, int KB, long long it
         const int r = rbeg + e / n4, q = e % n4;
         float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int c = c_lo; c <= c_hi; ++c) {
-            const long long first = (long long)c * iters / G;
-            const int slot = 2 * c + ((int)(first / KB) == tile ? 0 : 1);
+            const int slot = sk_piece_slot(c, tile, KB, iters, G);
             const float4 v = reinterpret_cast<const float4 *>(ws + ((size_t)slot * bmt + r) * N)[q];
             s.x += v.x;
             s.y += v.y;
@@ -463,7 +447,7 @@ static int umma_plan(int M, int N, int K, UmmaPlan *p) {
     if (q.stages > UM_MAX_STAGES) q.stages = UM_MAX_STAGES;
     q.smem = UM_SMEM_FIXED + (size_t)q.stages * stage;
     for (int c = 1; c < q.grid && !q.split; ++c)
-        if (((long long)c * q.iters / q.grid) % q.KB) q.split = true;
+        if (sk_begin(c, q.iters, q.grid) % q.KB) q.split = true;
     q.ws_floats = q.split ? (size_t)2 * q.grid * UM_BM * N : 0;
     *p = q;
     return OSRC_OK;
