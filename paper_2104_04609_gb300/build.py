@@ -33,7 +33,7 @@ def _nvcc():
 def _deps():
     files = [os.path.join(CSRC, s) for s in SOURCES]
     files += [os.path.abspath(__file__), os.path.join(CSRC, "osrc_internal.cuh"), os.path.join(CSRC, "ffmath.cuh"),
-              os.path.join(CSRC, "stream_k.cuh"),
+              os.path.join(CSRC, "stream_k.cuh"), os.path.join(CSRC, "dense_sched.cuh"),
               os.path.join(os.path.dirname(HERE), "include", "osrc_pmchwt.h")]
     return files
 

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "osrc_internal.cuh"
+#include "dense_sched.cuh"
 
 namespace {
 
@@ -295,17 +296,8 @@ struct DenseSched {
 // and the stash row; false when out of range
 __device__ __forceinline__ bool dense_pair(const DenseSched &sc, int lp, int &t, int &s, long long &row) {
     if (sc.diag) {  // folded triangular enumeration of i < k within one list
-        const int f = blockIdx.y, n = sc.na;
-        const long long j = (long long)blockIdx.x * DA_PAIRS + lp;
-        int i = -1, k = -1;
-        if (j < n - 1 - f) {
-            i = f;
-            k = f + 1 + (int)j;
-        } else if (n - 1 - f != f && j < n - 1) {
-            i = n - 1 - f;
-            k = i + 1 + (int)(j - (n - 1 - f));
-        }
-        if (i < 0 || k >= n) return false;
+        int i, k;
+        if (!dense_diag_pair((int)blockIdx.y, (long long)blockIdx.x * DA_PAIRS + lp, sc.na, &i, &k)) return false;
         t = sc.la[i];
         s = sc.la[k];
         row = -1;
@@ -781,28 +773,8 @@ int dense_assemble(osrc_problem *pb, cudaStream_t st) {
                  pb->mesh->d_tcomp.p, pb->p.formulation == OSRC_MULLER ? -1.0 : 1.0, pb->p.k_int_im};
     // colours: greedy, in triangle order, so that triangles sharing a vertex
     // differ; lists of each colour's triangles (ascending)
-    std::vector<int> col(nt, -1);
-    int ncol = 0;
-    {
-        std::vector<int> seen(64, -1);
-        for (int t = 0; t < nt; ++t) {
-            for (int a = 0; a < 3; ++a) {
-                const int v = m->tris[3 * t + a];
-                for (int e = m->vt_ptr[v]; e < m->vt_ptr[v + 1]; ++e) {
-                    const int c2 = col[m->vt_idx[e] / 3];
-                    if (c2 >= 0) {
-                        if (c2 >= (int)seen.size()) seen.resize(2 * c2 + 2, -1);
-                        seen[c2] = t;
-                    }
-                }
-            }
-            int c = 0;
-            while (c < (int)seen.size() && seen[c] == t) ++c;
-            col[t] = c;
-            if (c >= (int)seen.size()) seen.resize(2 * c + 2, -1);
-            ncol = std::max(ncol, c + 1);
-        }
-    }
+    std::vector<int> col;
+    const int ncol = dense_colour(nt, m->tris.data(), m->vt_ptr.data(), m->vt_idx.data(), col);
     std::vector<int> cbeg(ncol + 1, 0), order(nt);
     for (int t = 0; t < nt; ++t) cbeg[col[t] + 1]++;
     for (int c = 0; c < ncol; ++c) cbeg[c + 1] += cbeg[c];
