@@ -198,29 +198,36 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
-        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
-                 "sw_power_cap"]
         with open(self.path) as f:
-            for line in f:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    idx = int(parts[0])
-                except ValueError:
-                    continue
-                if idx not in self.gpus:
-                    continue
-                try:
-                    sm.append(float(parts[1]))
-                    mx.append(float(parts[2]))
-                except ValueError:
-                    pass
-                for n, v in zip(names[1:], parts[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(n)
+            out = self.parse(f, self.gpus)
         os.unlink(self.path)
+        return out
+
+    @staticmethod
+    def parse(lines, gpus):
+        """Median and maximum SM clock and the throttle reasons seen, from
+        nvidia-smi CSV lines of QUERY (no header, no units) for the GPUs in
+        gpus; lines of other GPUs and unreadable lines are skipped."""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                idx = int(parts[0])
+            except ValueError:
+                continue
+            if idx not in gpus:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                pass
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}

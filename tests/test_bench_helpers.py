@@ -48,3 +48,23 @@ def test_bench_p1_mass_and_solution_error():
     W2 = dict(W, verts=v @ R.T)
     e2 = bench.solution_error_vs_mie(W2, 1.01 * x, R @ d)
     assert abs(e2["both"] - 0.01) < 1e-12
+
+
+def test_clock_record_parsing():
+    """The clocks object of the bench line: median / max SM clock of the
+    sampled GPU and the throttle reasons seen while the timed region ran."""
+    lines = [
+        "0, 2070, 2070, 1100.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "0, 2055, 2070, 1380.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n",
+        "0, 2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "1, 900, 2070, 300.0, 0x0000000000000008, Active, Not Active, Not Active, Not Active\n",  # other GPU
+        "0, [N/A], 2070, 1000, 0x0, Not Active, Not Active, Not Active, Not Active\n",            # no clock
+        "garbage line\n",
+    ]
+    r = bench.ClockSampler.parse(lines, [0])
+    assert r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0 and r["samples"] == 3
+    assert r["reasons"] == ["sw_power_cap"]
+    r = bench.ClockSampler.parse(lines, [0, 1])
+    assert r["reasons"] == ["hw_slowdown", "sw_power_cap"] and r["samples"] == 4
+    r = bench.ClockSampler.parse([], [0])
+    assert r["sm_mhz"] is None and r["reasons"] == [] and r["samples"] == 0
